@@ -1,0 +1,267 @@
+"""Pins of the CPU oracle against things other than itself (CPU only).
+
+Each pin targets a plausible mistake: a hand evaluation of Eqs. (4)-(9)
+(wrong sign or offset in the index map, a dropped flip), a dense measurement
+matrix built by pattern placement and transposed by numpy (wrong pairing of
+axes, wrong centring, non-square mix-ups), closed special cases (N = 1 is a
+180-degree kernel rotation, shift-invariant PSFs), invariants the paper
+states (reversibility, Sec. 3; summed slices rotated by 180 degrees, Sec. 3),
+the adjoint identity of the projectors and central finite differences.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import lfgen
+import oracle
+
+
+def _read_golden(path):
+    rows = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            p, u = int(tok[0]), int(tok[1])
+            if tok[2] == "-":
+                paper, trans = None, (int(tok[3]), int(tok[4]))
+            else:
+                paper = (int(tok[2]), int(tok[3]))
+                trans = (int(tok[4]), int(tok[5]))
+            rows[(p, u)] = (paper, trans)
+    return rows
+
+
+def _tagged_1d(N, K):
+    """1-D array (Ny = Kt = 1) whose value encodes its own (a, s) position."""
+    H = np.zeros(N * K)
+    for a in range(N):
+        for s in range(K):
+            H[a * K + s] = 100 * a + s + 1
+    return H
+
+
+def _tag(a, s):
+    return 100 * a + s + 1
+
+
+@pytest.mark.parametrize("fname,N,K", [("eqs4to9_nx3_ns5.txt", 3, 5),
+                                       ("eqs4to9_nx3_ns3.txt", 3, 3)])
+def test_golden_hand_evaluation(golden_dir, fname, N, K):
+    rows = _read_golden(os.path.join(golden_dir, fname))
+    assert len(rows) == N * K
+    H = _tagged_1d(N, K)
+    pw = oracle.paper_window(H, N, 1, [K], [1])
+    tr = oracle.transpose(H, N, 1, [K], [1])
+    for (p, u), (paper, trans) in rows.items():
+        i = p * K + u
+        assert tr[i] == _tag(*trans), (p, u)
+        assert pw[i] == (0 if paper is None else _tag(*paper)), (p, u)
+
+
+SHAPES = [  # Nx, Ny, Ks, Kt
+    (3, 3, 9, 9), (5, 3, 15, 9), (3, 5, 5, 3), (1, 3, 5, 7), (5, 5, 5, 5),
+    (3, 3, 3, 3), (7, 5, 7, 11),
+]
+
+
+def _rand(shape_elems, seed):
+    return np.random.default_rng(seed).uniform(-1, 1, shape_elems)
+
+
+@pytest.mark.parametrize("Nx,Ny,Ks,Kt", SHAPES)
+def test_dense_measurement_matrix_transpose(Nx, Ny, Ks, Kt):
+    """H' read off the numpy transpose of the dense Eq. (1) matrix, every pixel."""
+    Hz = _rand((Nx, Ny, Ks, Kt), 1)
+    Mx = -(-Ks // Nx) + 2
+    My = -(-Kt // Ny) + 2
+    Wx, Wy = Mx * Nx, My * Ny
+    B = oracle.measurement_matrix(Hz, Mx, My, periodic=True).T  # [voxel][pixel]
+    Hp = oracle.transpose(Hz.reshape(-1), Nx, Ny, [Ks], [Kt]).reshape(Nx, Ny, Ks, Kt)
+    cs, ct = (Ks - 1) // 2, (Kt - 1) // 2
+    for Sx in range(Wx):
+        for Sy in range(Wy):
+            col = B[:, Sx * Wy + Sy].reshape(Wx, Wy).copy()
+            win = np.empty((Ks, Kt))
+            for u in range(Ks):
+                for v in range(Kt):
+                    X, Y = (Sx + u - cs) % Wx, (Sy + v - ct) % Wy
+                    win[u, v] = col[X, Y]
+                    col[X, Y] = 0.0
+            np.testing.assert_array_equal(win, Hp[Sx % Nx, Sy % Ny])
+            # nothing outside the pixel-centred window reaches this pixel
+            assert not np.any(col)
+
+
+PW_SHAPES = SHAPES + [(11, 11, 89, 89), (5, 7, 15, 21), (7, 3, 5, 3), (9, 9, 27, 45)]
+
+
+@pytest.mark.parametrize("Nx,Ny,Ks,Kt", PW_SHAPES)
+def test_paper_window_is_masked_transpose(Nx, Ny, Ks, Kt):
+    """Eqs. (4)-(9) write exactly the transpose, except on the overhang entries."""
+    H = _rand(Nx * Ny * Ks * Kt, 2)
+    pw = oracle.paper_window(H, Nx, Ny, [Ks], [Kt]).reshape(Nx, Ny, Ks, Kt)
+    tr = oracle.transpose(H, Nx, Ny, [Ks], [Kt]).reshape(Nx, Ny, Ks, Kt)
+    hx, hy = (Nx - 1) // 2, (Ny - 1) // 2
+    p = np.arange(Nx)[:, None, None, None]
+    q = np.arange(Ny)[None, :, None, None]
+    u = np.arange(Ks)[None, None, :, None]
+    v = np.arange(Kt)[None, None, None, :]
+    keep = (p + u >= hx) & (p + u <= Ks - 1 + hx) & (q + v >= hy) & (q + v <= Kt - 1 + hy)
+    np.testing.assert_array_equal(pw, np.where(keep, tr, 0.0))
+    if Ks >= Nx:
+        keep_x = (np.arange(Nx)[:, None] + np.arange(Ks)[None, :])
+        dropped = np.sum((keep_x < hx) | (keep_x > Ks - 1 + hx))
+        assert dropped == hx * (hx + 1)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16, np.float64, np.uint8])
+def test_involution_and_adjoint(dtype):
+    """Reversibility (Sec. 3): mapping H' again returns H; the adjoint is the map."""
+    Nx, Ny, Ks, Kt = 5, 3, [15, 5, 9], [9, 3, 21]
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    rng = np.random.default_rng(3)
+    if dtype == np.uint8:
+        H = rng.integers(0, 256, n).astype(np.uint8)
+    else:
+        H = rng.uniform(-1, 1, n).astype(dtype)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    assert not np.array_equal(Hp, H)
+    np.testing.assert_array_equal(oracle.transpose(Hp, Nx, Ny, Ks, Kt), H)
+    np.testing.assert_array_equal(oracle.transpose_adjoint(H, Nx, Ny, Ks, Kt), Hp)
+
+
+def test_multisets_and_summed_slices():
+    """Each depth's values are preserved; Sec. 3's summed-slice identity holds."""
+    spec = lfgen.config_specs("tiny")[0]
+    H = lfgen.generate(spec).numpy()
+    Hp = oracle.transpose(H, spec.Nx, spec.Ny, spec.Ks, spec.Kt)
+    off = lfgen.depth_offsets(spec)
+    for z, (ks, kt) in enumerate(zip(spec.Ks, spec.Kt)):
+        n = spec.Nx * spec.Ny * ks * kt
+        a = H[off[z]:off[z] + n].reshape(spec.Nx, spec.Ny, ks, kt)
+        b = Hp[off[z]:off[z] + n].reshape(spec.Nx, spec.Ny, ks, kt)
+        np.testing.assert_array_equal(np.sort(a.view(np.uint32), axis=None),
+                                      np.sort(b.view(np.uint32), axis=None))
+        # for each (u, v): the N^2 summands of H' equal those of H at (K-1-u, K-1-v)
+        lhs = np.sort(b.reshape(-1, ks, kt), axis=0)
+        rhs = np.sort(a[:, :, ::-1, ::-1].reshape(-1, ks, kt), axis=0)
+        np.testing.assert_array_equal(lhs, rhs)
+        # the summed image of H' is the summed image of H rotated by 180 degrees
+        s_hp = b.astype(np.float64).sum(axis=(0, 1))
+        s_h = np.rot90(a.astype(np.float64).sum(axis=(0, 1)), 2)
+        np.testing.assert_allclose(s_hp, s_h, rtol=1e-13, atol=1e-15)
+
+
+def test_single_position_is_rot180():
+    """N = 1 (shift-invariant imaging): H' is the 180-degree rotation of each kernel."""
+    Ks, Kt = [5, 9, 3], [7, 9, 1]
+    H = _rand(sum(a * b for a, b in zip(Ks, Kt)), 4)
+    Hp = oracle.transpose(H, 1, 1, Ks, Kt)
+    off = 0
+    for ks, kt in zip(Ks, Kt):
+        k = H[off:off + ks * kt].reshape(ks, kt)
+        np.testing.assert_array_equal(Hp[off:off + ks * kt].reshape(ks, kt), np.rot90(k, 2))
+        off += ks * kt
+
+
+def test_shift_invariant_kernel():
+    """All cell positions share one kernel: every H' slice is that kernel rotated."""
+    Nx, Ny, K = 5, 3, 15
+    k = _rand((K, K), 5)
+    Hz = np.broadcast_to(k, (Nx, Ny, K, K)).copy()
+    Hp = oracle.transpose(Hz.reshape(-1), Nx, Ny, [K], [K]).reshape(Nx, Ny, K, K)
+    for p in range(Nx):
+        for q in range(Ny):
+            np.testing.assert_array_equal(Hp[p, q], np.rot90(k, 2))
+
+
+def test_special_bit_patterns_survive():
+    """The map moves bits: NaN payloads, -0, inf and subnormals come through."""
+    Nx, Ny, Ks, Kt = 3, 3, [9], [9]
+    n = 81 * 9
+    bits = np.random.default_rng(6).integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    specials = np.array([0x7fc00001, 0x7f800001, 0xffc12345, 0x80000000, 0x7f800000,
+                         0xff800000, 0x00000001, 0x807fffff], dtype=np.uint32)
+    bits[:len(specials)] = specials
+    H = bits.view(np.float32)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(np.sort(Hp.view(np.uint32)), np.sort(bits))
+    np.testing.assert_array_equal(oracle.transpose(Hp, Nx, Ny, Ks, Kt).view(np.uint32), bits)
+
+
+def _proj_case(seed=7):
+    Nx, Ny, Ks, Kt = 3, 5, [9, 3, 15], [15, 5, 5]
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    rng = np.random.default_rng(seed)
+    H = rng.uniform(0, 1, n)
+    Wx, Wy = 13, 17
+    g = rng.uniform(0, 1, (len(Ks), Wx, Wy))
+    f = rng.uniform(0, 1, (Wx, Wy))
+    return Nx, Ny, Ks, Kt, H, g, f
+
+
+def test_adjoint_identity_fp64():
+    """<H g, f> = <g, H' f> on a finite zero-padded domain (FP64)."""
+    Nx, Ny, Ks, Kt, H, g, f = _proj_case()
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    lhs = np.sum(oracle.forward(H, Nx, Ny, Ks, Kt, g) * f)
+    rhs = np.sum(g * oracle.backproject(Hp, Nx, Ny, Ks, Kt, f))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_projectors_match_dense_matrix():
+    """Forward = A g and backprojection = A^T f with A built by pattern placement."""
+    Nx, Ny, K = 3, 3, 9
+    rng = np.random.default_rng(8)
+    Hz = rng.uniform(0, 1, (Nx, Ny, K, K))
+    Mx = My = 4
+    A = oracle.measurement_matrix(Hz, Mx, My, periodic=False)
+    W = Mx * Nx
+    g = rng.uniform(0, 1, (1, W, W))
+    f = rng.uniform(0, 1, (W, W))
+    np.testing.assert_allclose(oracle.forward(Hz.reshape(-1), Nx, Ny, [K], [K], g).reshape(-1),
+                               A @ g.reshape(-1), rtol=1e-13, atol=1e-13)
+    Hp = oracle.transpose(Hz.reshape(-1), Nx, Ny, [K], [K])
+    np.testing.assert_allclose(oracle.backproject(Hp, Nx, Ny, [K], [K], f).reshape(-1),
+                               A.T @ f.reshape(-1), rtol=1e-13, atol=1e-13)
+
+
+def test_backproject_points_match_full():
+    Nx, Ny, Ks, Kt, H, g, f = _proj_case(9)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    full = oracle.backproject(Hp, Nx, Ny, Ks, Kt, f)
+    rng = np.random.default_rng(10)
+    pts = np.stack([rng.integers(0, len(Ks), 200), rng.integers(0, f.shape[0], 200),
+                    rng.integers(0, f.shape[1], 200)], axis=1)
+    got = oracle.backproject_points(Hp, Nx, Ny, Ks, Kt, f, pts)
+    np.testing.assert_allclose(got, full[pts[:, 0], pts[:, 1], pts[:, 2]], rtol=1e-14, atol=1e-14)
+
+
+def test_gradient_central_differences():
+    """dL/dH for L = sum (H'(H) f - g_ref)^2 against FP64 central differences."""
+    Nx, Ny, Ks, Kt = 3, 3, [9, 3], [9, 3]
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    rng = np.random.default_rng(11)
+    H = rng.uniform(0, 1, n)
+    W = 2 * Nx
+    f = rng.uniform(0, 1, (W, W))
+    gref = rng.uniform(0, 1, (len(Ks), W, W))
+
+    def loss(Hv):
+        g = oracle.backproject(oracle.transpose(Hv, Nx, Ny, Ks, Kt), Nx, Ny, Ks, Kt, f)
+        return np.sum((g - gref) ** 2)
+
+    g = oracle.backproject(oracle.transpose(H, Nx, Ny, Ks, Kt), Nx, Ny, Ks, Kt, f)
+    dhp = oracle.grad_hp(f, 2.0 * (g - gref), Nx, Ny, Ks, Kt)
+    dh = oracle.transpose_adjoint(dhp, Nx, Ny, Ks, Kt)
+    h = 1e-6
+    for i in rng.choice(n, 40, replace=False):
+        Hplus, Hminus = H.copy(), H.copy()
+        Hplus[i] += h
+        Hminus[i] -= h
+        fd = (loss(Hplus) - loss(Hminus)) / (2 * h)
+        assert abs(fd - dh[i]) <= 1e-6 * max(1.0, abs(dh[i])), (i, fd, dh[i])

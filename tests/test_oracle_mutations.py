@@ -1,0 +1,129 @@
+"""Planted mistakes in the oracle must be caught by its pins (CPU only).
+
+Each case copies lfbp_oracle.c with one plausible slip (wrong sign, dropped
+flip, off-by-one, swapped axis), builds the copy into a temporary directory
+and checks that the hand-evaluated Eqs. (4)-(9) tables or the dense
+measurement-matrix transpose reject it.  Every slip keeps all indices in
+range, so the mutated code cannot read or write outside its arrays.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "lfbp_oracle.c")
+
+MUTATIONS = {
+    "transpose_sign": ("long Xx = Sx + u - cs, Xy = Sy + v - ct;",
+                       "long Xx = Sx - u + cs, Xy = Sy + v - ct;"),
+    "cutout_flip": ("long k = S - X + (K - 1) / 2;", "long k = X - S + (K - 1) / 2;"),
+    "transpose_cell_offset": ("int a = (int)floor_mod(Xx, Nx);      /* voxel's cell position */",
+                              "int a = (int)floor_mod(Xx + 1, Nx);"),
+    "transpose_axes": ("int b = (int)floor_mod(Xy, Ny);\n                    int s = cutout_index(Sx, Xx, ks);",
+                       "int b = (int)floor_mod(Xx, Ny);\n                    int s = cutout_index(Sx, Xx, ks);"),
+    "eq8_no_flip": ("long sp = ns - s + (ns % 2);", "long sp = s;"),
+    "eq6_offset": ("xp[m] = s - nx + alpha[m] + floor_div(nx - 1, 2) - dS;",
+                   "xp[m] = s - nx + alpha[m] + floor_div(nx - 1, 2) - dS + 1;"),
+    "eq5_wrap": ("if (alpha <= 0) return alpha + ceil_div(1 - alpha, n) * n;",
+                 "if (alpha <= 0) return alpha + floor_div(1 - alpha, n) * n + n;"),
+    "eq4_alpha": ("long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);",
+                  "long dS = floor_div(ns - nx + 2, 2), dT = floor_div(nt - ny, 2);"),
+}
+
+
+def _build_variant(tmp_path, name):
+    src = open(SRC).read()
+    old, new = MUTATIONS[name]
+    assert src.count(old) == 1, name
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / f"{name}.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-o", str(so), str(path)])
+    lib = ctypes.CDLL(str(so))
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.oracle_transpose.argtypes = [P, P, I, I, I, I, P, P, I]
+    lib.oracle_paper_window.argtypes = [P, P, I, I, I, I, P, P]
+    return lib
+
+
+def _run(fn, H, Nx, Ny, Ks, Kt, *extra):
+    out = np.zeros_like(H)
+    ks = np.asarray(Ks, dtype=np.int32)
+    kt = np.asarray(Kt, dtype=np.int32)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = fn(p(H), p(out), H.itemsize, Nx, Ny, len(ks), p(ks), p(kt), *extra)
+    return rc, out
+
+
+def _pins_pass(lib):
+    """True iff the variant passes the golden tables and the dense-matrix pin."""
+    from test_oracle import _read_golden, _tagged_1d, _tag
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    for fname, N, K in [("eqs4to9_nx3_ns5.txt", 3, 5), ("eqs4to9_nx3_ns3.txt", 3, 3)]:
+        rows = _read_golden(os.path.join(gold, fname))
+        H = _tagged_1d(N, K)
+        rc_t, tr = _run(lib.oracle_transpose, H, N, 1, [K], [1], 1)
+        rc_p, pw = _run(lib.oracle_paper_window, H, N, 1, [K], [1])
+        if rc_t != 0 or rc_p != 0:
+            return False
+        for (p, u), (paper, trans) in rows.items():
+            if tr[p * K + u] != _tag(*trans):
+                return False
+            if pw[p * K + u] != (0 if paper is None else _tag(*paper)):
+                return False
+    Nx, Ny, Ks, Kt = 5, 3, 15, 9
+    Hz = np.random.default_rng(1).uniform(-1, 1, (Nx, Ny, Ks, Kt))
+    rc, Hp = _run(lib.oracle_transpose, Hz.reshape(-1), Nx, Ny, [Ks], [Kt], 1)
+    if rc != 0:
+        return False
+    Hp = Hp.reshape(Nx, Ny, Ks, Kt)
+    Mx, My = 5, 5
+    B = oracle.measurement_matrix(Hz, Mx, My).T
+    Wy = My * Ny
+    for Sx, Sy in [(0, 0), (3, 7), (11, 2)]:
+        col = B[:, Sx * Wy + Sy].reshape(Mx * Nx, Wy)
+        for u in range(Ks):
+            for v in range(Kt):
+                X, Y = (Sx + u - 7) % (Mx * Nx), (Sy + v - 4) % Wy
+                if col[X, Y] != Hp[Sx % Nx, Sy % Ny, u, v]:
+                    return False
+    # Eqs. (4)-(9) with several added slices (alpha reaches -2 and below):
+    # the paper's loop must equal the transpose on the entries it writes
+    for Nx, Ny, Ks, Kt in [(3, 5, 9, 15), (5, 3, 25, 9)]:
+        H = np.random.default_rng(2).uniform(-1, 1, Nx * Ny * Ks * Kt)
+        rc_t, tr = _run(lib.oracle_transpose, H, Nx, Ny, [Ks], [Kt], 1)
+        rc_p, pw = _run(lib.oracle_paper_window, H, Nx, Ny, [Ks], [Kt])
+        if rc_t != 0 or rc_p != 0:
+            return False
+        hx, hy = (Nx - 1) // 2, (Ny - 1) // 2
+        p = np.arange(Nx)[:, None, None, None]
+        q = np.arange(Ny)[None, :, None, None]
+        u = np.arange(Ks)[None, None, :, None]
+        v = np.arange(Kt)[None, None, None, :]
+        keep = ((p + u >= hx) & (p + u <= Ks - 1 + hx) & (q + v >= hy) & (q + v <= Kt - 1 + hy))
+        want = np.where(keep, tr.reshape(Nx, Ny, Ks, Kt), 0.0)
+        if not np.array_equal(pw.reshape(Nx, Ny, Ks, Kt), want):
+            return False
+    return True
+
+
+def test_unmutated_passes(tmp_path):
+    src = open(SRC).read()
+    path = tmp_path / "plain.c"
+    path.write_text(src)
+    so = tmp_path / "plain.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-o", str(so), str(path)])
+    lib = ctypes.CDLL(str(so))
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.oracle_transpose.argtypes = [P, P, I, I, I, I, P, P, I]
+    lib.oracle_paper_window.argtypes = [P, P, I, I, I, I, P, P]
+    assert _pins_pass(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    assert not _pins_pass(_build_variant(tmp_path, name))
