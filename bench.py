@@ -1,0 +1,433 @@
+"""Benchmark: H' build throughput (GB/s of algorithmic bytes) on GB300.
+
+One step = H -> H' over every depth of the workload (all steps of the map:
+per-depth split, index map, flip, exchange, data movement), with the input
+resident in HBM.  The headline form is the batched persistent launch; the
+plain per-depth form is timed beside it on the same GPU.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload highres|mid|ragged|autograd|tiny] [--dtype f32|f16]
+
+Algorithmic bytes per step = 2 * sum_z Nx*Ny*Ks_z*Kt_z * esize (every element
+read once and written once).  Inputs are larger than L2 (129 MB) for the
+default workload, so no flush runs between steps.  Under torchrun every
+rank maps its own copy of the workload (independent problems, no
+collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "H' build GB/s and % of HBM peak on 1 GB300, batched vs per-depth form, bit-exact"
+SPEC_GBS = 8000.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("lfbp.cu", "lfbp_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2003_09133_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_record(workload, dtype):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        ent = rec.get(f"{workload}:{dtype}")
+        if ent and ent.get("source_sha") == _kernel_source_sha():
+            return ent
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0, period_ms=50):
+        self.index, self.period_ms = index, period_ms
+        self.proc, self.path = None, None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for _, _, flags in rows:
+            for n, f in zip(names, flags[1:]):
+                if f.lower() in ("active", "0x1", "1"):
+                    seen.add(n)
+        mhz = sorted(r[0] for r in rows)
+        return {"sm_mhz": mhz[len(mhz) // 2], "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(seen)}
+
+
+def _workload_desc(specs, dtype_override):
+    if len(specs) == 1:
+        s = specs[0]
+        return (f"{s.name}: Nx=Ny={s.Nx}, Nz={s.Nz}, K_z {min(s.Ks)}..{max(s.Ks)} px, "
+                f"ragged in depth, {dtype_override or s.dtype}")
+    return f"{specs[0].name[:6]}: {len(specs)} arrays, mixed fp32/fp16, ragged"
+
+
+def _dist():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _cpu_oracle_rate(specs, Hs_host, dtype_override, budget_s=12.0, max_passes=4):
+    """Time the CPU oracle (as it stands) on the workload: GB/s of algorithmic bytes."""
+    import numpy as np
+    import oracle
+    done_bytes, t_total, passes = 0, 0.0, 0
+    cores = oracle.threads(0)
+    sample_desc = []
+    while passes < max_passes and t_total < budget_s:
+        for s, H in zip(specs, Hs_host):
+            t0 = time.perf_counter()
+            oracle.transpose(H, s.Nx, s.Ny, s.Ks, s.Kt)
+            t_total += time.perf_counter() - t0
+            done_bytes += 2 * H.nbytes
+            if passes == 0:
+                sample_desc.append(s.name)
+            if t_total >= budget_s:
+                break
+        passes += 1
+    return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "seconds": round(t_total, 3),
+            "sample": f"{done_bytes / 2 / 1e9:.2f} GB of H mapped by oracle.transpose "
+                      f"({passes} pass(es) over {'+'.join(sample_desc)}; C, OpenMP {cores} threads)"}
+
+
+def _reference_sample(specs, budget_elems=48_000_000):
+    """Evenly spaced depths of the workload holding about budget_elems elements."""
+    import lfgen
+    depths = []
+    for ai, s in enumerate(specs):
+        off = lfgen.depth_offsets(s)
+        for z in range(s.Nz):
+            depths.append((ai, z, off[z], s.Nx * s.Ny * s.Ks[z] * s.Kt[z]))
+    total = sum(d[3] for d in depths)
+    m = max(1, round(len(depths) * budget_elems / max(1, total)))
+    stride = max(1, len(depths) // m)
+    picks, acc = [], 0
+    for d in depths[stride // 2::stride]:
+        if picks and acc + d[3] > 1.5 * budget_elems:
+            continue
+        picks.append(d)
+        acc += d[3]
+    return picks, acc
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores, same metric and workload.
+
+    Each step maps a fixed sample of the workload's depths (every k-th depth,
+    about 48 M elements) with oracle.transpose, so that a run of --steps K
+    stays within a few minutes; the value is that sample's GB/s.
+    """
+    import torch
+    import lfgen
+    import oracle
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    specs = _pick_specs(args)
+    picks, acc = _reference_sample(specs)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    arrays = {}
+    for ai in sorted({p[0] for p in picks}):
+        s = specs[ai]
+        arrays[ai] = lfgen.generate(s, device=dev).to(_torch_dtype(args, s)).cpu().numpy()
+    sample = [(specs[ai], arrays[ai][off:off + n].copy(), z) for ai, z, off, n in picks]
+    nbytes = sum(2 * h.nbytes for _, h, _ in sample)
+
+    def one_step():
+        for s, h, z in sample:
+            oracle.transpose(h, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
+
+    for _ in range(args.warmup):
+        one_step()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        one_step()
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    val = nbytes / t / 1e9
+    cores = oracle.threads(0)
+    desc = (f"{len(sample)} of the workload's depths (evenly spaced), "
+            f"{acc / 1e6:.1f} M elements, {nbytes / 2 / 1e9:.3f} GB of H) per step, "
+            f"oracle.transpose in C with OpenMP")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(val, 3), "unit": "GB/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": _dtype_name(args, specs), "data": "synthetic",
+        "config": _config(args, specs),
+        "cpu_baseline": {"value": round(val, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(val, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _torch_dtype(args, spec):
+    import torch
+    if args.dtype == "f16":
+        return torch.float16
+    if args.dtype == "f32":
+        return torch.float32
+    return spec.torch_dtype
+
+
+def _dtype_name(args, specs):
+    if args.dtype:
+        return args.dtype
+    names = sorted({s.dtype for s in specs})
+    return "+".join(names)
+
+
+def _pick_specs(args):
+    import lfgen
+    return lfgen.config_specs(args.workload)
+
+
+def _config(args, specs):
+    import lfgen
+    elems = sum(lfgen.array_elems(s) for s in specs)
+    return {"workload": _workload_desc(specs, args.dtype), "arrays": len(specs),
+            "elements_per_rank": elems, "form": "batched persistent (1 launch, CUDA graph)",
+            "l2": "inputs larger than L2 (no flush)" if elems * 2 > 129e6 else
+                  "L2 flushed between steps"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import lfgen
+    import paper_2003_09133_gb300 as lf
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    lf.load()
+    specs = _pick_specs(args)
+    plans, Hs, outs = [], [], []
+    for s in specs:
+        dt = _torch_dtype(args, s)
+        plans.append(lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, dt))
+        Hs.append(lfgen.generate(s, device="cuda").to(dt))
+        outs.append(torch.empty_like(Hs[-1]))
+    torch.cuda.synchronize()
+    step_bytes = sum(2 * h.numel() * h.element_size() for h in Hs)
+    step_elems = sum(h.numel() for h in Hs)
+    flush = None
+    if step_bytes < 2 * 129e6:
+        flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step_batched():
+        lf.backproject_batched(plans, Hs, outs)
+
+    def step_plain():
+        for p, h, o in zip(plans, Hs, outs):
+            lf.backproject_array(p, h, o)
+
+    def timed(fn, steps, warmup, clocks=False):
+        for _ in range(warmup):
+            fn()
+        lf.sync_status()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        _barrier(world)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.__enter__()
+        for a, b in ev:
+            if flush is not None:
+                flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        _barrier(world)
+        if sampler:
+            sampler.__exit__(None, None, None)
+        lf.sync_status()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        mean = sum(ms) / len(ms)
+        return _max_over_ranks(mean, world), min(ms), (sampler.summary() if sampler else None)
+
+    t_batched, best_batched, clocks = timed(step_batched, args.steps, args.warmup, clocks=True)
+    t_plain, best_plain, _ = timed(step_plain, max(3, args.steps // 4), max(3, args.warmup))
+
+    # end to end through the public API: pinned host H -> device -> H' -> pinned host
+    e2e = None
+    if not args.no_e2e:
+        hosts = [h.cpu().pin_memory() for h in Hs]
+        host_out = [torch.empty_like(h, device="cpu").pin_memory() for h in Hs]
+        dev_in = [torch.empty_like(h) for h in Hs]
+
+        def step_e2e():
+            for hi, di in zip(hosts, dev_in):
+                di.copy_(hi, non_blocking=True)
+            lf.backproject_batched(plans, dev_in, outs)
+            for do, ho in zip(outs, host_out):
+                ho.copy_(do, non_blocking=True)
+
+        n_e2e = max(3, min(args.steps, 20))
+        t_e2e, _, _ = timed(step_e2e, n_e2e, 2)
+        nbytes = sum(h.numel() * h.element_size() for h in Hs)
+        e2e = {"value": round(world * step_bytes / (t_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "ms_per_step": round(t_e2e, 3)}
+        del hosts, host_out, dev_in
+
+    peak, peak_kind = _peaks()
+    achieved = step_bytes / (t_batched * 1e-3) / 1e9
+    value = world * achieved
+    traffic = _traffic_record(args.workload, _dtype_name(args, specs))
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batched, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": _dtype_name(args, specs), "data": "synthetic", "config": _config(args, specs),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "k_gather_persistent",
+                     "traffic": traffic["bytes_per_launch"] if traffic else None,
+                     "algorithmic_bytes_per_launch": step_bytes},
+        "pct_of_8TBps_spec": round(100 * achieved / SPEC_GBS, 2),
+        "elements_per_s": round(world * step_elems / (t_batched * 1e-3), 1),
+        "best_ms_per_step": round(best_batched, 4),
+        "plain": {"ms_per_step": round(t_plain, 4),
+                  "value": round(world * step_bytes / (t_plain * 1e-3) / 1e9, 3),
+                  "best_ms_per_step": round(best_plain, 4),
+                  "launches_per_step": sum(p.Nz for p in plans), "kernel": "k_gather_depth"},
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        Hh = [h.cpu().numpy() for h in Hs]
+        line["cpu_baseline"] = _cpu_oracle_rate(specs, Hh, args.dtype)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="highres",
+                    choices=["tiny", "mid", "ragged", "highres", "autograd"])
+    ap.add_argument("--dtype", choices=["f32", "f16"], default=None)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,148 @@
+/*
+ * lfbp -- light-field backprojection arrays on one GPU (sm_103a).
+ *
+ * Builds the backprojection array H' from the shift-variant light-field PSF
+ * array H as the pure re-arrangement derived in Eberhart, "Efficient
+ * computation of backprojection arrays for 3D light field deconvolution"
+ * (arXiv 2003.09133), Sec. 3, Eqs. (4)-(9): per depth, a flip of the pixel
+ * axes of each cut-out combined with a cyclic exchange of the source
+ * positions of the elementary cell.
+ *
+ * ARRAY LAYOUT (H, H' and their gradients alike).  One flat buffer per
+ * array, depth-major and ragged in depth.  Depth z holds Nx*Ny*Ks[z]*Kt[z]
+ * elements in row-major [a][b][s][t] order and starts at element
+ * lfbp_plan_depth_offset(plan, z).  In H, (a, b) is the source position in
+ * the elementary cell (the paper's x, y; Sec. 2.1, Sec. 3) and (s, t) the
+ * pixel of the voxel-centred cut-out (the paper's s, t).  In H', (a, b) is
+ * the pixel position inside the lenslet (the paper's x', y') and (s, t) the
+ * voxel of the pixel-centred window (the paper's s', t').  The paper's x
+ * pairs with s and y with t.
+ *
+ * THE MAP (default, LFBP_MAP_TRANSPOSE).  With c_s = (Ks-1)/2, c_t = (Kt-1)/2:
+ *     H'[p][q][u][v] = H[(p+u-c_s) mod Nx][(q+v-c_t) mod Ny][Ks-1-u][Kt-1-v]
+ * which is the transpose of the measurement operator of Eq. (1) stored
+ * pixel-centred.  It is a permutation of each depth and its own inverse
+ * (Sec. 3: processing H' gives back H).  Element values are moved as raw
+ * bits (fp32 or fp16 storage); no arithmetic is done on them.
+ *
+ * LFBP_MAP_PAPER_WINDOW reproduces the loop ranges of Eqs. (4)-(9) literally
+ * (m = 1..n_s): entries with p+u < h_x, p+u > Ks-1+h_x, q+v < h_y or
+ * q+v > Kt-1+h_y (h = (N-1)/2) are written as zero bits instead.
+ *
+ * CONVENTIONS.  All device pointers are owned by the caller and must stay
+ * valid until the stream work completes.  Every call that takes a stream
+ * enqueues asynchronous work on it (NULL = legacy default stream) and
+ * returns without synchronising; an error inside a kernel is reported by
+ * lfbp_sync_status.  Return values: LFBP_OK (0) or a negative LFBP_ERR_*;
+ * lfbp_last_error() gives a message for the calling thread's last failure.
+ * Plans are immutable after creation and may be shared between threads;
+ * calls on the same plan from several threads are safe when they use
+ * different output buffers.
+ */
+#ifndef LFBP_H
+#define LFBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LFBP_F32 = 0, LFBP_F16 = 1 } lfbp_dtype;
+typedef enum { LFBP_MAP_TRANSPOSE = 0, LFBP_MAP_PAPER_WINDOW = 1 } lfbp_mode;
+
+#define LFBP_OK 0
+#define LFBP_ERR_BAD_SHAPE (-1) /* even or non-positive N or K, too large a shape */
+#define LFBP_ERR_NULL (-2)      /* a required pointer is NULL                     */
+#define LFBP_ERR_ALIGN (-3)     /* a buffer does not start on a 16-byte boundary  */
+#define LFBP_ERR_ALIAS (-4)     /* input and output buffers overlap               */
+#define LFBP_ERR_DTYPE (-5)     /* unknown dtype or plans of mixed element size   */
+#define LFBP_ERR_CUDA (-6)      /* a CUDA runtime call failed                     */
+#define LFBP_ERR_TIMEOUT (-7)   /* a bounded in-kernel wait gave up               */
+#define LFBP_ERR_NOMEM (-8)     /* host or device allocation failed               */
+#define LFBP_ERR_INVALID (-9)   /* other invalid argument                         */
+
+typedef struct lfbp_plan_s* lfbp_plan; /* opaque; owned by the library */
+
+/*
+ * Square elementary cell (Nx = Ny = Nnum, Ks = Kt = Kz[z]).  Nnum and every
+ * Kz[z] must be odd and >= 1 (Sec. 3: n_x, n_y odd; odd n_s makes Eq. (8) a
+ * flip, see lfbp_plan_create2).  Kz is copied.  Nz = 0 makes an empty plan.
+ * On success *out receives a plan to be released with lfbp_plan_destroy.
+ */
+int lfbp_plan_create(lfbp_plan* out, int Nnum, int Nz, const int* Kz, lfbp_dtype dt,
+                     lfbp_mode mode);
+
+/*
+ * General cell (Sec. 3: "separate treatment of x and y ... allows
+ * non-symmetric cases with n_x != n_y", e.g. hexagonal MLAs): Nx x Ny source
+ * positions, per-depth cut-outs of Ks[z] x Kt[z] pixels.  All odd and >= 1;
+ * Nx, Ny <= 4095 and Ks, Kt <= 65535.  Even cut-out sizes are rejected
+ * (LFBP_ERR_BAD_SHAPE): Eq. (8) then drops one pixel row and the map is not
+ * a permutation.
+ */
+int lfbp_plan_create2(lfbp_plan* out, int Nx, int Ny, int Nz, const int* Ks, const int* Kt,
+                      lfbp_dtype dt, lfbp_mode mode);
+
+void lfbp_plan_destroy(lfbp_plan p);
+
+/* Total elements of one array, sum_z Nx*Ny*Ks[z]*Kt[z]; 0 for a NULL plan. */
+size_t lfbp_plan_elems(lfbp_plan p);
+/* First element of depth z (0 <= z <= Nz; z = Nz gives lfbp_plan_elems). */
+size_t lfbp_plan_depth_offset(lfbp_plan p, int z);
+/* Bytes per element of the plan's dtype (4 or 2). */
+int lfbp_plan_esize(lfbp_plan p);
+
+/*
+ * H -> H' with one kernel launch per depth (Sec. 3: the z-planes are
+ * independent).  dH, dHp: device buffers of lfbp_plan_elems(p) elements,
+ * 16-byte aligned, not overlapping (in-place is rejected with
+ * LFBP_ERR_ALIAS).  The plan's mode selects the full transpose or the
+ * paper-window variant.
+ */
+int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_stream);
+
+/*
+ * H -> H' for n arrays at once, in one persistent launch over a ragged work
+ * list of all depths of all arrays (mixed fp32 / fp16 plans allowed).  The
+ * work list, launch shape and a CUDA graph of the launch are built on the
+ * first call for a given list of plans and reused while the same plans (by
+ * handle) come back; pointers may change between calls.  The first call for
+ * a new list of plans allocates device memory and must not be made during
+ * stream capture.  plans[i], dH[i], dHp[i] as for lfbp_backproject_array;
+ * no output may overlap any input or other output.
+ */
+int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
+                             void* const* dHp, void* cuda_stream);
+
+/*
+ * Adjoint of the plan's map, applied to a gradient with respect to H'
+ * (dHp_grad) to give the gradient with respect to H (dH_grad).  For
+ * LFBP_MAP_TRANSPOSE the map is its own inverse and its own adjoint
+ * (Sec. 3, reversibility), so this is the same gather; for
+ * LFBP_MAP_PAPER_WINDOW it gathers the unmasked entries and writes zeros
+ * where the forward map dropped an entry.  Buffers as for
+ * lfbp_backproject_array.
+ */
+int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_stream);
+
+/*
+ * Synchronise the stream, then return and clear the library's device status
+ * word for the current device: LFBP_OK, or LFBP_ERR_TIMEOUT when a bounded
+ * in-kernel wait gave up (the output is then incomplete), or LFBP_ERR_CUDA
+ * when the synchronisation itself failed.
+ */
+int lfbp_sync_status(void* cuda_stream);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* lfbp_last_error(void);
+
+/* Library version string. */
+const char* lfbp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LFBP_H */

@@ -1,0 +1,180 @@
+// Host emulation of the lfbp tile code -- TEST INFRASTRUCTURE.
+//
+// Compiles the device tile functions of lfbp_device.cuh as ordinary C++ with
+// checked stand-ins for the GPU primitives, and runs every tile of a plan
+// sequentially (producer lanes 0..31, then consumer threads) so that the
+// CPU tests can check, before any GPU run, that
+//   * every bulk copy is 16-byte aligned, a multiple of 16 bytes, reads only
+//     inside the input array and writes only inside its stage,
+//   * the bytes announced with expect_tx equal the bytes copied,
+//   * every shared-memory read is inside the stage and every global store is
+//     inside the output array and aligned,
+//   * every output byte is written exactly once,
+// and compare the result with the CPU oracle.
+#include <cstddef>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#define __device__
+#define __host__
+#define __forceinline__ inline
+#define LFBP_HOST_EMULATION 1
+
+struct uint4 {
+  unsigned x, y, z, w;
+};
+
+namespace {
+const unsigned char* g_in = nullptr;
+size_t g_in_bytes = 0;
+unsigned char* g_out = nullptr;
+size_t g_out_bytes = 0;
+unsigned char* g_counts = nullptr;
+unsigned char* g_stage = nullptr;
+size_t g_stage_bytes = 0;
+unsigned long long g_expect = 0, g_copied = 0, g_arrive = 0;
+long g_errors = 0;
+char g_msg[512] = {0};
+
+void err(const char* what, long long a, long long b) {
+  if (g_errors++ == 0) std::snprintf(g_msg, sizeof(g_msg), "%s (%lld, %lld)", what, a, b);
+}
+}  // namespace
+
+static inline uint32_t __umulhi(uint32_t a, uint32_t b) {
+  return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+}
+static inline void __syncwarp() {}
+static inline unsigned __ldg(const unsigned* p) {
+  const unsigned char* c = (const unsigned char*)p;
+  if (c < g_in || c + 4 > g_in + g_in_bytes || ((uintptr_t)c & 3)) err("ldg32 out of range", c - g_in, 0);
+  return *p;
+}
+static inline unsigned short __ldg(const unsigned short* p) {
+  const unsigned char* c = (const unsigned char*)p;
+  if (c < g_in || c + 2 > g_in + g_in_bytes || ((uintptr_t)c & 1)) err("ldg16 out of range", c - g_in, 0);
+  return *p;
+}
+namespace lfbp {
+static inline uint32_t smem_addr(const void* p) {
+  const unsigned char* c = (const unsigned char*)p;
+  if (c < g_stage || c > g_stage + g_stage_bytes) err("smem_addr outside stage", c - g_stage, 0);
+  return (uint32_t)(c - g_stage);
+}
+static inline void fence_proxy_async_smem() {}
+static inline void mbar_expect_tx(uint32_t, uint32_t bytes) { g_expect += bytes; }
+static inline void mbar_arrive(uint32_t) { ++g_arrive; }
+static inline void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t) {
+  const unsigned char* s = (const unsigned char*)src;
+  if (bytes == 0 || (bytes & 15)) err("bulk size not a positive multiple of 16", bytes, 0);
+  if (((uintptr_t)s & 15) || (dst & 15)) err("bulk copy misaligned", (uintptr_t)s & 15, dst & 15);
+  if (s < g_in || s + bytes > g_in + g_in_bytes) err("bulk copy reads outside input", s - g_in, bytes);
+  if ((size_t)dst + bytes > g_stage_bytes) err("bulk copy writes outside stage", dst, bytes);
+  if (g_errors == 0) std::memcpy(g_stage + dst, s, bytes);
+  g_copied += bytes;
+}
+static inline void emu_smem_check(long long byte_off) {
+  if (byte_off < 0 || (size_t)byte_off >= g_stage_bytes) err("smem read outside stage", byte_off, 0);
+}
+static inline void count_store(const unsigned char* p, size_t n) {
+  if (p < g_out || p + n > g_out + g_out_bytes) {
+    err("store outside output", p - g_out, (long long)n);
+    return;
+  }
+  for (size_t i = 0; i < n; ++i) g_counts[(p - g_out) + i]++;
+}
+static inline void st_global_16(void* p, uint4 w) {
+  if ((uintptr_t)p & 15) err("16-byte store misaligned", (uintptr_t)p & 15, 0);
+  count_store((unsigned char*)p, 16);
+  if (g_errors == 0) std::memcpy(p, &w, 16);
+}
+template <class T>
+static inline void st_global_elem(T* p, T v) {
+  if ((uintptr_t)p & (sizeof(T) - 1)) err("element store misaligned", (uintptr_t)p, 0);
+  count_store((unsigned char*)p, sizeof(T));
+  if (g_errors == 0) *p = v;
+}
+}  // namespace lfbp
+#define LFBP_SMEM_CHECK(idx) emu_smem_check((long long)(idx) * ES)
+
+#include "lfbp_device.cuh"
+
+using namespace lfbp;
+
+extern "C" const char* emu_message() { return g_msg; }
+
+// Runs every tile of every depth of one array through the tile code.
+// Returns the number of violations (0 = clean); stats[0] = tiles, stats[1] =
+// bytes copied by bulk copies, stats[2] = max tile bytes.
+extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned char* counts,
+                        int Nx, int Ny, int Nz, const int* Ks, const int* Kt, int es, int mode,
+                        int target, int nthr, unsigned long long* stats) {
+  g_errors = 0;
+  g_msg[0] = 0;
+  size_t total = 0;
+  std::vector<size_t> off(Nz + 1, 0);
+  for (int z = 0; z < Nz; ++z) {
+    off[z + 1] = off[z] + (size_t)Nx * Ny * Ks[z] * Kt[z];
+  }
+  total = off[Nz] * es;
+  g_in = in;
+  g_in_bytes = total;
+  g_out = out;
+  g_out_bytes = total;
+  g_counts = counts;
+  const unsigned char* safe_end = in + (total & ~(size_t)15);
+  unsigned long long tiles = 0, copied = 0, maxb = 0;
+  for (int z = 0; z < Nz && g_errors == 0; ++z) {
+    DepthTiling d = tile_depth(Ny, Ks[z], Kt[z], es, target);
+    if ((unsigned long long)d.max_tile_bytes > maxb) maxb = d.max_tile_bytes;
+    JobDesc jd;
+    jd.off_bytes = off[z] * es;
+    jd.arr = 0;
+    jd.Nx = Nx;
+    jd.Ny = Ny;
+    jd.Ks = Ks[z];
+    jd.Kt = Kt[z];
+    jd.es = es;
+    jd.mode = mode;
+    jd.pad = 0;
+    std::vector<unsigned char> stage((size_t)d.max_tile_bytes + 64);
+    for (int ub = 0; ub < d.nU; ++ub)
+      for (int p = 0; p < Nx; ++p)
+        for (int vb = 0; vb < d.nV; ++vb) {
+          TileDesc td;
+          td.job = 0;
+          td.p = (unsigned short)p;
+          td.u0 = (unsigned short)(ub * d.J);
+          td.v0 = (unsigned short)(vb * d.V);
+          td.nrows = (unsigned short)lfbp_min(d.J, Ks[z] - ub * d.J);
+          td.ncols = (unsigned short)lfbp_min(d.V, Kt[z] - vb * d.V);
+          td.pad = 0;
+          const unsigned tile_bytes = td.nrows * Ny * slot_bytes(td.ncols, es);
+          if ((int)tile_bytes > d.max_tile_bytes) err("tile larger than its depth's maximum", tile_bytes, d.max_tile_bytes);
+          std::memset(stage.data(), 0xA5, stage.size());
+          g_stage = stage.data();
+          g_stage_bytes = tile_bytes;
+          g_expect = g_copied = g_arrive = 0;
+          TileInfo ti;
+          const unsigned char* in_depth = in + jd.off_bytes;
+          unsigned char* out_depth = out + jd.off_bytes;
+          make_tile_info(ti, 0, td, jd, in_depth, out_depth);
+          for (int lane = 0; lane < 32; ++lane)
+            issue_tile_loads(td, jd, in_depth, safe_end, stage.data(), 0, lane);
+          if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
+          if (g_arrive != 1) err("producer arrivals != 1", g_arrive, 0);
+          for (int t = 0; t < nthr; ++t) gather_store_dispatch(ti, stage.data(), t, nthr);
+          ++tiles;
+          copied += g_copied;
+          if (g_errors) break;
+        }
+  }
+  if (stats) {
+    stats[0] = tiles;
+    stats[1] = copied;
+    stats[2] = maxb;
+  }
+  return g_errors;
+}

@@ -1,0 +1,115 @@
+"""The C-ABI library loads, exports what include/lfbp.h declares, and
+validates its arguments on the host (CPU only: no call here launches work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lfbp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2003_09133_gb300 import _lib
+    return _lib.load(build_if_missing=True)
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lfbp_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _declared()
+    assert "lfbp_backproject_array" in names and "lfbp_adjoint" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_2003_09133_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == _declared()
+
+
+def _plan(lib, Nx, Ny, Ks, Kt, dt=0, mode=0):
+    h = ctypes.c_void_p()
+    n = len(Ks)
+    ks = (ctypes.c_int * max(1, n))(*Ks)
+    kt = (ctypes.c_int * max(1, n))(*Kt)
+    rc = lib.lfbp_plan_create2(ctypes.byref(h), Nx, Ny, n, ctypes.cast(ks, ctypes.c_void_p),
+                               ctypes.cast(kt, ctypes.c_void_p), dt, mode)
+    return rc, h
+
+
+@pytest.mark.parametrize("args,code", [
+    ((4, 5, [15], [15]), -1),      # even Nx (Sec. 3 requires odd n_x)
+    ((5, 6, [15], [15]), -1),      # even Ny
+    ((5, 5, [14], [15]), -1),      # even Ks
+    ((5, 5, [15], [0]), -1),       # Kt < 1
+    ((0, 5, [15], [15]), -1),
+    ((1025, 5, [15], [15]), -1),   # beyond the supported cell size
+    ((5, 5, [15], [15], 7), -5),   # unknown dtype
+    ((5, 5, [15], [15], 0, 3), -9),  # unknown mode
+])
+def test_plan_validation(lib, args, code):
+    rc, h = _plan(lib, *args)
+    assert rc == code
+    assert not h.value
+    assert lib.lfbp_last_error()
+
+
+def test_plan_sizes_and_offsets(lib):
+    Ks, Kt = [15, 5, 25], [9, 3, 27]
+    rc, h = _plan(lib, 5, 3, Ks, Kt, 1)
+    assert rc == 0
+    sizes = [5 * 3 * a * b for a, b in zip(Ks, Kt)]
+    assert lib.lfbp_plan_elems(h) == sum(sizes)
+    assert lib.lfbp_plan_esize(h) == 2
+    acc = 0
+    for z in range(3):
+        assert lib.lfbp_plan_depth_offset(h, z) == acc
+        acc += sizes[z]
+    assert lib.lfbp_plan_depth_offset(h, 3) == acc
+    lib.lfbp_plan_destroy(h)
+
+
+def test_empty_plan(lib):
+    rc, h = _plan(lib, 5, 5, [], [])
+    assert rc == 0 and lib.lfbp_plan_elems(h) == 0
+    lib.lfbp_plan_destroy(h)
+
+
+def test_buffer_validation_before_any_launch(lib):
+    rc, h = _plan(lib, 5, 5, [15], [15])
+    assert rc == 0
+    nbytes = 5 * 5 * 15 * 15 * 4
+    A, B = 0x10000000, 0x20000000   # never dereferenced: validation fails first
+    assert lib.lfbp_backproject_array(None, A, B, None) == -2
+    assert lib.lfbp_backproject_array(h, None, B, None) == -2
+    assert lib.lfbp_backproject_array(h, A + 4, B, None) == -3
+    assert lib.lfbp_backproject_array(h, A, B + 8, None) == -3
+    assert lib.lfbp_backproject_array(h, A, A, None) == -4
+    assert lib.lfbp_backproject_array(h, A, A + ((nbytes - 16) & ~15), None) == -4
+    assert lib.lfbp_adjoint(h, A, A + 16, None) == -4
+    assert b"overlap" in lib.lfbp_last_error()
+    arr = (ctypes.c_void_p * 1)(h)
+    ins = (ctypes.c_void_p * 1)(A)
+    outs = (ctypes.c_void_p * 1)(A + 32)
+    P = ctypes.c_void_p
+    assert lib.lfbp_backproject_batched(1, ctypes.cast(arr, P), ctypes.cast(ins, P),
+                                        ctypes.cast(outs, P), None) == -4
+    assert lib.lfbp_backproject_batched(65, ctypes.cast(arr, P), ctypes.cast(ins, P),
+                                        ctypes.cast(outs, P), None) == -9
+    assert lib.lfbp_backproject_batched(0, None, None, None, None) == 0
+    lib.lfbp_plan_destroy(h)
+
+
+def test_python_binding_refuses_without_library(monkeypatch, tmp_path):
+    from paper_2003_09133_gb300 import _lib, build
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()

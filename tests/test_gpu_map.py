@@ -1,0 +1,208 @@
+"""GPU parity of H -> H' against the CPU oracle, bit for bit (needs a GB300).
+
+Every comparison is on raw bit patterns: the map only moves values, so fp32
+and fp16 results must equal the oracle's exactly, NaN payloads included.
+"""
+import numpy as np
+import pytest
+import torch
+
+import lfgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lf():
+    import paper_2003_09133_gb300 as m
+    m.load(build_if_missing=True)
+    torch.cuda.set_device(0)
+    return m
+
+
+def _bits(a: np.ndarray):
+    return a.view(np.uint32 if a.itemsize == 4 else np.uint16)
+
+
+def _assert_same_bits(got: torch.Tensor, want: np.ndarray, what=""):
+    g = got.cpu().numpy()
+    gb, wb = _bits(g), _bits(want)
+    if not np.array_equal(gb, wb):
+        bad = np.flatnonzero(gb != wb)
+        raise AssertionError(f"{what}: {bad.size} of {gb.size} elements differ, first at {bad[:8]}")
+
+
+def _random_bits(n, dtype, seed, device="cuda"):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    if dtype == torch.float32:
+        x = torch.randint(-2 ** 31, 2 ** 31 - 1, (n,), generator=g, dtype=torch.int64)
+        return x.to(torch.int32).view(torch.float32).to(device)
+    x = torch.randint(-2 ** 15, 2 ** 15 - 1, (n,), generator=g, dtype=torch.int32)
+    return x.to(torch.int16).view(torch.float16).to(device)
+
+
+SHAPES = [
+    (5, 5, [15, 15, 15], [15, 15, 15]),
+    (3, 5, [9, 3, 15], [15, 5, 5]),
+    (1, 1, [5, 1, 9], [7, 1, 3]),
+    (7, 3, [21, 7], [9, 33]),
+    (19, 19, [95, 57, 19], [95, 57, 19]),
+    (11, 11, [99, 33, 11], [99, 33, 11]),
+    (9, 13, [27, 3, 1], [39, 13, 5]),
+    (51, 51, [153], [153]),           # rows larger than one stage: column-split tiles
+    (31, 31, [249], [249]),
+    (95, 55, [181], [181]),           # the non-square R29 cell shape (Sec. 4)
+    (11, 11, [89], [89]),             # K not a multiple of N (Table 1 shapes)
+]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}")
+def test_random_bits_plain_batched_adjoint(lf, shape, dtype):
+    Nx, Ny, Ks, Kt = shape
+    plan = lf.Plan(Nx, Ny, Ks, Kt, dtype)
+    H = _random_bits(plan.elems, dtype, 11)
+    Hn = H.cpu().numpy()
+    want = oracle.transpose(Hn, Nx, Ny, Ks, Kt)
+    _assert_same_bits(lf.backproject_array(plan, H), want, "plain")
+    _assert_same_bits(lf.backproject_batched([plan], [H])[0], want, "batched")
+    _assert_same_bits(lf.adjoint(plan, H), oracle.transpose_adjoint(Hn, Nx, Ny, Ks, Kt), "adjoint")
+    lf.sync_status()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("shape", SHAPES[:7], ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}")
+def test_paper_window_mode(lf, shape, dtype):
+    Nx, Ny, Ks, Kt = shape
+    plan = lf.Plan(Nx, Ny, Ks, Kt, dtype, mode=lf.MAP_PAPER_WINDOW)
+    H = _random_bits(plan.elems, dtype, 12)
+    Hn = H.cpu().numpy()
+    _assert_same_bits(lf.backproject_array(plan, H), oracle.paper_window(Hn, Nx, Ny, Ks, Kt), "plain")
+    _assert_same_bits(lf.backproject_batched([plan], [H])[0],
+                      oracle.paper_window(Hn, Nx, Ny, Ks, Kt), "batched")
+    keep = oracle.paper_window(np.ones(plan.elems), Nx, Ny, Ks, Kt) != 0
+    Y = Hn.copy()
+    Y[~keep] = 0
+    _assert_same_bits(lf.adjoint(plan, H), oracle.transpose_adjoint(Y, Nx, Ny, Ks, Kt), "adjoint")
+    lf.sync_status()
+
+
+def test_guard_bands_untouched(lf):
+    """Canaries around the output catch any write outside it."""
+    Nx, Ny, Ks, Kt = 7, 5, [21, 9, 35], [15, 5, 45]
+    for dtype in (torch.float32, torch.float16):
+        plan = lf.Plan(Nx, Ny, Ks, Kt, dtype)
+        n = plan.elems
+        H = _random_bits(n, dtype, 13)
+        pad = 64 // plan.esize  # 64 bytes on each side, keeps 16-byte alignment
+        buf = torch.full((n + 2 * pad,), float("nan"), dtype=dtype, device="cuda")
+        canary = buf.clone()
+        out = buf[pad:pad + n]
+        lf.backproject_array(plan, H, out)
+        lf.backproject_batched([plan], [H], [out])
+        torch.cuda.synchronize()
+        assert torch.equal(buf[:pad].view(torch.int16 if dtype == torch.float16 else torch.int32),
+                           canary[:pad].view(torch.int16 if dtype == torch.float16 else torch.int32))
+        assert torch.equal(buf[pad + n:].view(torch.int16 if dtype == torch.float16 else torch.int32),
+                           canary[pad + n:].view(torch.int16 if dtype == torch.float16 else torch.int32))
+        _assert_same_bits(out, oracle.transpose(H.cpu().numpy(), Nx, Ny, Ks, Kt), "guarded")
+
+
+def test_special_bit_patterns(lf):
+    Nx, Ny, Ks, Kt = 5, 5, [15], [15]
+    plan = lf.Plan(Nx, Ny, Ks, Kt, torch.float32)
+    bits = np.random.default_rng(14).integers(0, 2 ** 32, plan.elems, dtype=np.uint64).astype(np.uint32)
+    bits[:8] = [0x7fc00001, 0x7f800001, 0xffc12345, 0x80000000, 0x7f800000, 0xff800000,
+                0x00000001, 0x807fffff]
+    H = torch.from_numpy(bits.view(np.float32).copy()).cuda()
+    want = oracle.transpose(bits.view(np.float32), Nx, Ny, Ks, Kt)
+    _assert_same_bits(lf.backproject_array(plan, H), want, "plain")
+    _assert_same_bits(lf.backproject_batched([plan], [H])[0], want, "batched")
+
+
+def test_batched_mixed_dtypes_and_pointer_changes(lf):
+    """One persistent launch over fp32 and fp16 arrays; replay with new buffers."""
+    shapes = [(5, 5, [15, 25], [15, 25], torch.float32), (3, 7, [9, 27, 3], [21, 7, 35], torch.float16),
+              (19, 19, [57], [57], torch.float16), (11, 11, [33, 55], [33, 55], torch.float32)]
+    plans = [lf.Plan(a, b, c, d, t) for a, b, c, d, t in shapes]
+    for rep in range(3):
+        Hs = [_random_bits(p.elems, p.dtype, 20 + rep * 10 + i) for i, p in enumerate(plans)]
+        outs = lf.backproject_batched(plans, Hs)
+        for p, H, o in zip(plans, Hs, outs):
+            _assert_same_bits(o, oracle.transpose(H.cpu().numpy(), p.Nx, p.Ny, p.Ks, p.Kt), f"rep{rep}")
+    lf.sync_status()
+
+
+def test_tiny_workload(lf):
+    spec = lfgen.config_specs("tiny")[0]
+    H = lfgen.generate(spec).cuda()
+    want = oracle.transpose(H.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt)
+    for dtype in (torch.float32, torch.float16):
+        Hd = H.to(dtype)
+        wd = want.astype(np.float32).astype(np.float16) if dtype == torch.float16 else want
+        plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, dtype)
+        _assert_same_bits(lf.backproject_array(plan, Hd), wd, "plain")
+        _assert_same_bits(lf.backproject_batched([plan], [Hd])[0], wd, "batched")
+    pw = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32, mode=lf.MAP_PAPER_WINDOW)
+    _assert_same_bits(lf.backproject_array(pw, H),
+                      oracle.paper_window(H.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt), "window")
+
+
+def test_autograd_backward_is_the_adjoint(lf):
+    spec = lfgen.config_specs("tiny")[0]
+    plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32)
+    H = lfgen.generate(spec).cuda().requires_grad_(True)
+    Hp = lf.backprojection_array(H, plan)
+    w = torch.randn_like(Hp)
+    (Hp * w).sum().backward()
+    want = oracle.transpose_adjoint(w.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt)
+    _assert_same_bits(H.grad, want, "grad")
+
+
+def test_sync_status_ok(lf):
+    lf.sync_status()
+
+
+def _full_workload(lf, name, dtype=None, forms=("batched", "plain")):
+    specs = lfgen.config_specs(name)
+    plans, Hs = [], []
+    for s in specs:
+        dt = dtype or s.torch_dtype
+        plans.append(lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, dt))
+        Hs.append(lfgen.generate(s, device="cuda").to(dt))
+    outs = {}
+    if "batched" in forms:
+        outs["batched"] = lf.backproject_batched(plans, Hs)
+    if "plain" in forms:
+        outs["plain"] = [lf.backproject_array(p, h) for p, h in zip(plans, Hs)]
+    lf.sync_status()
+    for i, (s, H) in enumerate(zip(specs, Hs)):
+        want = oracle.transpose(H.cpu().numpy(), s.Nx, s.Ny, s.Ks, s.Kt)
+        for form, o in outs.items():
+            _assert_same_bits(o[i], want, f"{name}[{i}] {form}")
+        for form in outs:
+            outs[form][i] = None
+        Hs[i] = None
+        del want
+        torch.cuda.empty_cache()
+
+
+def test_mid_workload_full(lf):
+    _full_workload(lf, "mid")
+
+
+def test_highres_workload_full_fp32(lf):
+    _full_workload(lf, "highres")
+
+
+def test_highres_workload_full_fp16(lf):
+    _full_workload(lf, "highres", dtype=torch.float16)
+
+
+def test_ragged_workload_full(lf):
+    _full_workload(lf, "ragged")
+
+
+def test_autograd_workload_map(lf):
+    _full_workload(lf, "autograd")

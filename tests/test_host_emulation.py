@@ -1,0 +1,121 @@
+"""The kernel's tile code, run on the CPU with every memory access checked.
+
+tests/host_emu/lfbp_emu.cpp compiles the device tile functions of
+lfbp_device.cuh as host C++ with checked stand-ins for TMA bulk copies,
+mbarrier transactions and global stores.  These CPU tests show, before any
+GPU run, that each launch shape keeps all copies aligned and inside their
+buffers, writes every output byte exactly once, and reproduces the oracle.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, "host_emu", "lfbp_emu.cpp")
+
+
+@pytest.fixture(scope="module")
+def emu(tmp_path_factory):
+    so = str(tmp_path_factory.mktemp("emu") / "libemu.so")
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-w", "-shared", "-fPIC",
+                           "-I", os.path.join(ROOT, "paper_2003_09133_gb300", "csrc"),
+                           "-I", os.path.join(ROOT, "include"), "-o", so, SRC])
+    lib = ctypes.CDLL(so)
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.emu_run.argtypes = [P, P, P, I, I, I, P, P, I, I, I, I, P]
+    lib.emu_run.restype = ctypes.c_long
+    lib.emu_message.restype = ctypes.c_char_p
+    return lib
+
+
+def _aligned(nbytes, offset=0):
+    """uint8 view of nbytes starting `offset` bytes after a 64-byte boundary."""
+    raw = np.zeros(nbytes + 128, dtype=np.uint8)
+    base = (-raw.ctypes.data) % 64 + offset
+    return raw[base:base + nbytes]
+
+
+def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=256):
+    es = H.itemsize
+    nbytes = H.nbytes
+    hin = _aligned(nbytes)
+    hin[:] = H.view(np.uint8)
+    out = _aligned(nbytes)
+    out[:] = 0x5A
+    counts = np.zeros(nbytes, dtype=np.uint8)
+    ks = np.asarray(Ks, dtype=np.int32)
+    kt = np.asarray(Kt, dtype=np.int32)
+    stats = np.zeros(3, dtype=np.uint64)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    nerr = emu.emu_run(p(hin), p(out), p(counts), Nx, Ny, len(ks), p(ks), p(kt), es, mode,
+                       target, nthr, p(stats))
+    assert nerr == 0, emu.emu_message().decode()
+    np.testing.assert_array_equal(counts, 1)
+    return out.view(H.dtype), stats
+
+
+def _random_bits(n, dtype, seed):
+    rng = np.random.default_rng(seed)
+    if dtype == np.float32:
+        return rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32).view(np.float32)
+    return rng.integers(0, 2 ** 16, n, dtype=np.uint32).astype(np.uint16).view(np.float16)
+
+
+SHAPES = [
+    # Nx, Ny, Ks, Kt, tile target (small targets force partial tiles and column splits)
+    (5, 5, [15, 15, 15], [15, 15, 15], 32768),
+    (5, 5, [15, 5, 25], [15, 5, 25], 600),
+    (3, 5, [9, 3, 15], [15, 5, 5], 32768),
+    (1, 1, [5, 1, 9], [7, 1, 3], 32768),
+    (7, 3, [21, 7], [9, 33], 1500),
+    (19, 19, [95, 57], [95, 57], 32768),
+    (19, 19, [133], [133], 4096),
+    (11, 11, [99, 33], [99, 33], 20000),
+    (15, 15, [45, 75], [45, 75], 32768),
+    (9, 13, [27, 3, 1], [39, 13, 5], 2048),
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}_t{s[4]}")
+def test_tiles_transpose(emu, shape, dtype):
+    Nx, Ny, Ks, Kt, target = shape
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    H = _random_bits(n, dtype, 1)
+    got, stats = _run(emu, H, Nx, Ny, Ks, Kt, 0, target)
+    want = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+@pytest.mark.parametrize("shape", SHAPES[:6], ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}_t{s[4]}")
+def test_tiles_paper_window_and_adjoint(emu, shape, dtype):
+    Nx, Ny, Ks, Kt, target = shape
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    H = _random_bits(n, dtype, 2)
+    got, _ = _run(emu, H, Nx, Ny, Ks, Kt, 1, target)
+    want = oracle.paper_window(H, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+    # adjoint of the windowed map: keep only the entries the forward map writes
+    keep = oracle.paper_window(np.ones(n), Nx, Ny, Ks, Kt) != 0
+    Y = H.copy()
+    Y[~keep] = 0
+    got2, _ = _run(emu, H, Nx, Ny, Ks, Kt, 2, target)
+    want2 = oracle.transpose_adjoint(Y, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(got2.view(np.uint8), want2.view(np.uint8))
+
+
+def test_thread_count_does_not_matter(emu):
+    Nx, Ny, Ks, Kt = 5, 3, [15, 9], [9, 21]
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    H = _random_bits(n, np.float32, 3)
+    want = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    for nthr in (1, 32, 96, 256, 288):
+        got, _ = _run(emu, H, Nx, Ny, Ks, Kt, 0, 2048, nthr)
+        np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
