@@ -78,7 +78,7 @@ int lfbp_plan_create(lfbp_plan* out, int Nnum, int Nz, const int* Kz, lfbp_dtype
  * General cell (Sec. 3: "separate treatment of x and y ... allows
  * non-symmetric cases with n_x != n_y", e.g. hexagonal MLAs): Nx x Ny source
  * positions, per-depth cut-outs of Ks[z] x Kt[z] pixels.  All odd and >= 1;
- * Nx, Ny <= 4095 and Ks, Kt <= 65535.  Even cut-out sizes are rejected
+ * Nx, Ny <= 1023 and Ks, Kt <= 16383.  Even cut-out sizes are rejected
  * (LFBP_ERR_BAD_SHAPE): Eq. (8) then drops one pixel row and the map is not
  * a permutation.
  */
@@ -104,6 +104,24 @@ int lfbp_plan_esize(lfbp_plan p);
 int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_stream);
 
 /*
+ * H -> H' from host memory to host memory.  The host->device copy of one
+ * chunk of depths, the map of the previous chunk (one launch per depth) and
+ * the device->host copy of the chunk before overlap on two library-owned
+ * helper streams and the caller's stream (Sec. 3: the z-planes are
+ * independent, so each chunk is mapped as soon as it has arrived).
+ * H_host, Hp_host: host buffers of lfbp_plan_elems(p) elements, not
+ * overlapping; page-locked (pinned) memory is needed for the copies to run
+ * asynchronously and overlap.  dH_work, dHp_work: caller-owned device
+ * buffers of the same size, 16-byte aligned, not overlapping (they hold H
+ * and H' afterwards).  All work is ordered after earlier work on cuda_stream,
+ * and later work on cuda_stream waits for all of it (including the last
+ * copy to Hp_host); the call itself does not block.  The first call on a
+ * device creates the helper streams.
+ */
+int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH_work,
+                                void* dHp_work, void* cuda_stream);
+
+/*
  * H -> H' for n arrays at once, in one persistent launch over a ragged work
  * list of all depths of all arrays (mixed fp32 / fp16 plans allowed).  The
  * work list, launch shape and a CUDA graph of the launch are built on the
@@ -126,6 +144,39 @@ int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* d
  * lfbp_backproject_array.
  */
 int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_stream);
+
+/*
+ * Backprojection of a sensor image through H' (the H' f inside the
+ * Richardson-Lucy update, Eq. 2) on a finite Wx x Wy sensor whose voxel grid
+ * coincides laterally with the pixel grid; the cell position of a point P is
+ * P mod N and points outside the sensor contribute nothing:
+ *   g[z][X][Y] = sum_{u,v} f[X-u+c_s][Y-v+c_t] * H'_z[(X-u+c_s) mod Nx][(Y-v+c_t) mod Ny][u][v]
+ * dHp: H' in the plan's layout (LFBP_F32 plans only); df: [Wx][Wy] fp32;
+ * dg: [Nz][Wx][Wy] fp32 output.  Sums run in fp32 in a fixed order
+ * (deterministic).  Requires Kt <= 3072 (LFBP_ERR_BAD_SHAPE otherwise).
+ */
+int lfbp_backproject_volume(lfbp_plan p, const void* dHp, const float* df, int Wx, int Wy,
+                            float* dg, void* cuda_stream);
+
+/*
+ * Forward projection f = H g (Eq. 1): every voxel adds its cut-out of H,
+ * scaled by its value, onto the sensor (cut-out centred on the voxel):
+ *   f[S] = sum_z sum_{s,t} g[z][S-s+c_s][.] * H_z[(S-s+c_s) mod Nx][..][s][t]
+ * dH: H (LFBP_F32 plans only); dg: [Nz][Wx][Wy]; df: [Wx][Wy] output.
+ * Depths are accumulated in order z = 0..Nz-1 (deterministic).
+ */
+int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, int Wy, float* df,
+                         void* cuda_stream);
+
+/*
+ * Gradient of a loss L(g) with g = H' f (lfbp_backproject_volume) with respect
+ * to the entries of H', given dL/dg ([Nz][Wx][Wy] fp32):
+ *   dL/dH'_z[p][q][u][v] = sum over pixels S of cell (p, q) of f[S] * dL/dg_z[S + (u-c_s, v-c_t)]
+ * df: [Wx][Wy]; dHp_grad: output in the plan's layout (fp32).  Each output is
+ * one thread's fixed-order fp32 sum (deterministic, no atomics).
+ */
+int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
+                                 void* dHp_grad, void* cuda_stream);
 
 /*
  * Synchronise the stream, then return and clear the library's device status

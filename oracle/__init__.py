@@ -52,6 +52,7 @@ def _load():
             "oracle_backproject_f64": [P, I, I, I, P, P, P, I, I, P],
             "oracle_backproject_points": [P, I, I, I, P, P, P, I, I, L, P, P, I],
             "oracle_grad_hp_f64": [P, P, I, I, I, P, P, I, I, P, I],
+            "oracle_grad_hp_points": [P, P, I, I, I, P, P, I, I, L, P, P, I],
             "oracle_threads": [I],
         }.items():
             fn = getattr(_lib, name)
@@ -164,6 +165,21 @@ def grad_hp(f: np.ndarray, r: np.ndarray, Nx, Ny, Ks, Kt, nthreads: int = 0) -> 
     out = np.empty(n)
     _check(_load().oracle_grad_hp_f64(_ptr(f), _ptr(r), Nx, Ny, Nz, _ptr(ks), _ptr(kt),
                                       Wx, Wy, _ptr(out), nthreads), "oracle_grad_hp_f64")
+    return out
+
+
+def grad_hp_points(f: np.ndarray, r: np.ndarray, Nx, Ny, Ks, Kt, pts: np.ndarray,
+                   nthreads: int = 0) -> np.ndarray:
+    """``grad_hp`` at entries pts[i] = (z, p, q, u, v), each computed on its own."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    pts = np.ascontiguousarray(pts, dtype=np.int32)
+    Nz, Wx, Wy = r.shape
+    ks, kt = _ints(Ks), _ints(Kt)
+    out = np.empty(len(pts))
+    _check(_load().oracle_grad_hp_points(_ptr(f), _ptr(r), Nx, Ny, Nz, _ptr(ks), _ptr(kt), Wx, Wy,
+                                         len(pts), _ptr(pts), _ptr(out), nthreads),
+           "oracle_grad_hp_points")
     return out
 
 

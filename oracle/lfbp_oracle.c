@@ -30,6 +30,7 @@
  *   oracle_backproject_f64  g = H' f, the backprojection used in Eq. (2).
  *   oracle_backproject_points  the same, one voxel at a time.
  *   oracle_grad_hp_f64      d/dH' of sum (H' f - g_ref)^2 given the residual.
+ *   oracle_grad_hp_points   the same, one entry at a time.
  *
  * Parity: every function is pinned by the oracle's own CPU tests against
  * something other than itself (a dense measurement matrix built by pattern
@@ -396,5 +397,33 @@ int oracle_grad_hp_f64(const double* f, const double* r, int Nx, int Ny, int Nz,
             }
     }
     free(off);
+    return 0;
+}
+
+/* oracle_grad_hp_f64 at selected entries, one by one: pts holds npts
+ * 5-tuples (z, p, q, u, v); the residual r is [Nz][W_x][W_y]. */
+int oracle_grad_hp_points(const double* f, const double* r, int Nx, int Ny, int Nz,
+                          const int* Ks, const int* Kt, int Wx, int Wy, long npts,
+                          const int* pts, double* out, int nthreads) {
+    if (!f || !r || !pts || !out || !Ks || !Kt) return -1;
+    set_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+    for (long i = 0; i < npts; ++i) {
+        int z = pts[5 * i], p = pts[5 * i + 1], q = pts[5 * i + 2];
+        int u = pts[5 * i + 3], v = pts[5 * i + 4];
+        int cs = (Ks[z] - 1) / 2, ct = (Kt[z] - 1) / 2;
+        const double* rz = r + (size_t)z * Wx * Wy;
+        double acc = 0.0;
+        for (long Sx = p; Sx < Wx; Sx += Nx) {
+            long X = Sx + u - cs;
+            if (X < 0 || X >= Wx) continue;
+            for (long Sy = q; Sy < Wy; Sy += Ny) {
+                long Y = Sy + v - ct;
+                if (Y < 0 || Y >= Wy) continue;
+                acc += f[(size_t)Sx * Wy + Sy] * rz[(size_t)X * Wy + Y];
+            }
+        }
+        out[i] = acc;
+    }
     return 0;
 }

@@ -34,8 +34,12 @@ SIGNATURES = {
     "lfbp_plan_depth_offset": ([_P, _I], _S),
     "lfbp_plan_esize": ([_P], _I),
     "lfbp_backproject_array": ([_P, _P, _P, _P], _I),
+    "lfbp_backproject_array_host": ([_P, _P, _P, _P, _P, _P], _I),
     "lfbp_backproject_batched": ([_I, _P, _P, _P, _P], _I),
     "lfbp_adjoint": ([_P, _P, _P, _P], _I),
+    "lfbp_backproject_volume": ([_P, _P, _P, _I, _I, _P, _P], _I),
+    "lfbp_forward_project": ([_P, _P, _P, _I, _I, _P, _P], _I),
+    "lfbp_backproject_volume_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_sync_status": ([_P], _I),
     "lfbp_last_error": ([], ctypes.c_char_p),
     "lfbp_version": ([], ctypes.c_char_p),
@@ -170,6 +174,33 @@ def backproject_array(plan: Plan, H: torch.Tensor, out: torch.Tensor = None, str
     return out
 
 
+def backproject_array_host(plan: Plan, H_host: torch.Tensor, out_host: torch.Tensor = None,
+                           work=None, stream=None):
+    """H -> H' from host to host with copies overlapping the map (``lfbp_backproject_array_host``).
+
+    ``H_host`` should be a pinned CPU tensor; ``work`` = (dH, dHp) device tensors
+    of the plan's size (allocated on the current device when omitted).
+    """
+    if not isinstance(H_host, torch.Tensor) or H_host.is_cuda:
+        raise ValueError("H_host must be a CPU tensor")
+    if H_host.dtype != plan.dtype or H_host.numel() != plan.elems or not H_host.is_contiguous():
+        raise ValueError("H_host does not match the plan")
+    if out_host is None:
+        out_host = torch.empty_like(H_host, pin_memory=H_host.is_pinned())
+    if work is None:
+        work = (torch.empty(plan.elems, dtype=plan.dtype, device="cuda"),
+                torch.empty(plan.elems, dtype=plan.dtype, device="cuda"))
+    dH, dHp = work
+    _check_tensor(plan, dH, "dH_work")
+    _check_tensor(plan, dHp, "dHp_work")
+    with torch.cuda.device(dH.device):
+        _check(plan._lib.lfbp_backproject_array_host(plan.handle, H_host.data_ptr(),
+                                                     out_host.data_ptr(), dH.data_ptr(),
+                                                     dHp.data_ptr(), _stream_ptr(stream)),
+               "lfbp_backproject_array_host")
+    return out_host
+
+
 def backproject_batched(plans: Sequence[Plan], Hs: Sequence[torch.Tensor],
                         outs: Sequence[torch.Tensor] = None, stream=None):
     """H -> H' for several arrays in one persistent launch (``lfbp_backproject_batched``)."""
@@ -202,6 +233,63 @@ def adjoint(plan: Plan, dHp: torch.Tensor, out: torch.Tensor = None, stream=None
     with torch.cuda.device(dHp.device):
         _check(plan._lib.lfbp_adjoint(plan.handle, dHp.data_ptr(), out.data_ptr(),
                                       _stream_ptr(stream)), "lfbp_adjoint")
+    return out
+
+
+def _check_f32(t: torch.Tensor, shape, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+def backproject_volume(plan: Plan, Hp: torch.Tensor, f: torch.Tensor, out: torch.Tensor = None,
+                       stream=None):
+    """g = H' f on a finite sensor (``lfbp_backproject_volume``): f [Wx, Wy] -> g [Nz, Wx, Wy]."""
+    _check_tensor(plan, Hp, "Hp")
+    Wx, Wy = f.shape
+    _check_f32(f, (Wx, Wy), "f")
+    if out is None:
+        out = torch.empty((plan.Nz, Wx, Wy), dtype=torch.float32, device=f.device)
+    _check_f32(out, (plan.Nz, Wx, Wy), "out")
+    with torch.cuda.device(f.device):
+        _check(plan._lib.lfbp_backproject_volume(plan.handle, Hp.data_ptr(), f.data_ptr(), Wx, Wy,
+                                                 out.data_ptr(), _stream_ptr(stream)),
+               "lfbp_backproject_volume")
+    return out
+
+
+def forward_project(plan: Plan, H: torch.Tensor, g: torch.Tensor, out: torch.Tensor = None,
+                    stream=None):
+    """f = H g, Eq. (1) (``lfbp_forward_project``): g [Nz, Wx, Wy] -> f [Wx, Wy]."""
+    _check_tensor(plan, H, "H")
+    Nz, Wx, Wy = g.shape
+    _check_f32(g, (plan.Nz, Wx, Wy), "g")
+    if out is None:
+        out = torch.empty((Wx, Wy), dtype=torch.float32, device=g.device)
+    _check_f32(out, (Wx, Wy), "out")
+    with torch.cuda.device(g.device):
+        _check(plan._lib.lfbp_forward_project(plan.handle, H.data_ptr(), g.data_ptr(), Wx, Wy,
+                                              out.data_ptr(), _stream_ptr(stream)),
+               "lfbp_forward_project")
+    return out
+
+
+def backproject_volume_grad(plan: Plan, f: torch.Tensor, grad_g: torch.Tensor,
+                            out: torch.Tensor = None, stream=None):
+    """dL/dH' from dL/dg for g = H' f (``lfbp_backproject_volume_grad``)."""
+    Wx, Wy = f.shape
+    _check_f32(f, (Wx, Wy), "f")
+    _check_f32(grad_g, (plan.Nz, Wx, Wy), "grad_g")
+    if out is None:
+        out = torch.empty(plan.elems, dtype=torch.float32, device=f.device)
+    _check_tensor(plan, out, "out")
+    with torch.cuda.device(f.device):
+        _check(plan._lib.lfbp_backproject_volume_grad(plan.handle, f.data_ptr(), grad_g.data_ptr(),
+                                                      Wx, Wy, out.data_ptr(), _stream_ptr(stream)),
+               "lfbp_backproject_volume_grad")
     return out
 
 

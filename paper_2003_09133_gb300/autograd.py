@@ -27,3 +27,24 @@ class LFBackproject(torch.autograd.Function):
 def backprojection_array(H: torch.Tensor, plan: "_lib.Plan") -> torch.Tensor:
     """Differentiable H -> H' for a flat ragged array ``H`` described by ``plan``."""
     return LFBackproject.apply(H, plan)
+
+
+class LFBackprojectVolume(torch.autograd.Function):
+    """g = H' f with f fixed; differentiable with respect to H'."""
+
+    @staticmethod
+    def forward(ctx, Hp: torch.Tensor, f: torch.Tensor, plan: "_lib.Plan"):
+        f = f.contiguous()
+        ctx.plan = plan
+        ctx.save_for_backward(f)
+        return _lib.backproject_volume(plan, Hp.contiguous(), f)
+
+    @staticmethod
+    def backward(ctx, grad_g: torch.Tensor):
+        (f,) = ctx.saved_tensors
+        return _lib.backproject_volume_grad(ctx.plan, f, grad_g.contiguous()), None, None
+
+
+def backproject_volume(Hp: torch.Tensor, f: torch.Tensor, plan: "_lib.Plan") -> torch.Tensor:
+    """Differentiable (in H') backprojection g = H' f of a sensor image f [Wx, Wy]."""
+    return LFBackprojectVolume.apply(Hp, f, plan)

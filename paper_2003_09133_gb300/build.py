@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblfbp.so")
 
-SOURCES = ["lfbp.cu"]
+SOURCES = ["lfbp.cu", "lfbp_project.cu"]
 HEADERS = ["lfbp_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -32,44 +32,41 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
 constexpr int kConsumerWarps = 8;
 constexpr int kPersistentThreads = 32 * (1 + kConsumerWarps);
-constexpr int kInfoBytes = 256;  // per-stage TileInfo slot (aligned)
-static_assert(sizeof(TileInfo) <= kInfoBytes, "TileInfo too large");
+constexpr int kInfoBytes = 64;  // per-stage slot for the tile descriptor
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 
 // ------------------------------------------------------------------ plain --
-// grid = (nV, Nx, nU) tiles of one depth; block = kPlainThreads.
-// smem: [stage: tile bytes][TileInfo][mbarrier]
+// grid = (nV, Nx, nU) tiles of one depth; block = kPlainThreads; one tile per
+// CTA.  `base` carries the depth's shape, pitch and flags; the CTA fills in
+// its own p, u0, v0, nrows, ncols.
+// smem: [stage: tile bytes][mbarrier]
 __global__ void __launch_bounds__(kPlainThreads)
-    k_gather_depth(JobDesc jd, const unsigned char* __restrict__ in_depth,
+    k_gather_depth(TileDesc base, const unsigned char* __restrict__ in_depth,
                    const unsigned char* in_safe_end, unsigned char* __restrict__ out_depth, int J,
                    int V, int stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage = smem;
-  TileInfo* ti = reinterpret_cast<TileInfo*>(smem + stage_bytes);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes + kInfoBytes);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes);
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-  TileDesc td;
-  td.job = 0;
+  TileDesc td = base;
   td.p = (unsigned short)blockIdx.y;
   const int u0 = blockIdx.z * J, v0 = blockIdx.x * V;
   td.u0 = (unsigned short)u0;
   td.v0 = (unsigned short)v0;
-  td.nrows = (unsigned short)min(J, jd.Ks - u0);
-  td.ncols = (unsigned short)min(V, jd.Kt - v0);
-  td.pad = 0;
+  td.nrows = (unsigned short)min(J, (int)base.Ks - u0);
+  td.ncols = (unsigned short)min(V, (int)base.Kt - v0);
 
   const uint32_t b = smem_addr(bar);
   if (tid == 0) {
     abort_flag = 0;
     mbar_init(b, 1);
     fence_mbar_init();
-    make_tile_info(*ti, 0, td, jd, in_depth, out_depth);
   }
   __syncthreads();
-  if (warp == 0) issue_tile_loads(td, jd, in_depth, in_safe_end, stage, b, lane);
+  if (warp == 0) issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane);
   if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
     set_status(kStatusTimeout);
     abort_flag = 1;
@@ -77,18 +74,22 @@ __global__ void __launch_bounds__(kPlainThreads)
     mbar_wait_bounded(b, 0, nullptr, kWaitLimitNs);
     return;
   }
-  gather_store_dispatch(*ti, stage, tid, kPlainThreads);
+  gather_tile_any(td, stage, in_depth, out_depth, warp, kPlainThreads / 32, lane);
 }
 
 // ------------------------------------------------------------- persistent --
-// grid = SMs * ctas_per_sm; block = kPersistentThreads.
-// smem: [nstages x stage_bytes][nstages x TileInfo][full[nstages]][empty[nstages]]
-__global__ void __launch_bounds__(kPersistentThreads)
-    k_gather_persistent(const __grid_constant__ BatchPtrs ptrs, const JobDesc* __restrict__ jobs,
-                        const TileDesc* __restrict__ tiles, int ntiles, unsigned* counter,
-                        int stage_bytes, int nstages) {
+// grid = SMs * ctas_per_sm; block = kPersistentThreads.  CTA c takes tiles
+// c, c + grid, c + 2 grid, ... (consecutive tiles are neighbours in memory, so
+// the tiles in flight at any time cover one contiguous stretch of the work
+// list).  Warp 0 produces: it prefetches the next descriptor, waits for a free
+// stage, and issues the stage's bulk copies; warps 1..8 consume.
+// smem: [nstages x stage_bytes][nstages x descriptor][full[nstages]][empty[nstages]]
+__global__ void __launch_bounds__(kPersistentThreads, 2)
+    k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
+                        const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
+                        int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
-  TileInfo* infos = reinterpret_cast<TileInfo*>(smem + (size_t)nstages * stage_bytes);
+  TileDesc* infos = reinterpret_cast<TileDesc*>(smem + (size_t)nstages * stage_bytes);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * (stage_bytes + kInfoBytes));
   uint64_t* empty = full + nstages;
   __shared__ int abort_flag;
@@ -107,9 +108,15 @@ __global__ void __launch_bounds__(kPersistentThreads)
   if (warp == 0) {
     // ---- producer warp
     int it = 0;
-    for (;; ++it) {
+    int t = blockIdx.x;
+    TileDesc td;
+    if (t < ntiles) td = tiles[t];
+    for (;; ++it, t += gridDim.x) {
       const int s = it % nstages;
       const uint32_t fb = smem_addr(&full[s]);
+      TileDesc next;
+      const int tn = t + (int)gridDim.x;
+      if (tn < ntiles) next = tiles[tn];  // in flight while this tile is issued
       if (it >= nstages) {
         const uint32_t par = (uint32_t)((it / nstages - 1) & 1);
         if (!mbar_wait_bounded(smem_addr(&empty[s]), par, &abort_flag, kWaitLimitNs)) {
@@ -120,26 +127,24 @@ __global__ void __launch_bounds__(kPersistentThreads)
           break;
         }
       }
-      int t = 0;
-      if (lane == 0) t = (int)atomicAdd(counter, 1u);
-      t = __shfl_sync(0xffffffffu, t, 0);
       if (t >= ntiles) {
         if (lane == 0) {
-          infos[s].tile = -1;
+          infos[s].pad = 0xffff;  // end of work
           mbar_arrive(fb);
         }
         ++it;
         break;
       }
-      const TileDesc td = tiles[t];
-      const JobDesc jd = jobs[td.job];
-      const unsigned char* in_arr = ptrs.in[jd.arr];
-      const unsigned char* in_depth = in_arr + jd.off_bytes;
-      unsigned char* out_depth = ptrs.out[jd.arr] + jd.off_bytes;
-      const unsigned char* safe_end = in_arr + (ptrs.in_bytes[jd.arr] & ~15ull);
-      if (lane == 0) make_tile_info(infos[s], t, td, jd, in_depth, out_depth);
+      const unsigned char* in_arr = ptrs.in[td.arr];
+      const unsigned char* in_depth = in_arr + td.off_bytes;
+      const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
+      if (lane == 0) {
+        infos[s] = td;
+        infos[s].pad = 0;
+      }
       __syncwarp();
-      issue_tile_loads(td, jd, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane);
+      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane);
+      td = next;
     }
     // make sure no copy into this CTA's shared memory is still in flight
     if (lane == 0) {
@@ -152,7 +157,7 @@ __global__ void __launch_bounds__(kPersistentThreads)
     }
   } else {
     // ---- consumer warps
-    const int ctid = tid - 32, nthr = 32 * kConsumerWarps;
+    const int cw = warp - 1;
     for (int it = 0;; ++it) {
       const int s = it % nstages;
       const uint32_t par = (uint32_t)((it / nstages) & 1);
@@ -163,9 +168,12 @@ __global__ void __launch_bounds__(kPersistentThreads)
         }
         break;
       }
-      const TileInfo& ti = infos[s];
-      if (ti.tile < 0) break;
-      gather_store_dispatch(ti, smem + (size_t)s * stage_bytes, ctid, nthr);
+      const TileDesc td = infos[s];
+      if (td.pad == 0xffff) break;
+      const unsigned char* in_depth = ptrs.in[td.arr] + td.off_bytes;
+      unsigned char* out_depth = ptrs.out[td.arr] + td.off_bytes;
+      gather_tile_any(td, smem + (size_t)s * stage_bytes, in_depth, out_depth, cw, kConsumerWarps,
+                      lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
     }
@@ -175,6 +183,13 @@ __global__ void __launch_bounds__(kPersistentThreads)
 }  // namespace lfbp
 
 // ====================================================================== host
+namespace lfbp {
+int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, const float* in,
+                             int Wx, int Wy, float* out, int accumulate, cudaStream_t st);
+int launch_backproject_grad(const float* f, const float* dg, int Nx, int Ny, int Ks, int Kt,
+                            int Wx, int Wy, float* dA, cudaStream_t st);
+}  // namespace lfbp
+
 using namespace lfbp;
 
 struct lfbp_plan_s {
@@ -185,6 +200,10 @@ struct lfbp_plan_s {
   int es = 4;
   std::vector<size_t> off;  // Nz + 1
   unsigned long long uid = 0;
+  // per-depth tiling for the tile-size target `tiling_target` (built lazily)
+  std::mutex mu;
+  int tiling_target = 0;
+  std::vector<lfbp::DepthTiling> tiling;
 };
 
 namespace {
@@ -260,41 +279,157 @@ int device_props(int* dev, int* sms, int* smem_optin) {
   return LFBP_OK;
 }
 
-// One launch per depth of the plain kernel.
-int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st) {
-  int rc = check_buffers(p, in, out);
-  if (rc) return rc;
+// Per-depth tiling of a plan for a tile-size target, cached in the plan.
+const std::vector<DepthTiling>& plan_tiling(lfbp_plan p, int target) {
+  std::lock_guard<std::mutex> lk(p->mu);
+  if (p->tiling_target != target || (int)p->tiling.size() != p->Nz) {
+    p->tiling.clear();
+    for (int z = 0; z < p->Nz; ++z)
+      p->tiling.push_back(tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, target));
+    p->tiling_target = target;
+  }
+  return p->tiling;
+}
+
+TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr) {
+  TileDesc t;
+  std::memset(&t, 0, sizeof(t));
+  t.off_bytes = p->off[z] * (size_t)p->es;
+  t.Nx = (unsigned short)p->Nx;
+  t.Ny = (unsigned short)p->Ny;
+  t.Ks = (unsigned short)p->Ks[z];
+  t.Kt = (unsigned short)p->Kt[z];
+  t.P = (unsigned short)d.P;
+  t.arr = (unsigned char)arr;
+  t.flags = (unsigned char)((p->es == 2 ? 1 : 0) | (mode << 1));
+  return t;
+}
+
+// One launch per depth of the plain kernel, for depths [z0, z1).
+int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int mode, int z0,
+                 int z1, cudaStream_t st) {
   const Tuning tu = default_tuning();
-  const unsigned char* inb = (const unsigned char*)in;
-  unsigned char* outb = (unsigned char*)out;
   const size_t arr_bytes = p->off.back() * (size_t)p->es;
   const unsigned char* safe_end = inb + (arr_bytes & ~(size_t)15);
+  const std::vector<DepthTiling>& tl = plan_tiling(p, tu.tile_bytes);
   int max_smem = 0;
-  for (int z = 0; z < p->Nz; ++z) {
-    DepthTiling d = tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, tu.tile_bytes);
-    max_smem = std::max(max_smem, d.max_tile_bytes);
-  }
-  const int smem_total = max_smem + kInfoBytes + 16;
-  if ((rc = ensure_smem_attr((const void*)k_gather_depth, smem_total))) return rc;
-  for (int z = 0; z < p->Nz; ++z) {
-    DepthTiling d = tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, tu.tile_bytes);
-    JobDesc jd;
-    jd.off_bytes = p->off[z] * (size_t)p->es;
-    jd.arr = 0;
-    jd.Nx = p->Nx;
-    jd.Ny = p->Ny;
-    jd.Ks = p->Ks[z];
-    jd.Kt = p->Kt[z];
-    jd.es = p->es;
-    jd.mode = mode;
-    jd.pad = 0;
+  for (int z = z0; z < z1; ++z) max_smem = std::max(max_smem, tl[z].max_tile_bytes);
+  int rc = ensure_smem_attr((const void*)k_gather_depth, max_smem + 16);
+  if (rc) return rc;
+  for (int z = z0; z < z1; ++z) {
+    const DepthTiling& d = tl[z];
+    const TileDesc base = depth_desc(p, z, d, mode, 0);
     dim3 grid(d.nV, p->Nx, d.nU);
-    const int smem = d.max_tile_bytes;
-    k_gather_depth<<<grid, kPlainThreads, smem + kInfoBytes + 16, st>>>(
-        jd, inb + jd.off_bytes, safe_end, outb + jd.off_bytes, d.J, d.V, smem);
+    const int smem = (d.max_tile_bytes + 15) & ~15;
+    k_gather_depth<<<grid, kPlainThreads, smem + 16, st>>>(
+        base, inb + base.off_bytes, safe_end, outb + base.off_bytes, d.J, d.V, smem);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_gather_depth launch");
+  return LFBP_OK;
+}
+
+int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st) {
+  int rc = check_buffers(p, in, out);
+  if (rc) return rc;
+  return launch_plain(p, (const unsigned char*)in, (unsigned char*)out, mode, 0, p->Nz, st);
+}
+
+// --------------------------------------------------- host-to-host pipeline --
+// Per device: two helper streams and a pool of events for overlapping the
+// host->device copy of depth chunk c+1, the map of chunk c on the caller's
+// stream and the device->host copy of chunk c-1.
+struct HostPipe {
+  int dev = -1;
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  std::vector<cudaEvent_t> ev;
+  std::mutex mu;
+  ~HostPipe() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (h2d) cudaStreamDestroy(h2d);
+    if (d2h) cudaStreamDestroy(d2h);
+  }
+};
+std::vector<std::unique_ptr<HostPipe>> g_pipes;  // guarded by g_mu
+
+int get_pipe(int dev, HostPipe** out) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& p : g_pipes)
+    if (p->dev == dev) {
+      *out = p.get();
+      return LFBP_OK;
+    }
+  std::unique_ptr<HostPipe> hp(new HostPipe());
+  hp->dev = dev;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  if ((e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamCreate");
+  *out = hp.get();
+  g_pipes.push_back(std::move(hp));
+  return LFBP_OK;
+}
+
+int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp, int mode,
+             cudaStream_t st) {
+  int rc = check_buffers(p, dH, dHp);
+  if (rc) return rc;
+  const size_t bytes = p->off.back() * (size_t)p->es;
+  if (bytes == 0) return LFBP_OK;
+  if (!H_host || !Hp_host) return fail(LFBP_ERR_NULL, "host buffer pointer is NULL");
+  if (overlaps(H_host, bytes, Hp_host, bytes))
+    return fail(LFBP_ERR_ALIAS, "host input and output overlap");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  HostPipe* hp = nullptr;
+  if ((rc = get_pipe(dev, &hp))) return rc;
+  // chunks of consecutive depths of at least 32 MB each (fewer, larger copies)
+  std::vector<int> cut(1, 0);
+  size_t acc = 0;
+  for (int z = 0; z < p->Nz; ++z) {
+    acc += (p->off[z + 1] - p->off[z]) * (size_t)p->es;
+    if (acc >= (32u << 20) || z + 1 == p->Nz) {
+      cut.push_back(z + 1);
+      acc = 0;
+    }
+  }
+  const int nch = (int)cut.size() - 1;
+  std::lock_guard<std::mutex> lk(hp->mu);
+  while ((int)hp->ev.size() < 3 * nch + 1) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventCreate");
+    hp->ev.push_back(ev);
+  }
+  const unsigned char* hin = (const unsigned char*)H_host;
+  unsigned char* hout = (unsigned char*)Hp_host;
+  unsigned char* din = (unsigned char*)dH;
+  unsigned char* dout = (unsigned char*)dHp;
+  cudaEvent_t start = hp->ev[3 * nch];
+  if ((e = cudaEventRecord(start, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(hp->h2d, start, 0)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamWaitEvent");
+  for (int c = 0; c < nch; ++c) {
+    const size_t o = p->off[cut[c]] * (size_t)p->es;
+    const size_t n = (p->off[cut[c + 1]] - p->off[cut[c]]) * (size_t)p->es;
+    cudaEvent_t in_ready = hp->ev[3 * c], mapped = hp->ev[3 * c + 1], out_done = hp->ev[3 * c + 2];
+    if ((e = cudaMemcpyAsync(din + o, hin + o, n, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+    cudaEventRecord(in_ready, hp->h2d);
+    cudaStreamWaitEvent(st, in_ready, 0);
+    if ((rc = launch_plain(p, din, dout, mode, cut[c], cut[c + 1], st))) return rc;
+    cudaEventRecord(mapped, st);
+    cudaStreamWaitEvent(hp->d2h, mapped, 0);
+    if ((e = cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    cudaEventRecord(out_done, hp->d2h);
+  }
+  // the caller's stream sees the whole call complete: last copy-out, and (by
+  // stream order) every map launched on it
+  if ((e = cudaStreamWaitEvent(st, hp->ev[3 * (nch - 1) + 2], 0)) != cudaSuccess)
+    return cuda_fail(e, "cudaStreamWaitEvent");
   return LFBP_OK;
 }
 
@@ -302,11 +437,9 @@ int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st)
 struct BatchState {
   int dev = -1;
   std::vector<unsigned long long> uids;
-  int ntiles = 0, njobs = 0;
+  int ntiles = 0;
   int stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
-  JobDesc* d_jobs = nullptr;
   TileDesc* d_tiles = nullptr;
-  unsigned* d_counter = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t knode = nullptr;
@@ -315,9 +448,7 @@ struct BatchState {
   ~BatchState() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
-    if (d_jobs) cudaFree(d_jobs);
     if (d_tiles) cudaFree(d_tiles);
-    if (d_counter) cudaFree(d_counter);
   }
 };
 
@@ -325,50 +456,43 @@ std::vector<std::unique_ptr<BatchState>> g_batches;  // guarded by g_mu
 unsigned long long g_clock = 0;
 constexpr size_t kMaxCachedBatches = 8;
 
-int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu) {
-  int sms = 0, optin = 0, dev = 0;
-  int rc = device_props(&dev, &sms, &optin);
-  if (rc) return rc;
-  bs.dev = dev;
-  std::vector<JobDesc> jobs;
-  std::vector<TileDesc> tiles;
-  int max_tile = 0;
+// Work list of all depths of all arrays: per depth, u-block major, then p,
+// then v-block, so that tiles in flight together touch neighbouring input
+// segments and neighbouring output runs.
+void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc>& tiles,
+                 int* max_tile) {
+  *max_tile = 0;
   for (int i = 0; i < n; ++i) {
     lfbp_plan p = plans[i];
+    const std::vector<DepthTiling>& tl = plan_tiling(p, target);
     for (int z = 0; z < p->Nz; ++z) {
-      DepthTiling d = tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, tu.tile_bytes);
-      max_tile = std::max(max_tile, d.max_tile_bytes);
-      JobDesc jd;
-      jd.off_bytes = p->off[z] * (size_t)p->es;
-      jd.arr = i;
-      jd.Nx = p->Nx;
-      jd.Ny = p->Ny;
-      jd.Ks = p->Ks[z];
-      jd.Kt = p->Kt[z];
-      jd.es = p->es;
-      jd.mode = (int)p->mode;
-      jd.pad = 0;
-      const unsigned job = (unsigned)jobs.size();
-      jobs.push_back(jd);
-      // u-block major, then p, then v-block: tiles in flight together touch
-      // neighbouring input segments and neighbouring output runs
+      const DepthTiling& d = tl[z];
+      *max_tile = std::max(*max_tile, d.max_tile_bytes);
+      const TileDesc base = depth_desc(p, z, d, (int)p->mode, i);
       for (int ub = 0; ub < d.nU; ++ub)
         for (int pp = 0; pp < p->Nx; ++pp)
           for (int vb = 0; vb < d.nV; ++vb) {
-            TileDesc t;
-            t.job = job;
+            TileDesc t = base;
             t.p = (unsigned short)pp;
             t.u0 = (unsigned short)(ub * d.J);
             t.v0 = (unsigned short)(vb * d.V);
             t.nrows = (unsigned short)std::min(d.J, p->Ks[z] - ub * d.J);
             t.ncols = (unsigned short)std::min(d.V, p->Kt[z] - vb * d.V);
-            t.pad = 0;
             tiles.push_back(t);
           }
     }
   }
+}
+
+int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu) {
+  int sms = 0, optin = 0, dev = 0;
+  int rc = device_props(&dev, &sms, &optin);
+  if (rc) return rc;
+  bs.dev = dev;
+  std::vector<TileDesc> tiles;
+  int max_tile = 0;
+  build_tiles(n, plans, tu.tile_bytes, tiles, &max_tile);
   bs.ntiles = (int)tiles.size();
-  bs.njobs = (int)jobs.size();
   bs.stage_bytes = (max_tile + 127) & ~127;
   const int per_cta_budget = std::min(optin, (227 * 1024) / tu.ctas_per_sm - 1024);
   const int per_stage = bs.stage_bytes + kInfoBytes + 16;
@@ -378,15 +502,8 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
   bs.nstages = nst;
   bs.smem = nst * per_stage;
-  bs.grid = sms * tu.ctas_per_sm;
+  bs.grid = std::max(1, std::min(sms * tu.ctas_per_sm, bs.ntiles));
   cudaError_t e;
-  if (bs.njobs) {
-    if ((e = cudaMalloc(&bs.d_jobs, sizeof(JobDesc) * jobs.size())) != cudaSuccess)
-      return cuda_fail(e, "cudaMalloc(jobs)");
-    if ((e = cudaMemcpy(bs.d_jobs, jobs.data(), sizeof(JobDesc) * jobs.size(),
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpy(jobs)");
-  }
   if (bs.ntiles) {
     if ((e = cudaMalloc(&bs.d_tiles, sizeof(TileDesc) * tiles.size())) != cudaSuccess)
       return cuda_fail(e, "cudaMalloc(tiles)");
@@ -394,25 +511,12 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(tiles)");
   }
-  if ((e = cudaMalloc(&bs.d_counter, 16)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(counter)");
   if ((rc = ensure_smem_attr((const void*)k_gather_persistent, bs.smem))) return rc;
-
-  // graph: counter reset, then the persistent kernel
+  // a one-node graph: relaunching it costs one cudaGraphLaunch; pointer
+  // changes are patched into the node's parameters
   if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
-  cudaMemsetParams mp;
-  std::memset(&mp, 0, sizeof(mp));
-  mp.dst = bs.d_counter;
-  mp.value = 0;
-  mp.elementSize = 4;
-  mp.width = 1;
-  mp.height = 1;
-  mp.pitch = 4;
-  cudaGraphNode_t mnode;
-  if ((e = cudaGraphAddMemsetNode(&mnode, bs.graph, nullptr, 0, &mp)) != cudaSuccess)
-    return cuda_fail(e, "cudaGraphAddMemsetNode");
   std::memset(&bs.ptrs, 0, sizeof(bs.ptrs));
-  void* args[] = {&bs.ptrs, &bs.d_jobs, &bs.d_tiles, &bs.ntiles, &bs.d_counter, &bs.stage_bytes,
-                  &bs.nstages};
+  void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.func = (void*)k_gather_persistent;
@@ -420,7 +524,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   kp.blockDim = dim3(kPersistentThreads);
   kp.sharedMemBytes = bs.smem;
   kp.kernelParams = args;
-  if ((e = cudaGraphAddKernelNode(&bs.knode, bs.graph, &mnode, 1, &kp)) != cudaSuccess)
+  if ((e = cudaGraphAddKernelNode(&bs.knode, bs.graph, nullptr, 0, &kp)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphAddKernelNode");
   if ((e = cudaGraphInstantiate(&bs.exec, bs.graph, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphInstantiate");
@@ -486,8 +590,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   }
   if (std::memcmp(&np, &bs->ptrs, sizeof(np)) != 0) {
     bs->ptrs = np;
-    void* args[] = {&bs->ptrs, &bs->d_jobs, &bs->d_tiles, &bs->ntiles, &bs->d_counter,
-                    &bs->stage_bytes, &bs->nstages};
+    void* args[] = {&bs->ptrs, &bs->d_tiles, &bs->ntiles, &bs->stage_bytes, &bs->nstages};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.func = (void*)k_gather_persistent;
@@ -499,6 +602,21 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
       return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
   }
   if ((e = cudaGraphLaunch(bs->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return LFBP_OK;
+}
+
+int check_projector(lfbp_plan p, const void* a, const void* b, const void* out, int Wx, int Wy,
+                    size_t out_bytes) {
+  if (!p) return fail(LFBP_ERR_NULL, "plan is NULL");
+  if (p->dt != LFBP_F32) return fail(LFBP_ERR_DTYPE, "projectors need an LFBP_F32 plan");
+  if (Wx < 1 || Wy < 1) return fail(LFBP_ERR_BAD_SHAPE, "sensor must be at least 1 x 1");
+  for (int z = 0; z < p->Nz; ++z)
+    if (p->Kt[z] > 3072) return fail(LFBP_ERR_BAD_SHAPE, "projectors need Kt <= 3072");
+  if ((p->Nz > 0 && !a) || !b || !out) return fail(LFBP_ERR_NULL, "buffer pointer is NULL");
+  if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)out) & 3)
+    return fail(LFBP_ERR_ALIGN, "buffers must be 4-byte aligned");
+  const size_t sa = p->off.back() * 4;
+  if (a && overlaps(a, sa, out, out_bytes)) return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   return LFBP_OK;
 }
 
@@ -584,6 +702,12 @@ int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_st
   return run_plain(p, dH, dHp, (int)p->mode, (cudaStream_t)cuda_stream);
 }
 
+int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH_work,
+                                void* dHp_work, void* cuda_stream) {
+  if (!p) return fail(LFBP_ERR_NULL, "plan is NULL");
+  return run_host(p, H_host, Hp_host, dH_work, dHp_work, (int)p->mode, (cudaStream_t)cuda_stream);
+}
+
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream) {
   return run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);
@@ -593,6 +717,56 @@ int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_st
   if (!p) return fail(LFBP_ERR_NULL, "plan is NULL");
   const int mode = p->mode == LFBP_MAP_TRANSPOSE ? 0 : 2;
   return run_plain(p, dHp_grad, dH_grad, mode, (cudaStream_t)cuda_stream);
+}
+
+int lfbp_backproject_volume(lfbp_plan p, const void* dHp, const float* df, int Wx, int Wy,
+                            float* dg, void* cuda_stream) {
+  int rc = check_projector(p, dHp, df, dg, Wx, Wy, (size_t)(p ? p->Nz : 0) * Wx * Wy * 4);
+  if (rc) return rc;
+  if (overlaps(df, (size_t)Wx * Wy * 4, dg, (size_t)p->Nz * Wx * Wy * 4))
+    return fail(LFBP_ERR_ALIAS, "output overlaps an input");
+  const float* hp = (const float*)dHp;
+  for (int z = 0; z < p->Nz; ++z) {
+    if (launch_shift_variant_sum(hp + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z], df, Wx, Wy,
+                                 dg + (size_t)z * Wx * Wy, 0, (cudaStream_t)cuda_stream))
+      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
+  }
+  return LFBP_OK;
+}
+
+int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, int Wy, float* df,
+                         void* cuda_stream) {
+  int rc = check_projector(p, dH, dg, df, Wx, Wy, (size_t)Wx * Wy * 4);
+  if (rc) return rc;
+  if (overlaps(df, (size_t)Wx * Wy * 4, dg, (size_t)p->Nz * Wx * Wy * 4))
+    return fail(LFBP_ERR_ALIAS, "output overlaps an input");
+  const float* h = (const float*)dH;
+  if (p->Nz == 0) {
+    cudaError_t e = cudaMemsetAsync(df, 0, (size_t)Wx * Wy * 4, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  }
+  for (int z = 0; z < p->Nz; ++z) {
+    if (launch_shift_variant_sum(h + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z],
+                                 dg + (size_t)z * Wx * Wy, Wx, Wy, df, z > 0,
+                                 (cudaStream_t)cuda_stream))
+      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
+  }
+  return LFBP_OK;
+}
+
+int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
+                                 void* dHp_grad, void* cuda_stream) {
+  int rc = check_projector(p, dgrad, df, dHp_grad, Wx, Wy, p ? p->off.back() * 4 : 0);
+  if (rc) return rc;
+  if (overlaps(df, (size_t)Wx * Wy * 4, dHp_grad, p->off.back() * 4))
+    return fail(LFBP_ERR_ALIAS, "output overlaps an input");
+  float* out = (float*)dHp_grad;
+  for (int z = 0; z < p->Nz; ++z) {
+    if (launch_backproject_grad(df, dgrad + (size_t)z * Wx * Wy, p->Nx, p->Ny, p->Ks[z], p->Kt[z],
+                                Wx, Wy, out + p->off[z], (cudaStream_t)cuda_stream))
+      return fail(LFBP_ERR_CUDA, "k_backproject_grad launch failed");
+  }
+  return LFBP_OK;
 }
 
 int lfbp_sync_status(void* cuda_stream) {

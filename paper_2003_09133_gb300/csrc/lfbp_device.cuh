@@ -7,14 +7,27 @@
 // per q, stride Ks*Kt); its source row (a, s) = ((p+u-c_s) mod Nx, Ks-1-u) is
 // Ny contiguous segments of Kt elements (one per b).  Within the row, output
 // element (q, v) comes from segment b = (q+v-c_t) mod Ny at t = Kt-1-v: a
-// reversal of the pixel axis and a cyclic exchange of the cell axis.
+// reversal of the pixel axis and a cyclic exchange of the cell axis, i.e. a
+// walk along a diagonal of the (b, t) plane.
 //
-// A tile is `nrows` consecutive output rows u0..u0+nrows-1 of one p (and a
-// column range v0..v0+ncols-1, all of Kt unless a row is too large for one
-// stage).  Its output is Ny contiguous runs of nrows*ncols elements; its
-// input is nrows*Ny segments, loaded with TMA bulk copies into shared memory
-// (each widened to 16-byte boundaries, since segments start anywhere), then
-// gathered through the index map and written with 128-bit stores.
+// TILE.  `nrows` consecutive output rows u0.. of one p, and the column range
+// v0..v0+ncols-1 (all of Kt unless one row does not fit a stage; then
+// nrows = 1).  Its output is Ny contiguous runs of nrows*ncols elements (one
+// per q); its input is nrows*Ny segments of ncols elements.
+//
+// SHARED-MEMORY LAYOUT.  Segment (j, b) is brought in by one TMA bulk copy,
+// widened to 16-byte boundaries because segments start anywhere; its element
+// i lands at  j*RP + R_j + b*P + i  (elements), where the slot pitch P is
+// congruent to Ks*Kt modulo 16/esize and R_j is the 16-byte phase of segment
+// (j, 0).  Every copy destination is then 16-byte aligned, and the address of
+// a diagonal walk is linear in b.  Among the pitches allowed, the planner
+// picks the one with the fewest shared-memory bank conflicts for the gather's
+// access pattern (choose_pitch).
+//
+// GATHER.  Each consumer warp instruction serves 4 output runs q..q+3 with 8
+// lanes each: 8 consecutive fp32 elements, or 8 consecutive fp16 pairs, i.e.
+// one aligned 32-byte sector per run.  The four runs sit at different 16-byte
+// phases in shared memory, which spreads a warp's loads over the banks.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -23,24 +36,19 @@ namespace lfbp {
 
 constexpr int kMaxBatch = 64;       // arrays per batched launch
 constexpr int kStatusTimeout = -7;  // LFBP_ERR_TIMEOUT
+constexpr int kGroupsPerItem = 4;   // sectors per run handled by one consumer work item
 
-// One (array, depth) of a batched launch.
-struct JobDesc {
-  unsigned long long off_bytes;  // byte offset of the depth inside its array
-  int arr;                       // array slot in BatchPtrs
-  int Nx, Ny, Ks, Kt;
-  int es;    // bytes per element: 4 or 2
-  int mode;  // 0 transpose, 1 paper window (forward), 2 paper window (adjoint)
-  int pad;
-};
-static_assert(sizeof(JobDesc) == 40, "JobDesc layout");
-
-// One tile of a job.
+// One tile, self-contained (32 bytes).
 struct TileDesc {
-  unsigned job;
-  unsigned short p, u0, v0, nrows, ncols, pad;
+  unsigned long long off_bytes;  // byte offset of the depth inside its array
+  unsigned short p, u0, v0, nrows, ncols;
+  unsigned short Nx, Ny, Ks, Kt;
+  unsigned short P;     // slot pitch in elements
+  unsigned char arr;    // array slot in BatchPtrs
+  unsigned char flags;  // bit 0: fp16 storage; bits 1-2: mode
+  unsigned short pad;
 };
-static_assert(sizeof(TileDesc) == 16, "TileDesc layout");
+static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
 
 struct BatchPtrs {
   const unsigned char* in[kMaxBatch];
@@ -63,76 +71,133 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) {
 }
 __device__ __forceinline__ uint32_t fmod_(uint32_t n, FastDiv f) { return n - fdiv(n, f) * f.d; }
 
-// Bytes of the shared-memory slot that holds a segment of n elements widened
-// to 16-byte boundaries, whatever its alignment.
-__host__ __device__ inline uint32_t slot_bytes(uint32_t n, uint32_t es) {
-  return (n * es + 16u - es + 15u) & ~15u;
-}
-
 inline int lfbp_min(int a, int b) { return a < b ? a : b; }
 inline int lfbp_max(int a, int b) { return a > b ? a : b; }
 
-// Host side: tiling of one depth, target = shared-memory bytes of one tile.
+// Row pitch (elements) of a tile whose slots have pitch P.
+__host__ __device__ inline int row_pitch(int Ny, int P, int es) {
+  const int E = 16 / es;
+  return ((Ny * P + E - 1) / E) * E;
+}
+
+// ------------------------------------------------------------ host planning --
+// Shared-memory bank wavefronts of the gather for one slot pitch P, averaged
+// over pseudo-random run phases and positions (the phases depend on buffer
+// addresses unknown at planning time).  Mirrors the consumer's lane mapping.
+inline double pitch_cost(int Ny, int Ks, int Kt, int ncols, int es, int P) {
+  const int SE = 32 / es, epl = es == 4 ? 1 : 2, E = 16 / es;
+  const long long KK = (long long)Ks * Kt;
+  const int ct = (Kt - 1) / 2;
+  const int cb = ((0 - ct) % Ny + Ny) % Ny;
+  uint32_t rng = 0x9e3779b9u ^ (uint32_t)((uint32_t)P * 2654435761u);
+  long long total = 0;
+  int count = 0;
+  for (int trial = 0; trial < 48; ++trial) {
+    rng = rng * 1664525u + 1013904223u;
+    const int q0 = (int)((rng >> 8) % (uint32_t)Ny);
+    rng = rng * 1664525u + 1013904223u;
+    const int out0 = (int)((rng >> 8) % 4096u);
+    rng = rng * 1664525u + 1013904223u;
+    const int R = (int)((rng >> 8) % 64u) * E + (int)((rng >> 20) % (uint32_t)E);
+    rng = rng * 1664525u + 1013904223u;
+    const int ngroups = lfbp_max(1, ncols / SE);
+    const int g = (int)((rng >> 8) % (uint32_t)ngroups);
+    for (int sub = 0; sub < epl; ++sub) {
+      long long words[32];
+      int n = 0;
+      for (int r = 0; r < 4; ++r) {
+        const int q = q0 + r;
+        if (q >= Ny) continue;
+        const int m = (int)((out0 + (long long)q * KK) % SE);
+        for (int k = 0; k < 8; ++k) {
+          const int vl = g * SE + k * epl + sub - m;
+          if (vl < 0 || vl >= ncols) continue;
+          const int b = (int)(((long long)q + cb + vl) % Ny);
+          const long long idx = (long long)R + (long long)b * P + ncols - 1 - vl;
+          words[n++] = (idx * es) / 4;
+        }
+      }
+      int worst = 0;
+      for (int bank = 0; bank < 32; ++bank) {
+        long long seen[32];
+        int ns = 0;
+        for (int i = 0; i < n; ++i) {
+          if ((int)(words[i] % 32) != bank) continue;
+          bool dup = false;
+          for (int s = 0; s < ns; ++s) dup = dup || seen[s] == words[i];
+          if (!dup) seen[ns++] = words[i];
+        }
+        worst = lfbp_max(worst, ns);
+      }
+      total += worst;
+      ++count;
+    }
+  }
+  return count ? (double)total / count : 0.0;
+}
+
+// Slot pitch for segments of ncols elements: P >= ncols + 2E - 2 (room for a
+// copy widened to 16-byte boundaries), P = Ks*Kt (mod E), fewest conflicts.
+inline int choose_pitch(int Ny, int Ks, int Kt, int ncols, int es) {
+  const int E = 16 / es;
+  const int KKm = (int)(((long long)Ks * Kt) % E);
+  int P0 = ncols + 2 * E - 2;
+  P0 += ((KKm - P0) % E + E) % E;
+  int best = P0;
+  double best_cost = 1e30;
+  for (int x = 0; x < 8; ++x) {
+    const int P = P0 + x * E;
+    const double cost = pitch_cost(Ny, Ks, Kt, ncols, es, P);
+    if (cost < best_cost - 1e-9) {
+      best_cost = cost;
+      best = P;
+    }
+  }
+  return best;
+}
+
 // Tiling of one depth: rows per tile J, columns per tile V (V = Kt unless one
-// row does not fit the target), and the counts of u- and v-blocks.
+// row does not fit the target), counts of u- and v-blocks, and slot pitch.
 struct DepthTiling {
-  int J, V, nU, nV;
+  int J, V, nU, nV, P, RP;
   int max_tile_bytes;
 };
 
 inline DepthTiling tile_depth(int Ny, int Ks, int Kt, int es, int target) {
   DepthTiling d;
-  const int row = Ny * (int)slot_bytes(Kt, es);
+  const int E = 16 / es;
+  int P = choose_pitch(Ny, Ks, Kt, Kt, es);
+  const int row = row_pitch(Ny, P, es) * es;
   if (row <= target) {
     d.V = Kt;
     d.nV = 1;
-    int J = lfbp_max(1, lfbp_min(Ks, target / row));
+    const int J = lfbp_max(1, lfbp_min(Ks, target / row));
     d.nU = (Ks + J - 1) / J;
     d.J = (Ks + d.nU - 1) / d.nU;
-    d.max_tile_bytes = d.J * row;
   } else {
     d.J = 1;
     d.nU = Ks;
     int nV = (row + target - 1) / target;
     for (;; ++nV) {
       const int V = (Kt + nV - 1) / nV;
-      if (Ny * (int)slot_bytes(V, es) <= target || V == 1) break;
+      const int Pmax = V + 2 * E - 2 + 8 * E;  // largest pitch choose_pitch can return
+      if (row_pitch(Ny, Pmax, es) * es <= target || V == 1) break;
     }
     d.V = (Kt + nV - 1) / nV;
     d.nV = (Kt + d.V - 1) / d.V;
-    d.max_tile_bytes = Ny * (int)slot_bytes(d.V, es);
+    P = choose_pitch(Ny, Ks, Kt, d.V, es);
   }
+  d.P = P;
+  d.RP = row_pitch(Ny, P, es);
+  d.max_tile_bytes = d.J * d.RP * es;
   return d;
 }
 
-// Everything the consumers need about the tile in a stage (filled by the
-// producer lane, read by all consumer threads).
-struct TileInfo {
-  unsigned long long out_run0;    // byte address of output run q = 0, element v0 of row u0
-  unsigned long long run_stride;  // bytes between runs q and q+1 (Ks*Kt*es)
-  int tile;                       // tile index, < 0 = no more work
-  int es, mode;
-  int Nx, Ny, Ks, Kt;
-  int p, u0, v0, nrows, ncols;
-  int L;       // elements per output run = nrows*ncols
-  int NC;      // 16-byte chunks reserved per run (covers any misalignment)
-  int slote;   // slot pitch in elements
-  int ap0;     // (p + u0 - c_s) mod Nx: source cell position of row u0
-  int s0;      // Ks - 1 - u0: source pixel row of row u0
-  int cb;      // (v0 - c_t) mod Ny
-  int om0;     // misalignment (elements mod 16/es) of output run q = 0
-  int kk;      // (Ks*Kt) mod (16/es): misalignment step between q runs / b segments
-  int inm;     // misalignment of the input depth base + t_lo (elements mod 16/es)
-  int nkk;     // (Ny*Ks*Kt) mod (16/es)
-  int ktm;     // Kt mod (16/es)
-  FastDiv fNC, fncols, fNy, fNx;
-};
-
 // ---------------------------------------------------------------- PTX ----
 // Under LFBP_HOST_EMULATION the including translation unit supplies host
-// stand-ins for these primitives (and for the two global-store helpers and
-// the shared-memory index check below), so that the tile code of this header
-// can be run on the CPU with every memory access checked.
+// stand-ins for these primitives (and for the global-store helper and the
+// shared-memory index check below), so that the tile code of this header can
+// be run on the CPU with every memory access checked.
 #ifndef LFBP_HOST_EMULATION
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -198,11 +263,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
   return false;
 }
 
-__device__ __forceinline__ void st_global_16(void* p, uint4 w) {
-  *reinterpret_cast<uint4*>(p) = w;
-}
 template <class T>
-__device__ __forceinline__ void st_global_elem(T* p, T v) {
+__device__ __forceinline__ void st_global(T* p, T v) {
   *p = v;
 }
 #define LFBP_SMEM_CHECK(idx)
@@ -213,74 +275,32 @@ __device__ __forceinline__ int pos_mod(int x, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Producer side: fill `ti` for tile `td` of job `jd` (one thread).
-__device__ __forceinline__ void make_tile_info(TileInfo& ti, int tile, const TileDesc& td,
-                                               const JobDesc& jd, const unsigned char* in_depth,
-                                               unsigned char* out_depth) {
-  const int es = jd.es, E = 16 / es;
-  ti.tile = tile;
-  ti.es = es;
-  ti.mode = jd.mode;
-  ti.Nx = jd.Nx;
-  ti.Ny = jd.Ny;
-  ti.Ks = jd.Ks;
-  ti.Kt = jd.Kt;
-  ti.p = td.p;
-  ti.u0 = td.u0;
-  ti.v0 = td.v0;
-  ti.nrows = td.nrows;
-  ti.ncols = td.ncols;
-  ti.L = td.nrows * td.ncols;
-  ti.NC = (E - 1 + ti.L + E - 1) / E;
-  ti.slote = (int)(slot_bytes(td.ncols, es) / es);
-  const int cs = (jd.Ks - 1) / 2, ct = (jd.Kt - 1) / 2;
-  ti.ap0 = pos_mod(td.p + td.u0 - cs, jd.Nx);
-  ti.s0 = jd.Ks - 1 - td.u0;
-  ti.cb = pos_mod(td.v0 - ct, jd.Ny);
-  const unsigned long long KK = (unsigned long long)jd.Ks * (unsigned long long)jd.Kt;
-  const unsigned long long run0 =
-      ((unsigned long long)td.p * jd.Ny * jd.Ks + td.u0) * jd.Kt + td.v0;  // elements
-  const unsigned long long out0 = (unsigned long long)out_depth + run0 * es;
-  ti.out_run0 = out0;
-  ti.run_stride = KK * es;
-  ti.om0 = (int)((out0 / es) & (E - 1));
-  ti.kk = (int)(KK & (E - 1));
-  const int t_lo = jd.Kt - td.v0 - td.ncols;
-  ti.inm = (int)((((unsigned long long)in_depth / es) + t_lo) & (E - 1));
-  ti.nkk = (int)(((unsigned long long)jd.Ny * KK) & (E - 1));
-  ti.ktm = jd.Kt & (E - 1);
-  ti.fNC = make_fastdiv(ti.NC);
-  ti.fncols = make_fastdiv(td.ncols);
-  ti.fNy = make_fastdiv(jd.Ny);
-  ti.fNx = make_fastdiv(jd.Nx);
-}
-
 // Producer side: issue the bulk copies of the tile's input segments into the
-// stage.  Called by all 32 lanes of one warp; lane 0 arrives on `bar` after
-// every lane has registered its bytes and issued its copies.  The last <16
-// bytes of an array that a 16-byte-widened copy would over-read are copied
-// with ordinary loads instead.
-__device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const JobDesc& jd,
-                                                 const unsigned char* in_depth,
+// stage.  Called by all 32 lanes of one warp; each lane registers the bytes
+// of its own copies on `bar` before issuing them, and lane 0 arrives after
+// every lane is done.  The last <16 bytes of an array that a 16-byte-widened
+// copy would over-read are copied with ordinary loads instead.
+__device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsigned char* in_depth,
                                                  const unsigned char* in_safe_end,
                                                  unsigned char* stage, uint32_t bar, int lane) {
-  const int es = jd.es;
-  const int Ny = jd.Ny, Ks = jd.Ks, Kt = jd.Kt;
+  const int es = (td.flags & 1) ? 2 : 4, E = 16 / es;
+  const int Nx = td.Nx, Ny = td.Ny, Ks = td.Ks, Kt = td.Kt, P = td.P;
+  const int RP = row_pitch(Ny, P, es);
   const int nslots = td.nrows * Ny;
-  const uint32_t sb = slot_bytes(td.ncols, es);
   const int cs = (Ks - 1) / 2;
   const int t_lo = Kt - td.v0 - td.ncols;
   const uint32_t seg_bytes = (uint32_t)td.ncols * es;
-  // pass 1: bytes this lane will bring in with bulk copies
+  const unsigned long long KK = (unsigned long long)Ks * Kt;
+  // pass 1: bytes this lane brings in with bulk copies
   uint32_t my_bytes = 0;
   for (int i = lane; i < nslots; i += 32) {
     const int j = i / Ny, b = i - j * Ny;
-    const int a = pos_mod(td.p + td.u0 + j - cs, jd.Nx);
+    const int a = pos_mod(td.p + td.u0 + j - cs, Nx);
     const int s = Ks - 1 - td.u0 - j;
     const unsigned long long seg = (((unsigned long long)a * Ny + b) * Ks + s) * Kt + t_lo;
-    const unsigned char* src = in_depth + seg * es;
-    const uintptr_t lo = (uintptr_t)src & ~(uintptr_t)15;
-    uintptr_t hi = ((uintptr_t)src + seg_bytes + 15) & ~(uintptr_t)15;
+    const uintptr_t src = (uintptr_t)(in_depth + seg * es);
+    const uintptr_t lo = src & ~(uintptr_t)15;
+    uintptr_t hi = (src + seg_bytes + 15) & ~(uintptr_t)15;
     if (hi > (uintptr_t)in_safe_end) hi = (uintptr_t)in_safe_end;
     if (hi > lo) my_bytes += (uint32_t)(hi - lo);
   }
@@ -288,18 +308,23 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const JobDe
   bool fixed = false;
   for (int i = lane; i < nslots; i += 32) {
     const int j = i / Ny, b = i - j * Ny;
-    const int a = pos_mod(td.p + td.u0 + j - cs, jd.Nx);
+    const int a = pos_mod(td.p + td.u0 + j - cs, Nx);
     const int s = Ks - 1 - td.u0 - j;
-    const unsigned long long seg = (((unsigned long long)a * Ny + b) * Ks + s) * Kt + t_lo;
-    const unsigned char* src = in_depth + seg * es;
-    const uintptr_t lo = (uintptr_t)src & ~(uintptr_t)15;
-    const uintptr_t end = (uintptr_t)src + seg_bytes;
+    const unsigned long long seg0 = (((unsigned long long)a * Ny) * Ks + s) * Kt + t_lo;
+    const unsigned long long seg = seg0 + (unsigned long long)b * KK;
+    const uintptr_t src = (uintptr_t)(in_depth + seg * es);
+    // phases (elements mod E) of segments (j, 0) and (j, b)
+    const int ph0 = (int)((((uintptr_t)in_depth / es) + seg0) & (E - 1));
+    const int phb = (int)((src / es) & (E - 1));
+    const int dst_el = j * RP + ph0 + b * P - phb;  // a multiple of E by the choice of P
+    unsigned char* dst = stage + (size_t)dst_el * es;
+    const uintptr_t lo = src & ~(uintptr_t)15;
+    const uintptr_t end = src + seg_bytes;
     uintptr_t hi = (end + 15) & ~(uintptr_t)15;
-    unsigned char* dst = stage + (size_t)i * sb;
     if (hi > (uintptr_t)in_safe_end) {
       hi = (uintptr_t)in_safe_end > lo ? (uintptr_t)in_safe_end : lo;
       // tail beyond the last full 16-byte block of the array: plain loads
-      for (uintptr_t x = hi > (uintptr_t)src ? hi : (uintptr_t)src; x < end; x += es) {
+      for (uintptr_t x = hi > src ? hi : src; x < end; x += es) {
         if (es == 4)
           *(uint32_t*)(dst + (x - lo)) = __ldg((const unsigned int*)x);
         else
@@ -314,109 +339,194 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const JobDe
   if (lane == 0) mbar_arrive(bar);
 }
 
-// Consumer side: gather the tile from the stage through the index map and
-// write its Ny output runs with 16-byte stores.  Threads [tid0, tid0+nthr)
-// share the work; chunk g = (run q, 16-byte block k of that run).
-template <int ES, int MODE>
-__device__ __forceinline__ void gather_store_tile(const TileInfo& ti, const unsigned char* stage,
-                                                  int tid, int nthr) {
-  using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+// Consumer side: tile constants derived from the descriptor.
+struct TileCtx {
+  const unsigned char* stage;
+  unsigned char* out_run0;  // byte address of run q = 0 at (u0, v0)
+  long long run_stride;     // bytes between runs q and q+1
+  int Nx, Ny, Ks, Kt, ncols, L, P, RP;
+  int p, u0, v0;
+  int cb;    // (v0 - c_t) mod Ny
+  int ap0;   // (p + u0 - c_s) mod Nx
+  int s0;    // Ks - 1 - u0
+  int inm;   // phase (mod E) of the input depth base + t_lo, in elements
+  int nkk;   // (Ny*Ks*Kt) mod E
+  int ktm;   // Kt mod E
+  int om0;   // absolute element index of run q = 0, mod 32/es
+  int kks;   // (Ks*Kt) mod 32/es
+  int sbn;   // (32/es) mod Ny
+  int ngc;   // work items per run
+  int items;
+  FastDiv fncols, fNy, fNx, fngc;
+};
+
+template <int ES>
+__device__ __forceinline__ void make_ctx(TileCtx& c, const TileDesc& td, const unsigned char* stage,
+                                         const unsigned char* in_depth, unsigned char* out_depth) {
+  constexpr int E = 16 / ES, SE = 32 / ES;
+  c.stage = stage;
+  c.Nx = td.Nx;
+  c.Ny = td.Ny;
+  c.Ks = td.Ks;
+  c.Kt = td.Kt;
+  c.ncols = td.ncols;
+  c.L = td.nrows * td.ncols;
+  c.P = td.P;
+  c.RP = row_pitch(td.Ny, td.P, ES);
+  c.p = td.p;
+  c.u0 = td.u0;
+  c.v0 = td.v0;
+  const int cs = (td.Ks - 1) / 2, ct = (td.Kt - 1) / 2;
+  c.cb = pos_mod(td.v0 - ct, td.Ny);
+  c.ap0 = pos_mod(td.p + td.u0 - cs, td.Nx);
+  c.s0 = td.Ks - 1 - td.u0;
+  const unsigned long long KK = (unsigned long long)td.Ks * td.Kt;
+  const int t_lo = td.Kt - td.v0 - td.ncols;
+  c.inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
+  c.nkk = (int)(((unsigned long long)td.Ny * KK) & (E - 1));
+  c.ktm = td.Kt & (E - 1);
+  const unsigned long long run0 =
+      ((unsigned long long)td.p * td.Ny * td.Ks + td.u0) * td.Kt + td.v0;  // elements
+  c.out_run0 = out_depth + run0 * ES;
+  c.run_stride = (long long)(KK * ES);
+  c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (SE - 1));
+  c.kks = (int)(KK & (SE - 1));
+  c.sbn = SE % td.Ny;
+  const int ng = (c.L + 2 * SE - 2) / SE;  // sectors per run, any alignment
+  c.ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
+  c.items = ((td.Ny + 3) >> 2) * c.ngc;
+  c.fncols = make_fastdiv(td.ncols);
+  c.fNy = make_fastdiv(td.Ny);
+  c.fNx = make_fastdiv(td.Nx);
+  c.fngc = make_fastdiv(c.ngc);
+}
+
+// Shared-memory element index of run-element e of run q, computed from
+// scratch; also returns row j, column vl, source b and cell a (for masks).
+template <int ES>
+__device__ __forceinline__ int src_index(const TileCtx& c, int q, int e, int& j, int& vl, int& b,
+                                         int& a) {
   constexpr int E = 16 / ES;
-  const T* sm = reinterpret_cast<const T*>(stage);
-  const int Ny = ti.Ny, Nx = ti.Nx, L = ti.L, NC = ti.NC, ncols = ti.ncols, slote = ti.slote;
-  const int kk = ti.kk, inm = ti.inm, nkk = ti.nkk, ktm = ti.ktm, s0 = ti.s0;
-  const int hx = (Nx - 1) / 2, hy = (Ny - 1) / 2;
-  const int total = Ny * NC;
-  for (int g = tid; g < total; g += nthr) {
-    const int q = (int)fdiv((uint32_t)g, ti.fNC);
-    const int k = g - q * NC;
-    const int m = (ti.om0 + q * kk) & (E - 1);
-    const int e0 = k * E - m;
-    if (e0 >= L) continue;
-    unsigned char* out = reinterpret_cast<unsigned char*>(ti.out_run0 + (unsigned long long)q * ti.run_stride) +
-                         (long long)e0 * ES;
-    const int ef = e0 > 0 ? e0 : 0;
-    int j = (int)fdiv((uint32_t)ef, ti.fncols);
-    int vl = ef - j * ncols;
-    int a = (int)fmod_((uint32_t)(ti.ap0 + j), ti.fNx);
-    int mj = (inm + a * nkk + (s0 - j) * ktm) & (E - 1);
-    const int bq0 = (int)fmod_((uint32_t)(q + ti.cb), ti.fNy);
-    int b = (int)fmod_((uint32_t)(bq0 + vl), ti.fNy);
-    bool rowkeep = true;
-    if (MODE == 1) rowkeep = (ti.p + ti.u0 + j >= hx) && (ti.p + ti.u0 + j <= ti.Ks - 1 + hx);
-    if (MODE == 2) rowkeep = (a + s0 - j >= hx) && (a + s0 - j <= ti.Ks - 1 + hx);
-    T vals[E];
-    uint32_t valid = 0;
+  j = (int)fdiv((uint32_t)e, c.fncols);
+  vl = e - j * c.ncols;
+  a = (int)fmod_((uint32_t)(c.ap0 + j), c.fNx);
+  const int ph = (c.inm + a * c.nkk + (c.s0 - j) * c.ktm) & (E - 1);
+  b = (int)fmod_((uint32_t)(q + c.cb + vl), c.fNy);
+  return j * c.RP + ph + b * c.P + c.ncols - 1 - vl;
+}
+
+template <int MODE>
+__device__ __forceinline__ bool keep_elem(const TileCtx& c, int q, int j, int vl, int b, int a) {
+  if (MODE == 0) return true;
+  const int hx = (c.Nx - 1) >> 1, hy = (c.Ny - 1) >> 1;
+  if (MODE == 1) {  // forward paper window: on the output position (p, u, q, v)
+    const int pu = c.p + c.u0 + j, qv = q + c.v0 + vl;
+    return pu >= hx && pu <= c.Ks - 1 + hx && qv >= hy && qv <= c.Kt - 1 + hy;
+  }
+  // adjoint of the paper window: on the source position (a, s, b, t)
+  const int as = a + c.s0 - j, bt = b + c.Kt - 1 - c.v0 - vl;
+  return as >= hx && as <= c.Ks - 1 + hx && bt >= hy && bt <= c.Kt - 1 + hy;
+}
+
+// Consumer side: gather the tile from the stage through the index map and
+// write its Ny output runs.  `w` is this warp's index among the `nwarps`
+// consumer warps of the CTA.
+template <int ES, int MODE>
+__device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps, int lane) {
+  using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+  constexpr int SE = 32 / ES, EPL = ES == 4 ? 1 : 2;
+  const T* sm = reinterpret_cast<const T*>(c.stage);
+  const int r = lane >> 3, k = lane & 7;
+  const int Ny = c.Ny, L = c.L, P = c.P, ncols = c.ncols;
+  for (int it = w; it < c.items; it += nwarps) {
+    const int qb = (int)fdiv((uint32_t)it, c.fngc);
+    const int gc = it - qb * c.ngc;
+    const int q = qb * 4 + r;
+    if (q >= Ny) continue;
+    const int m = (c.om0 + q * c.kks) & (SE - 1);
+    unsigned char* orow = c.out_run0 + (long long)q * c.run_stride;
+    const int e_begin = gc * (kGroupsPerItem * SE) + k * EPL - m;
+    const int e_last = e_begin + (kGroupsPerItem - 1) * SE + EPL - 1;
+    if (MODE == 0 && e_begin >= 0 && e_last < L) {
+      // fast path: every element of this lane's groups lies inside the run
+      int j, vl, b, a;
+      int idx = src_index<ES>(c, q, e_begin, j, vl, b, a);
+      int base = idx + vl - b * P;  // j*RP + phase_j + ncols - 1
+      int e = e_begin;
 #pragma unroll
-    for (int i = 0; i < E; ++i) {
-      const int e = e0 + i;
-      vals[i] = 0;
-      if (e >= 0 && e < L) {
-        valid |= 1u << i;
-        const int idx = (j * Ny + b) * slote + ((mj + b * kk) & (E - 1)) + ncols - 1 - vl;
-        LFBP_SMEM_CHECK(idx);
-        T x = sm[idx];
-        if (MODE == 1) {
-          const int v = ti.v0 + vl;
-          const bool keep = rowkeep && (q + v >= hy) && (q + v <= ti.Kt - 1 + hy);
-          x = keep ? x : (T)0;
-        } else if (MODE == 2) {
-          const int t = ti.Kt - 1 - ti.v0 - vl;
-          const bool keep = rowkeep && (b + t >= hy) && (b + t <= ti.Kt - 1 + hy);
-          x = keep ? x : (T)0;
+      for (int g = 0; g < kGroupsPerItem; ++g) {
+        const int i0 = base + b * P - vl;
+        LFBP_SMEM_CHECK(i0);
+        const T x0 = sm[i0];
+        if (EPL == 1) {
+          st_global(reinterpret_cast<T*>(orow) + e, x0);
+        } else {
+          int i1;
+          if (vl + 1 < ncols) {
+            const int b1 = b + 1 == Ny ? 0 : b + 1;
+            i1 = base + b1 * P - vl - 1;
+          } else {
+            int j1, vl1, bb, aa;
+            i1 = src_index<ES>(c, q, e + 1, j1, vl1, bb, aa);
+          }
+          LFBP_SMEM_CHECK(i1);
+          const T x1 = sm[i1];
+          st_global(reinterpret_cast<uint32_t*>(orow + (long long)e * ES),
+                    (uint32_t)x0 | ((uint32_t)x1 << 16));
         }
-        vals[i] = x;
-        ++vl;
-        ++b;
-        if (b == Ny) b = 0;
-        if (vl == ncols) {
-          vl = 0;
-          ++j;
-          ++a;
-          if (a == Nx) a = 0;
-          mj = (inm + a * nkk + (s0 - j) * ktm) & (E - 1);
-          b = bq0;
-          if (MODE == 1) rowkeep = (ti.p + ti.u0 + j >= hx) && (ti.p + ti.u0 + j <= ti.Ks - 1 + hx);
-          if (MODE == 2) rowkeep = (a + s0 - j >= hx) && (a + s0 - j <= ti.Ks - 1 + hx);
+        e += SE;
+        vl += SE;
+        b += c.sbn;
+        if (b >= Ny) b -= Ny;
+        if (vl >= ncols && g + 1 < kGroupsPerItem) {
+          idx = src_index<ES>(c, q, e, j, vl, b, a);
+          base = idx + vl - b * P;
         }
       }
-    }
-    if (valid == (1u << E) - 1u) {
-      uint4 w;
-      if (ES == 4) {
-        w.x = vals[0]; w.y = vals[1]; w.z = vals[2]; w.w = vals[3];
-      } else {
-        w.x = (uint32_t)vals[0] | ((uint32_t)vals[1] << 16);
-        w.y = (uint32_t)vals[2] | ((uint32_t)vals[3] << 16);
-        w.z = (uint32_t)vals[4] | ((uint32_t)vals[5] << 16);
-        w.w = (uint32_t)vals[6] | ((uint32_t)vals[7] << 16);
-      }
-      st_global_16(out, w);
     } else {
+      // checked path: run ends, and the paper-window masks
+#pragma unroll 1
+      for (int g = 0; g < kGroupsPerItem; ++g) {
 #pragma unroll
-      for (int i = 0; i < E; ++i)
-        if (valid & (1u << i)) st_global_elem(reinterpret_cast<T*>(out) + i, vals[i]);
+        for (int h = 0; h < EPL; ++h) {
+          const int e = e_begin + g * SE + h;
+          if (e < 0 || e >= L) continue;
+          int j, vl, b, a;
+          const int idx = src_index<ES>(c, q, e, j, vl, b, a);
+          LFBP_SMEM_CHECK(idx);
+          T x = sm[idx];
+          if (!keep_elem<MODE>(c, q, j, vl, b, a)) x = 0;
+          st_global(reinterpret_cast<T*>(orow) + e, x);
+        }
+      }
     }
   }
 }
 
-template <int MODE>
-__device__ __forceinline__ void gather_store_any(const TileInfo& ti, const unsigned char* stage,
-                                                 int tid, int nthr) {
-  if (ti.es == 4)
-    gather_store_tile<4, MODE>(ti, stage, tid, nthr);
+template <int ES>
+__device__ __forceinline__ void gather_tile_es(const TileDesc& td, const unsigned char* stage,
+                                               const unsigned char* in_depth,
+                                               unsigned char* out_depth, int w, int nwarps,
+                                               int lane) {
+  TileCtx c;
+  make_ctx<ES>(c, td, stage, in_depth, out_depth);
+  const int mode = (td.flags >> 1) & 3;
+  if (mode == 0)
+    gather_tile<ES, 0>(c, w, nwarps, lane);
+  else if (mode == 1)
+    gather_tile<ES, 1>(c, w, nwarps, lane);
   else
-    gather_store_tile<2, MODE>(ti, stage, tid, nthr);
+    gather_tile<ES, 2>(c, w, nwarps, lane);
 }
 
-__device__ __forceinline__ void gather_store_dispatch(const TileInfo& ti, const unsigned char* stage,
-                                                      int tid, int nthr) {
-  if (ti.mode == 0)
-    gather_store_any<0>(ti, stage, tid, nthr);
-  else if (ti.mode == 1)
-    gather_store_any<1>(ti, stage, tid, nthr);
+__device__ __forceinline__ void gather_tile_any(const TileDesc& td, const unsigned char* stage,
+                                                const unsigned char* in_depth,
+                                                unsigned char* out_depth, int w, int nwarps,
+                                                int lane) {
+  if (td.flags & 1)
+    gather_tile_es<2>(td, stage, in_depth, out_depth, w, nwarps, lane);
   else
-    gather_store_any<2>(ti, stage, tid, nthr);
+    gather_tile_es<4>(td, stage, in_depth, out_depth, w, nwarps, lane);
 }
 
 }  // namespace lfbp

@@ -85,14 +85,9 @@ static inline void count_store(const unsigned char* p, size_t n) {
   }
   for (size_t i = 0; i < n; ++i) g_counts[(p - g_out) + i]++;
 }
-static inline void st_global_16(void* p, uint4 w) {
-  if ((uintptr_t)p & 15) err("16-byte store misaligned", (uintptr_t)p & 15, 0);
-  count_store((unsigned char*)p, 16);
-  if (g_errors == 0) std::memcpy(p, &w, 16);
-}
 template <class T>
-static inline void st_global_elem(T* p, T v) {
-  if ((uintptr_t)p & (sizeof(T) - 1)) err("element store misaligned", (uintptr_t)p, 0);
+static inline void st_global(T* p, T v) {
+  if ((uintptr_t)p & (sizeof(T) - 1)) err("store misaligned", (long long)((uintptr_t)p & 15), (long long)sizeof(T));
   count_store((unsigned char*)p, sizeof(T));
   if (g_errors == 0) *p = v;
 }
@@ -107,7 +102,7 @@ extern "C" const char* emu_message() { return g_msg; }
 
 // Runs every tile of every depth of one array through the tile code.
 // Returns the number of violations (0 = clean); stats[0] = tiles, stats[1] =
-// bytes copied by bulk copies, stats[2] = max tile bytes.
+// bytes copied by bulk copies, stats[2] = max tile bytes.  nthr = consumer warps.
 extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned char* counts,
                         int Nx, int Ny, int Nz, const int* Ks, const int* Kt, int es, int mode,
                         int target, int nthr, unsigned long long* stats) {
@@ -129,43 +124,43 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
   for (int z = 0; z < Nz && g_errors == 0; ++z) {
     DepthTiling d = tile_depth(Ny, Ks[z], Kt[z], es, target);
     if ((unsigned long long)d.max_tile_bytes > maxb) maxb = d.max_tile_bytes;
-    JobDesc jd;
-    jd.off_bytes = off[z] * es;
-    jd.arr = 0;
-    jd.Nx = Nx;
-    jd.Ny = Ny;
-    jd.Ks = Ks[z];
-    jd.Kt = Kt[z];
-    jd.es = es;
-    jd.mode = mode;
-    jd.pad = 0;
+    TileDesc base;
+    std::memset(&base, 0, sizeof(base));
+    base.off_bytes = off[z] * es;
+    base.Nx = (unsigned short)Nx;
+    base.Ny = (unsigned short)Ny;
+    base.Ks = (unsigned short)Ks[z];
+    base.Kt = (unsigned short)Kt[z];
+    base.P = (unsigned short)d.P;
+    base.flags = (unsigned char)((es == 2 ? 1 : 0) | (mode << 1));
+    if ((d.P - (long long)Ks[z] * Kt[z]) % (16 / es) != 0) err("pitch not congruent to Ks*Kt", d.P, 0);
+    if (d.P < d.V + 2 * (16 / es) - 2) err("pitch too small", d.P, d.V);
     std::vector<unsigned char> stage((size_t)d.max_tile_bytes + 64);
     for (int ub = 0; ub < d.nU; ++ub)
       for (int p = 0; p < Nx; ++p)
         for (int vb = 0; vb < d.nV; ++vb) {
-          TileDesc td;
-          td.job = 0;
+          TileDesc td = base;
           td.p = (unsigned short)p;
           td.u0 = (unsigned short)(ub * d.J);
           td.v0 = (unsigned short)(vb * d.V);
           td.nrows = (unsigned short)lfbp_min(d.J, Ks[z] - ub * d.J);
           td.ncols = (unsigned short)lfbp_min(d.V, Kt[z] - vb * d.V);
-          td.pad = 0;
-          const unsigned tile_bytes = td.nrows * Ny * slot_bytes(td.ncols, es);
+          const unsigned tile_bytes = td.nrows * row_pitch(Ny, d.P, es) * es;
           if ((int)tile_bytes > d.max_tile_bytes) err("tile larger than its depth's maximum", tile_bytes, d.max_tile_bytes);
           std::memset(stage.data(), 0xA5, stage.size());
           g_stage = stage.data();
           g_stage_bytes = tile_bytes;
           g_expect = g_copied = g_arrive = 0;
-          TileInfo ti;
-          const unsigned char* in_depth = in + jd.off_bytes;
-          unsigned char* out_depth = out + jd.off_bytes;
-          make_tile_info(ti, 0, td, jd, in_depth, out_depth);
+          const unsigned char* in_depth = in + base.off_bytes;
+          unsigned char* out_depth = out + base.off_bytes;
           for (int lane = 0; lane < 32; ++lane)
-            issue_tile_loads(td, jd, in_depth, safe_end, stage.data(), 0, lane);
+            issue_tile_loads(td, in_depth, safe_end, stage.data(), 0, lane);
           if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
           if (g_arrive != 1) err("producer arrivals != 1", g_arrive, 0);
-          for (int t = 0; t < nthr; ++t) gather_store_dispatch(ti, stage.data(), t, nthr);
+          const int nwarps = nthr;  // here: number of consumer warps
+          for (int w = 0; w < nwarps; ++w)
+            for (int lane = 0; lane < 32; ++lane)
+              gather_tile_any(td, stage.data(), in_depth, out_depth, w, nwarps, lane);
           ++tiles;
           copied += g_copied;
           if (g_errors) break;

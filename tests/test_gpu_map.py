@@ -206,3 +206,16 @@ def test_ragged_workload_full(lf):
 
 def test_autograd_workload_map(lf):
     _full_workload(lf, "autograd")
+
+
+def test_host_to_host_pipeline(lf):
+    """Pinned host H -> device -> H' -> pinned host, copies overlapped with the map."""
+    for name, dtype in (("mid", torch.float32), ("tiny", torch.float16)):
+        spec = lfgen.config_specs(name)[0]
+        plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, dtype)
+        H = lfgen.generate(spec, device="cuda").to(dtype).cpu().pin_memory()
+        out = lf.backproject_array_host(plan, H)
+        torch.cuda.current_stream().synchronize()
+        lf.sync_status()
+        _assert_same_bits(out, oracle.transpose(H.numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt),
+                          f"host pipeline {name}")

@@ -41,7 +41,7 @@ def _aligned(nbytes, offset=0):
     return raw[base:base + nbytes]
 
 
-def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=256):
+def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=8):
     es = H.itemsize
     nbytes = H.nbytes
     hin = _aligned(nbytes)
@@ -79,6 +79,10 @@ SHAPES = [
     (11, 11, [99, 33], [99, 33], 20000),
     (15, 15, [45, 75], [45, 75], 32768),
     (9, 13, [27, 3, 1], [39, 13, 5], 2048),
+    (9, 9, [27, 45], [27, 45], 32768),       # short rows: pairs and sectors straddle rows
+    (5, 3, [3, 5, 7], [5, 7, 3], 32768),     # rows shorter than a sector
+    (3, 3, [1, 1], [1, 1], 32768),
+    (17, 17, [255], [255], 32768),
 ]
 
 
@@ -111,11 +115,12 @@ def test_tiles_paper_window_and_adjoint(emu, shape, dtype):
     np.testing.assert_array_equal(got2.view(np.uint8), want2.view(np.uint8))
 
 
-def test_thread_count_does_not_matter(emu):
+def test_warp_count_does_not_matter(emu):
     Nx, Ny, Ks, Kt = 5, 3, [15, 9], [9, 21]
     n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
-    H = _random_bits(n, np.float32, 3)
-    want = oracle.transpose(H, Nx, Ny, Ks, Kt)
-    for nthr in (1, 32, 96, 256, 288):
-        got, _ = _run(emu, H, Nx, Ny, Ks, Kt, 0, 2048, nthr)
-        np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+    for dtype in (np.float32, np.float16):
+        H = _random_bits(n, dtype, 3)
+        want = oracle.transpose(H, Nx, Ny, Ks, Kt)
+        for nwarps in (1, 3, 8, 9):
+            got, _ = _run(emu, H, Nx, Ny, Ks, Kt, 0, 2048, nwarps)
+            np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))

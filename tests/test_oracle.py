@@ -265,3 +265,22 @@ def test_gradient_central_differences():
         Hminus[i] -= h
         fd = (loss(Hplus) - loss(Hminus)) / (2 * h)
         assert abs(fd - dh[i]) <= 1e-6 * max(1.0, abs(dh[i])), (i, fd, dh[i])
+
+
+def test_grad_points_match_full():
+    Nx, Ny, Ks, Kt = 3, 5, [9, 15], [5, 25]
+    rng = np.random.default_rng(12)
+    Wx, Wy = 14, 23
+    f = rng.uniform(0, 1, (Wx, Wy))
+    r = rng.uniform(-1, 1, (2, Wx, Wy))
+    full = oracle.grad_hp(f, r, Nx, Ny, Ks, Kt)
+    off = [0, Nx * Ny * Ks[0] * Kt[0]]
+    pts, want = [], []
+    for _ in range(100):
+        z = int(rng.integers(0, 2))
+        p, q = int(rng.integers(0, Nx)), int(rng.integers(0, Ny))
+        u, v = int(rng.integers(0, Ks[z])), int(rng.integers(0, Kt[z]))
+        pts.append((z, p, q, u, v))
+        want.append(full[off[z] + ((p * Ny + q) * Ks[z] + u) * Kt[z] + v])
+    got = oracle.grad_hp_points(f, r, Nx, Ny, Ks, Kt, np.array(pts))
+    np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14)
