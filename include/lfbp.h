@@ -135,6 +135,21 @@ int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* d
                              void* const* dHp, void* cuda_stream);
 
 /*
+ * Autotuner for lfbp_backproject_batched: times a small grid of launch shapes
+ * (shared-memory bytes per tile in {16, 24, 32, 48} KiB x persistent CTAs per
+ * SM in {2, 3, 4}) on the given buffers with CUDA events (reps timed launches
+ * each, after one warm-up) and keeps the fastest for later batched calls with
+ * the same plans (by handle).  Writes H' into dHp as a side effect and
+ * synchronises the stream.  If the environment variable LFBP_TUNE_CACHE names
+ * a file, the choice is appended there, keyed by device name and array
+ * shapes, and later processes take it from there without timing.  tuned
+ * (may be NULL) receives {tile bytes, CTAs per SM, stages (0 = as many as
+ * fit)}.  Arguments otherwise as for lfbp_backproject_batched.
+ */
+int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
+                      void* cuda_stream, int reps, int* tuned);
+
+/*
  * Adjoint of the plan's map, applied to a gradient with respect to H'
  * (dHp_grad) to give the gradient with respect to H (dH_grad).  For
  * LFBP_MAP_TRANSPOSE the map is its own inverse and its own adjoint

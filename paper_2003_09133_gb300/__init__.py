@@ -7,7 +7,7 @@ gather.  PyTorch supplies device memory and streams only.
 """
 from ._lib import (F16, F32, MAP_PAPER_WINDOW, MAP_TRANSPOSE, LfbpError, Plan, adjoint,
                    backproject_array, backproject_array_host, backproject_batched,
-                   backproject_volume_grad,
+                   backproject_volume_grad, tune_batched,
                    forward_project, lib_path, load, sync_status)
 from ._lib import backproject_volume as backproject_volume_raw
 from .autograd import (LFBackproject, LFBackprojectVolume, backprojection_array,
@@ -18,5 +18,5 @@ __all__ = [
     "lib_path", "LfbpError", "LFBackproject", "backprojection_array", "MAP_TRANSPOSE",
     "MAP_PAPER_WINDOW", "F32", "F16", "LFBackprojectVolume", "backproject_volume",
     "backproject_volume_raw", "backproject_volume_grad", "forward_project",
-    "backproject_array_host",
+    "backproject_array_host", "tune_batched",
 ]

@@ -37,6 +37,7 @@ SIGNATURES = {
     "lfbp_backproject_array_host": ([_P, _P, _P, _P, _P, _P], _I),
     "lfbp_backproject_batched": ([_I, _P, _P, _P, _P], _I),
     "lfbp_adjoint": ([_P, _P, _P, _P], _I),
+    "lfbp_tune_batched": ([_I, _P, _P, _P, _P, _I, _P], _I),
     "lfbp_backproject_volume": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_forward_project": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_backproject_volume_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),
@@ -64,9 +65,10 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    check = os.environ.get("LFBP_CHECK", "") == "1"  # the self-checking build
+    path = _build.LIB_CHECK if check else _build.LIB
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(check=check)
     if not os.path.exists(path):
         raise RuntimeError(
             f"lfbp CUDA library not built ({path} missing); run "
@@ -222,6 +224,31 @@ def backproject_batched(plans: Sequence[Plan], Hs: Sequence[torch.Tensor],
                                             ctypes.cast(op, _P), _stream_ptr(stream)),
                "lfbp_backproject_batched")
     return outs
+
+
+def tune_batched(plans: Sequence[Plan], Hs: Sequence[torch.Tensor],
+                 outs: Sequence[torch.Tensor] = None, reps: int = 3, stream=None):
+    """Pick the fastest batched launch shape for these plans (``lfbp_tune_batched``).
+
+    Returns (tile_bytes, ctas_per_sm, stages); later ``backproject_batched``
+    calls with the same plans use it.
+    """
+    n = len(plans)
+    if outs is None:
+        outs = [torch.empty_like(h) for h in Hs]
+    for p, h, o in zip(plans, Hs, outs):
+        _check_tensor(p, h, "H")
+        _check_tensor(p, o, "out")
+    lib = load()
+    hp = (_P * max(1, n))(*[p.handle for p in plans])
+    ip = (_P * max(1, n))(*[h.data_ptr() for h in Hs])
+    op = (_P * max(1, n))(*[o.data_ptr() for o in outs])
+    res = (ctypes.c_int * 3)()
+    with torch.cuda.device(Hs[0].device):
+        _check(lib.lfbp_tune_batched(n, ctypes.cast(hp, _P), ctypes.cast(ip, _P), ctypes.cast(op, _P),
+                                     _stream_ptr(stream), int(reps), ctypes.cast(res, _P)),
+               "lfbp_tune_batched")
+    return tuple(res)
 
 
 def adjoint(plan: Plan, dHp: torch.Tensor, out: torch.Tensor = None, stream=None):

@@ -15,6 +15,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "liblfbp.so")
+# self-checking variant (-DLFBP_CHECK): bounds/alignment checks on every access
+LIB_CHECK = os.path.join(BUILD, "liblfbp_check.so")
 
 SOURCES = ["lfbp.cu", "lfbp_project.cu"]
 HEADERS = ["lfbp_device.cuh"]
@@ -28,23 +30,27 @@ def nvcc_path() -> str:
     return cand
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "lfbp.h")]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Build liblfbp.so if it is missing or older than its sources; return its path."""
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, extra=(), check: bool = False) -> str:
+    """Build liblfbp.so (or the self-checking liblfbp_check.so) if it is missing
+    or older than its sources; return its path."""
+    lib = LIB_CHECK if check else LIB
+    if not force and not _stale(lib):
+        return lib
     os.makedirs(BUILD, exist_ok=True)
     nvcc = nvcc_path()
     objs, procs = [], []
+    if check:
+        extra = list(extra) + ["-DLFBP_CHECK"]
     for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, src.replace(".cu", ".check.o" if check else ".o"))
         cmd = [nvcc, *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj, *extra]
         if verbose:
@@ -57,12 +63,12 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         logs.append(out.decode(errors="replace"))
         if p.returncode != 0:
             raise RuntimeError("nvcc failed:\n" + "\n".join(logs))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
         print("\n".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -32,7 +32,25 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
 constexpr int kConsumerWarps = 8;
 constexpr int kPersistentThreads = 32 * (1 + kConsumerWarps);
-constexpr int kInfoBytes = 64;  // per-stage slot for the tile descriptor
+constexpr int kInfoBytes = 256;  // per-stage slot for the tile descriptor and context
+static_assert(sizeof(TileDesc) + sizeof(TileCtx) <= kInfoBytes, "stage info too large");
+constexpr int kStatusBadLaunch = -9;  // LFBP_ERR_INVALID: launched with too little shared memory
+
+// Dynamic shared memory of the plain kernel for a stage of `stage_bytes`:
+// [stage][mbarrier, 16 B][TileCtx].
+__host__ __device__ constexpr int plain_smem_bytes(int stage_bytes) {
+  return stage_bytes + 16 + kInfoBytes;
+}
+// ... and of the persistent kernel: [stages][per-stage info][full, empty barriers].
+__host__ __device__ constexpr int persistent_smem_bytes(int stage_bytes, int nstages) {
+  return nstages * (stage_bytes + kInfoBytes) + nstages * 16;
+}
+
+__device__ __forceinline__ uint32_t dynamic_smem_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(r));
+  return r;
+}
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, code); }
 
@@ -40,7 +58,7 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, c
 // grid = (nV, Nx, nU) tiles of one depth; block = kPlainThreads; one tile per
 // CTA.  `base` carries the depth's shape, pitch and flags; the CTA fills in
 // its own p, u0, v0, nrows, ncols.
-// smem: [stage: tile bytes][mbarrier]
+// smem: [stage: tile bytes][mbarrier][TileCtx]
 __global__ void __launch_bounds__(kPlainThreads)
     k_gather_depth(TileDesc base, const unsigned char* __restrict__ in_depth,
                    const unsigned char* in_safe_end, unsigned char* __restrict__ out_depth, int J,
@@ -48,8 +66,13 @@ __global__ void __launch_bounds__(kPlainThreads)
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage = smem;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes);
+  TileCtx* ctx = reinterpret_cast<TileCtx*>(smem + stage_bytes + 16);
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (dynamic_smem_size() < (uint32_t)plain_smem_bytes(stage_bytes)) {
+    if (tid == 0) set_status(kStatusBadLaunch);
+    return;
+  }
 
   TileDesc td = base;
   td.p = (unsigned short)blockIdx.y;
@@ -65,6 +88,7 @@ __global__ void __launch_bounds__(kPlainThreads)
     mbar_init(b, 1);
     fence_mbar_init();
   }
+  if (warp == 1 && lane < 8) make_ctx_lane(*ctx, td, stage, in_depth, out_depth, lane);
   __syncthreads();
   if (warp == 0) issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane);
   if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
@@ -74,7 +98,7 @@ __global__ void __launch_bounds__(kPlainThreads)
     mbar_wait_bounded(b, 0, nullptr, kWaitLimitNs);
     return;
   }
-  gather_tile_any(td, stage, in_depth, out_depth, warp, kPlainThreads / 32, lane);
+  gather_tile_ctx(*ctx, warp, kPlainThreads / 32, lane);
 }
 
 // ------------------------------------------------------------- persistent --
@@ -84,16 +108,20 @@ __global__ void __launch_bounds__(kPlainThreads)
 // list).  Warp 0 produces: it prefetches the next descriptor, waits for a free
 // stage, and issues the stage's bulk copies; warps 1..8 consume.
 // smem: [nstages x stage_bytes][nstages x descriptor][full[nstages]][empty[nstages]]
-__global__ void __launch_bounds__(kPersistentThreads, 2)
+__global__ void __launch_bounds__(kPersistentThreads, 3)
     k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
                         const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
                         int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
-  TileDesc* infos = reinterpret_cast<TileDesc*>(smem + (size_t)nstages * stage_bytes);
+  unsigned char* info_base = smem + (size_t)nstages * stage_bytes;  // per stage: flag, TileCtx
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * (stage_bytes + kInfoBytes));
   uint64_t* empty = full + nstages;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (dynamic_smem_size() < (uint32_t)persistent_smem_bytes(stage_bytes, nstages)) {
+    if (tid == 0) set_status(kStatusBadLaunch);
+    return;
+  }
 
   if (tid == 0) {
     abort_flag = 0;
@@ -129,7 +157,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 2)
       }
       if (t >= ntiles) {
         if (lane == 0) {
-          infos[s].pad = 0xffff;  // end of work
+          *reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes) = 1;  // end of work
           mbar_arrive(fb);
         }
         ++it;
@@ -138,9 +166,12 @@ __global__ void __launch_bounds__(kPersistentThreads, 2)
       const unsigned char* in_arr = ptrs.in[td.arr];
       const unsigned char* in_depth = in_arr + td.off_bytes;
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
-      if (lane == 0) {
-        infos[s] = td;
-        infos[s].pad = 0;
+      {
+        unsigned char* info = info_base + (size_t)s * kInfoBytes;
+        if (lane == 0) *reinterpret_cast<int*>(info) = 0;
+        if (lane < 8)
+          make_ctx_lane(*reinterpret_cast<TileCtx*>(info + 16), td, smem + (size_t)s * stage_bytes,
+                        in_depth, ptrs.out[td.arr] + td.off_bytes, lane);
       }
       __syncwarp();
       issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane);
@@ -168,12 +199,9 @@ __global__ void __launch_bounds__(kPersistentThreads, 2)
         }
         break;
       }
-      const TileDesc td = infos[s];
-      if (td.pad == 0xffff) break;
-      const unsigned char* in_depth = ptrs.in[td.arr] + td.off_bytes;
-      unsigned char* out_depth = ptrs.out[td.arr] + td.off_bytes;
-      gather_tile_any(td, smem + (size_t)s * stage_bytes, in_depth, out_depth, cw, kConsumerWarps,
-                      lane);
+      const unsigned char* info = info_base + (size_t)s * kInfoBytes;
+      if (*reinterpret_cast<const int*>(info) != 0) break;
+      gather_tile_ctx(*reinterpret_cast<const TileCtx*>(info + 16), cw, kConsumerWarps, lane);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
     }
@@ -238,7 +266,7 @@ struct Tuning {
 Tuning default_tuning() {
   Tuning t;
   t.tile_bytes = env_int("LFBP_TILE_BYTES", 32768);
-  t.ctas_per_sm = env_int("LFBP_CTAS_PER_SM", 2);
+  t.ctas_per_sm = env_int("LFBP_CTAS_PER_SM", 3);
   t.stages = env_int("LFBP_STAGES", 0);
   if (t.tile_bytes < 1024) t.tile_bytes = 1024;
   if (t.tile_bytes > 65536) t.tile_bytes = 65536;
@@ -314,14 +342,14 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
   const std::vector<DepthTiling>& tl = plan_tiling(p, tu.tile_bytes);
   int max_smem = 0;
   for (int z = z0; z < z1; ++z) max_smem = std::max(max_smem, tl[z].max_tile_bytes);
-  int rc = ensure_smem_attr((const void*)k_gather_depth, max_smem + 16);
+  int rc = ensure_smem_attr((const void*)k_gather_depth, plain_smem_bytes((max_smem + 15) & ~15));
   if (rc) return rc;
   for (int z = z0; z < z1; ++z) {
     const DepthTiling& d = tl[z];
     const TileDesc base = depth_desc(p, z, d, mode, 0);
     dim3 grid(d.nV, p->Nx, d.nU);
     const int smem = (d.max_tile_bytes + 15) & ~15;
-    k_gather_depth<<<grid, kPlainThreads, smem + 16, st>>>(
+    k_gather_depth<<<grid, kPlainThreads, plain_smem_bytes(smem), st>>>(
         base, inb + base.off_bytes, safe_end, outb + base.off_bytes, d.J, d.V, smem);
   }
   cudaError_t e = cudaGetLastError();
@@ -437,6 +465,7 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
 struct BatchState {
   int dev = -1;
   std::vector<unsigned long long> uids;
+  Tuning tuning{0, 0, 0};
   int ntiles = 0;
   int stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
   TileDesc* d_tiles = nullptr;
@@ -453,6 +482,27 @@ struct BatchState {
 };
 
 std::vector<std::unique_ptr<BatchState>> g_batches;  // guarded by g_mu
+
+// Launch shapes chosen by lfbp_tune_batched, per list of plans (by uid).
+struct TunedEntry {
+  int dev;
+  std::vector<unsigned long long> uids;
+  Tuning tuning;
+};
+std::vector<TunedEntry> g_tuned;  // guarded by g_mu
+
+bool same_uids(const std::vector<unsigned long long>& u, int n, const lfbp_plan* plans) {
+  if ((int)u.size() != n) return false;
+  for (int i = 0; i < n; ++i)
+    if (u[i] != plans[i]->uid) return false;
+  return true;
+}
+
+Tuning tuning_for(int dev, int n, const lfbp_plan* plans) {
+  for (const TunedEntry& t : g_tuned)
+    if (t.dev == dev && same_uids(t.uids, n, plans)) return t.tuning;
+  return default_tuning();
+}
 unsigned long long g_clock = 0;
 constexpr size_t kMaxCachedBatches = 8;
 
@@ -495,13 +545,13 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   bs.ntiles = (int)tiles.size();
   bs.stage_bytes = (max_tile + 127) & ~127;
   const int per_cta_budget = std::min(optin, (227 * 1024) / tu.ctas_per_sm - 1024);
-  const int per_stage = bs.stage_bytes + kInfoBytes + 16;
+  const int per_stage = bs.stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
   int nst = per_cta_budget / per_stage;
   if (tu.stages > 0) nst = std::min(nst, tu.stages);
   if (nst < 2) nst = std::min(2, optin / per_stage);
   if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
   bs.nstages = nst;
-  bs.smem = nst * per_stage;
+  bs.smem = persistent_smem_bytes(bs.stage_bytes, nst);
   bs.grid = std::max(1, std::min(sms * tu.ctas_per_sm, bs.ntiles));
   cudaError_t e;
   if (bs.ntiles) {
@@ -553,15 +603,15 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   std::lock_guard<std::mutex> lk(g_mu);
+  const Tuning want = tuning_for(dev, n, plans);
   BatchState* bs = nullptr;
   for (auto& b : g_batches) {
-    if (b->dev != dev || (int)b->uids.size() != n) continue;
-    bool same = true;
-    for (int i = 0; i < n && same; ++i) same = b->uids[i] == plans[i]->uid;
-    if (same) {
-      bs = b.get();
-      break;
-    }
+    if (b->dev != dev || !same_uids(b->uids, n, plans)) continue;
+    if (b->tuning.tile_bytes != want.tile_bytes || b->tuning.ctas_per_sm != want.ctas_per_sm ||
+        b->tuning.stages != want.stages)
+      continue;
+    bs = b.get();
+    break;
   }
   if (!bs) {
     if (g_batches.size() >= kMaxCachedBatches) {
@@ -574,7 +624,8 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     }
     std::unique_ptr<BatchState> nb(new BatchState());
     for (int i = 0; i < n; ++i) nb->uids.push_back(plans[i]->uid);
-    int rc = build_batch(*nb, n, plans, default_tuning());
+    nb->tuning = want;
+    int rc = build_batch(*nb, n, plans, want);
     if (rc) return rc;
     bs = nb.get();
     g_batches.push_back(std::move(nb));
@@ -602,6 +653,128 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
       return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
   }
   if ((e = cudaGraphLaunch(bs->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  return LFBP_OK;
+}
+
+// ------------------------------------------------------------------ tuner --
+// Shape signature of a list of plans (for the tuning cache file).
+std::string plans_signature(int dev, int n, const lfbp_plan* plans) {
+  cudaDeviceProp prop;
+  std::string sig;
+  if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) sig += prop.name;
+  for (int i = 0; i < n; ++i) {
+    lfbp_plan p = plans[i];
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "|%d:%d:%d:%d:%d", p->Nx, p->Ny, p->es, (int)p->mode, p->Nz);
+    sig += buf;
+    unsigned long long h = 1469598103934665603ull;
+    for (int z = 0; z < p->Nz; ++z) {
+      h = (h ^ (unsigned long long)p->Ks[z]) * 1099511628211ull;
+      h = (h ^ (unsigned long long)p->Kt[z]) * 1099511628211ull;
+    }
+    std::snprintf(buf, sizeof(buf), ":%016llx", h);
+    sig += buf;
+  }
+  for (char& ch : sig)
+    if (ch == ' ' || ch == '\n' || ch == '\t') ch = '_';
+  return sig;
+}
+
+bool cache_lookup(const std::string& sig, Tuning* t) {
+  const char* path = std::getenv("LFBP_TUNE_CACHE");
+  if (!path || !*path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char key[4096];
+  Tuning x{0, 0, 0};
+  bool found = false;
+  while (std::fscanf(f, "%4095s %d %d %d", key, &x.tile_bytes, &x.ctas_per_sm, &x.stages) == 4)
+    if (sig == key) {
+      *t = x;
+      found = true;
+    }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const std::string& sig, const Tuning& t) {
+  const char* path = std::getenv("LFBP_TUNE_CACHE");
+  if (!path || !*path || sig.size() > 4000) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %d\n", sig.c_str(), t.tile_bytes, t.ctas_per_sm, t.stages);
+  std::fclose(f);
+}
+
+int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* const* out,
+                 cudaStream_t st, int reps, Tuning* chosen) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  const std::string sig = plans_signature(dev, n, plans);
+  Tuning best = default_tuning();
+  if (!cache_lookup(sig, &best)) {
+    const int tiles[] = {16384, 24576, 32768, 49152};
+    const int ctas[] = {2, 3, 4};
+    float best_ms = 1e30f;
+    cudaEvent_t a, b;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    BatchPtrs np;
+    std::memset(&np, 0, sizeof(np));
+    for (int i = 0; i < n; ++i) {
+      np.in[i] = (const unsigned char*)in[i];
+      np.out[i] = (unsigned char*)out[i];
+      np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
+    }
+    int rc = LFBP_OK;
+    for (int tb : tiles)
+      for (int cp : ctas) {
+        Tuning t{tb, cp, 0};
+        BatchState bs;
+        if (build_batch(bs, n, plans, t) != LFBP_OK || bs.nstages < 2) continue;
+        if (bs.ntiles == 0) continue;
+        const int smem = bs.smem;
+        for (int r = 0; r <= reps; ++r) {
+          if (r == 1) cudaEventRecord(a, st);
+          k_gather_persistent<<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.ntiles,
+                                                                         bs.stage_bytes, bs.nstages);
+        }
+        cudaEventRecord(b, st);
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
+          rc = cuda_fail(e, "tuning launch");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= (float)(reps > 0 ? reps : 1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    cache_store(sig, best);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    bool done = false;
+    for (TunedEntry& t : g_tuned)
+      if (t.dev == dev && same_uids(t.uids, n, plans)) {
+        t.tuning = best;
+        done = true;
+      }
+    if (!done) {
+      TunedEntry te;
+      te.dev = dev;
+      for (int i = 0; i < n; ++i) te.uids.push_back(plans[i]->uid);
+      te.tuning = best;
+      g_tuned.push_back(te);
+    }
+  }
+  if (chosen) *chosen = best;
   return LFBP_OK;
 }
 
@@ -676,6 +849,14 @@ void lfbp_plan_destroy(lfbp_plan p) {
   if (!p) return;
   {
     std::lock_guard<std::mutex> lk(g_mu);
+    for (size_t i = 0; i < g_tuned.size();) {
+      bool uses = false;
+      for (auto u : g_tuned[i].uids) uses |= (u == p->uid);
+      if (uses)
+        g_tuned.erase(g_tuned.begin() + i);
+      else
+        ++i;
+    }
     for (size_t i = 0; i < g_batches.size();) {
       bool uses = false;
       for (auto u : g_batches[i]->uids) uses |= (u == p->uid);
@@ -711,6 +892,22 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream) {
   return run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);
+}
+
+int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
+                      void* cuda_stream, int reps, int* tuned) {
+  int rc = run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);  // validates the arguments
+  if (rc) return rc;
+  if (n == 0) return LFBP_OK;
+  Tuning t{0, 0, 0};
+  rc = tune_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, reps < 1 ? 3 : reps, &t);
+  if (rc) return rc;
+  if (tuned) {
+    tuned[0] = t.tile_bytes;
+    tuned[1] = t.ctas_per_sm;
+    tuned[2] = t.stages;
+  }
+  return LFBP_OK;
 }
 
 int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_stream) {
@@ -772,19 +969,44 @@ int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgra
 int lfbp_sync_status(void* cuda_stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)cuda_stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+#if LFBP_CHECKED
+  {
+    CheckWord cw;
+    if ((e = cudaMemcpyFromSymbol(&cw, g_check, sizeof(cw))) != cudaSuccess)
+      return cuda_fail(e, "read check word");
+    if (cw.code != 0) {
+      CheckWord zero;
+      std::memset(&zero, 0, sizeof(zero));
+      cudaMemcpyToSymbol(g_check, &zero, sizeof(zero));
+      char msg[256];
+      std::snprintf(msg, sizeof(msg),
+                    "self-check violation: code %d (1 smem load, 2 store, 3 bulk copy, 4 tail "
+                    "load) block %d thread %d values %lld %lld",
+                    cw.code, cw.block, cw.thread, cw.a, cw.b);
+      return fail(LFBP_ERR_INVALID, msg);
+    }
+  }
+#endif
   int v = 0;
   if ((e = cudaMemcpyFromSymbol(&v, g_status, sizeof(int))) != cudaSuccess)
     return cuda_fail(e, "read status");
   if (v != 0) {
     const int zero = 0;
     cudaMemcpyToSymbol(g_status, &zero, sizeof(int));
-    return fail(v, "an in-kernel wait timed out; output incomplete");
+    return fail(v, v == LFBP_ERR_TIMEOUT ? "an in-kernel wait timed out; output incomplete"
+                                         : "a kernel was launched with too little shared memory");
   }
   return LFBP_OK;
 }
 
 const char* lfbp_last_error(void) { return t_err.c_str(); }
 
-const char* lfbp_version(void) { return "lfbp 0.1 (sm_103a)"; }
+const char* lfbp_version(void) {
+#if LFBP_CHECKED
+  return "lfbp 0.1 (sm_103a, self-checking build)";
+#else
+  return "lfbp 0.1 (sm_103a)";
+#endif
+}
 
 }  // extern "C"

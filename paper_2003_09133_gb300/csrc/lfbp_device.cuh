@@ -36,7 +36,7 @@ namespace lfbp {
 
 constexpr int kMaxBatch = 64;       // arrays per batched launch
 constexpr int kStatusTimeout = -7;  // LFBP_ERR_TIMEOUT
-constexpr int kGroupsPerItem = 4;   // sectors per run handled by one consumer work item
+constexpr int kGroupsPerItem = 8;   // sectors per run handled by one consumer work item
 
 // One tile, self-contained (32 bytes).
 struct TileDesc {
@@ -63,7 +63,7 @@ struct FastDiv {
 __host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
   FastDiv f;
   f.d = d;
-  f.m = d > 1 ? (uint32_t)((0x100000000ull + d - 1) / d) : 0u;
+  f.m = d > 1 ? 0xffffffffu / d + 1u : 0u;  // ceil(2^32 / d)
   return f;
 }
 __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) {
@@ -76,8 +76,8 @@ inline int lfbp_max(int a, int b) { return a > b ? a : b; }
 
 // Row pitch (elements) of a tile whose slots have pitch P.
 __host__ __device__ inline int row_pitch(int Ny, int P, int es) {
-  const int E = 16 / es;
-  return ((Ny * P + E - 1) / E) * E;
+  const int sh = es == 4 ? 2 : 3;  // log2(16 / es)
+  return ((Ny * P + (1 << sh) - 1) >> sh) << sh;
 }
 
 // ------------------------------------------------------------ host planning --
@@ -85,7 +85,7 @@ __host__ __device__ inline int row_pitch(int Ny, int P, int es) {
 // over pseudo-random run phases and positions (the phases depend on buffer
 // addresses unknown at planning time).  Mirrors the consumer's lane mapping.
 inline double pitch_cost(int Ny, int Ks, int Kt, int ncols, int es, int P) {
-  const int SE = 32 / es, epl = es == 4 ? 1 : 2, E = 16 / es;
+  const int epl = 16 / es, SE = 8 * epl, E = 16 / es;
   const long long KK = (long long)Ks * Kt;
   const int ct = (Kt - 1) / 2;
   const int cb = ((0 - ct) % Ny + Ny) % Ny;
@@ -267,8 +267,70 @@ template <class T>
 __device__ __forceinline__ void st_global(T* p, T v) {
   *p = v;
 }
+template <class T>
+__device__ __forceinline__ T lds(uint32_t addr);
+template <>
+__device__ __forceinline__ uint32_t lds<uint32_t>(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+template <>
+__device__ __forceinline__ uint16_t lds<uint16_t>(uint32_t addr) {
+  uint16_t v;
+  asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
+  return v;
+}
+// shared-memory load at a compile-time byte offset from a 32-bit address
+template <class T, int OFF>
+__device__ __forceinline__ T lds_off(uint32_t addr) {
+  if constexpr (sizeof(T) == 4) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+    return v;
+  } else {
+    uint16_t v;
+    asm volatile("ld.shared.u16 %0, [%1+%2];" : "=h"(v) : "r"(addr), "n"(OFF));
+    return v;
+  }
+}
 #define LFBP_SMEM_CHECK(idx)
 #endif  // LFBP_HOST_EMULATION
+
+// Self-checking build (LFBP_CHECK): every shared-memory load, global store and
+// bulk copy of the tile code is checked against its buffer; the first
+// violation is recorded in g_check (read by lfbp_sync_status) and the access
+// is skipped.  No trap, no fault: a bad index costs a wrong value, not the GPU.
+#if defined(LFBP_CHECK) && !defined(LFBP_HOST_EMULATION)
+struct CheckWord {
+  int code;  // 1 smem load, 2 global store, 3 bulk copy, 4 tail load
+  int thread;
+  int block;
+  int pad;
+  long long a, b;
+};
+static __device__ CheckWord g_check;
+__device__ __forceinline__ void check_fail(int code, long long a, long long b) {
+  if (atomicCAS(&g_check.code, 0, code) == 0) {
+    g_check.thread = threadIdx.x;
+    g_check.block = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    g_check.a = a;
+    g_check.b = b;
+  }
+}
+#define LFBP_CHECKED 1
+#else
+#define LFBP_CHECKED 0
+#endif
+
+// f(std::integral_constant<int, I>) for I = B .. E-1, unrolled at compile time
+template <int B, int E, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 __device__ __forceinline__ int pos_mod(int x, int n) {
   int r = x % n;
@@ -276,10 +338,11 @@ __device__ __forceinline__ int pos_mod(int x, int n) {
 }
 
 // Producer side: issue the bulk copies of the tile's input segments into the
-// stage.  Called by all 32 lanes of one warp; each lane registers the bytes
-// of its own copies on `bar` before issuing them, and lane 0 arrives after
-// every lane is done.  The last <16 bytes of an array that a 16-byte-widened
-// copy would over-read are copied with ordinary loads instead.
+// stage.  Called by all 32 lanes of one warp; lane i takes slots i, i+32, ...
+// (slot = j*Ny + b).  Each lane registers the bytes of its own copies on
+// `bar` before issuing them, and lane 0 arrives after every lane is done.
+// The last <16 bytes of an array that a 16-byte-widened copy would over-read
+// are copied with ordinary loads instead.
 __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsigned char* in_depth,
                                                  const unsigned char* in_safe_end,
                                                  unsigned char* stage, uint32_t bar, int lane) {
@@ -291,13 +354,23 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
   const int t_lo = Kt - td.v0 - td.ncols;
   const uint32_t seg_bytes = (uint32_t)td.ncols * es;
   const unsigned long long KK = (unsigned long long)Ks * Kt;
-  // pass 1: bytes this lane brings in with bulk copies
+  const unsigned long long NKK = (unsigned long long)Ny * KK;
+  const FastDiv fNy = make_fastdiv(Ny), fNx = make_fastdiv(Nx);
+  const int a0 = pos_mod(td.p + td.u0 - cs, Nx);
+  const uintptr_t in_el = (uintptr_t)in_depth / es;
+#if LFBP_CHECKED
+  const int nrows_bytes = td.nrows * RP * es;
+  const unsigned char* in_array = in_depth - td.off_bytes;
+#endif
+  // slot i = (row j, segment b): row j reads H[a_j][b][s_j][t_lo..], with
+  // a_j = (p + u0 + j - c_s) mod Nx and s_j = Ks - 1 - u0 - j
   uint32_t my_bytes = 0;
   for (int i = lane; i < nslots; i += 32) {
-    const int j = i / Ny, b = i - j * Ny;
-    const int a = pos_mod(td.p + td.u0 + j - cs, Nx);
-    const int s = Ks - 1 - td.u0 - j;
-    const unsigned long long seg = (((unsigned long long)a * Ny + b) * Ks + s) * Kt + t_lo;
+    const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
+    const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
+    const unsigned long long seg =
+        (unsigned long long)a * NKK + (unsigned long long)b * KK +
+        (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
     const uintptr_t src = (uintptr_t)(in_depth + seg * es);
     const uintptr_t lo = src & ~(uintptr_t)15;
     uintptr_t hi = (src + seg_bytes + 15) & ~(uintptr_t)15;
@@ -307,15 +380,15 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
   if (my_bytes) mbar_expect_tx(bar, my_bytes);
   bool fixed = false;
   for (int i = lane; i < nslots; i += 32) {
-    const int j = i / Ny, b = i - j * Ny;
-    const int a = pos_mod(td.p + td.u0 + j - cs, Nx);
-    const int s = Ks - 1 - td.u0 - j;
-    const unsigned long long seg0 = (((unsigned long long)a * Ny) * Ks + s) * Kt + t_lo;
+    const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
+    const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
+    const unsigned long long seg0 =
+        (unsigned long long)a * NKK + (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
     const unsigned long long seg = seg0 + (unsigned long long)b * KK;
     const uintptr_t src = (uintptr_t)(in_depth + seg * es);
     // phases (elements mod E) of segments (j, 0) and (j, b)
-    const int ph0 = (int)((((uintptr_t)in_depth / es) + seg0) & (E - 1));
-    const int phb = (int)((src / es) & (E - 1));
+    const int ph0 = (int)((in_el + seg0) & (E - 1));
+    const int phb = (int)((in_el + seg) & (E - 1));
     const int dst_el = j * RP + ph0 + b * P - phb;  // a multiple of E by the choice of P
     unsigned char* dst = stage + (size_t)dst_el * es;
     const uintptr_t lo = src & ~(uintptr_t)15;
@@ -325,6 +398,13 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
       hi = (uintptr_t)in_safe_end > lo ? (uintptr_t)in_safe_end : lo;
       // tail beyond the last full 16-byte block of the array: plain loads
       for (uintptr_t x = hi > src ? hi : src; x < end; x += es) {
+#if LFBP_CHECKED
+        if ((long long)(dst - stage) + (long long)(x - lo) + es > (long long)nrows_bytes ||
+            x < (uintptr_t)in_array || x + es > (uintptr_t)in_safe_end + 16) {
+          check_fail(4, (long long)(dst - stage) + (long long)(x - lo), (long long)nrows_bytes);
+          continue;
+        }
+#endif
         if (es == 4)
           *(uint32_t*)(dst + (x - lo)) = __ldg((const unsigned int*)x);
         else
@@ -332,6 +412,14 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
       }
       fixed = true;
     }
+#if LFBP_CHECKED
+    if (hi > lo && (dst < stage || (long long)(dst - stage) + (long long)(hi - lo) > (long long)nrows_bytes ||
+                    ((uintptr_t)dst & 15) || (lo & 15) || ((hi - lo) & 15) ||
+                    lo < (uintptr_t)in_array || hi > (uintptr_t)in_safe_end)) {
+      check_fail(3, (long long)(dst - stage), (long long)(hi - lo));
+      continue;
+    }
+#endif
     if (hi > lo) bulk_g2s(smem_addr(dst), (const void*)lo, (uint32_t)(hi - lo), bar);
   }
   if (fixed) fence_proxy_async_smem();
@@ -339,11 +427,18 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
   if (lane == 0) mbar_arrive(bar);
 }
 
-// Consumer side: tile constants derived from the descriptor.
-struct TileCtx {
-  const unsigned char* stage;
+// Tile constants derived from the descriptor: computed once per tile by the
+// eight lanes of one warp (make_ctx_lane) into shared memory, and copied into
+// registers by every consumer thread before its gather loop (a copy in
+// registers cannot be aliased by the gather's global stores, so it is not
+// re-read after each store).
+struct alignas(16) TileCtx {
+  uint32_t stage_s;         // shared-memory address of the stage
+  int tile_bytes;           // bytes of the tile's stage
   unsigned char* out_run0;  // byte address of run q = 0 at (u0, v0)
   long long run_stride;     // bytes between runs q and q+1
+  unsigned char* out_lo;    // the depth's output bytes [out_lo, out_hi)
+  unsigned char* out_hi;
   int Nx, Ny, Ks, Kt, ncols, L, P, RP;
   int p, u0, v0;
   int cb;    // (v0 - c_t) mod Ny
@@ -352,53 +447,158 @@ struct TileCtx {
   int inm;   // phase (mod E) of the input depth base + t_lo, in elements
   int nkk;   // (Ny*Ks*Kt) mod E
   int ktm;   // Kt mod E
-  int om0;   // absolute element index of run q = 0, mod 32/es
-  int kks;   // (Ks*Kt) mod 32/es
-  int sbn;   // (32/es) mod Ny
+  int om0;   // absolute element index of run q = 0, mod 128/es
+  int kks;   // (Ks*Kt) mod 128/es
+  int sbn;   // (128/es) mod Ny
   int ngc;   // work items per run
   int items;
+  int es, mode;
   FastDiv fncols, fNy, fNx, fngc;
 };
 
-template <int ES>
+// Lane `lane` (0..7) of a warp fills its share of the tile context; the
+// shares are independent, so the eight lanes run the divisions in parallel.
+__device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
+                                              const unsigned char* stage,
+                                              const unsigned char* in_depth,
+                                              unsigned char* out_depth, int lane) {
+  const int ES = (td.flags & 1) ? 2 : 4;
+  const int E = 16 / ES, GE = 128 / ES;  // GE: elements per run per gather group
+  const unsigned long long KK = (unsigned long long)td.Ks * td.Kt;
+  const int L = td.nrows * td.ncols;
+  switch (lane) {
+    case 0:
+      c.es = ES;
+      c.mode = (td.flags >> 1) & 3;
+      c.stage_s = smem_addr(stage);
+      c.Nx = td.Nx;
+      c.Ny = td.Ny;
+      c.Ks = td.Ks;
+      c.Kt = td.Kt;
+      c.ncols = td.ncols;
+      c.L = L;
+      c.P = td.P;
+      c.RP = row_pitch(td.Ny, td.P, ES);
+      c.tile_bytes = td.nrows * c.RP * ES;
+      c.p = td.p;
+      c.u0 = td.u0;
+      c.v0 = td.v0;
+      c.s0 = td.Ks - 1 - td.u0;
+      break;
+    case 1:
+      c.fncols = make_fastdiv(td.ncols);
+      break;
+    case 2:
+      c.fNy = make_fastdiv(td.Ny);
+      c.sbn = GE % td.Ny;
+      break;
+    case 3:
+      c.fNx = make_fastdiv(td.Nx);
+      break;
+    case 4: {
+      const int ng = (L + 2 * GE - 2) / GE;  // groups per run, any alignment
+      const int ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
+      c.ngc = ngc;
+      c.items = ((td.Ny + 3) >> 2) * ngc;
+      c.fngc = make_fastdiv(ngc);
+      break;
+    }
+    case 5:
+      c.cb = pos_mod((int)td.v0 - (td.Kt - 1) / 2, td.Ny);
+      c.ap0 = pos_mod((int)td.p + (int)td.u0 - (td.Ks - 1) / 2, td.Nx);
+      break;
+    case 6: {
+      const unsigned long long run0 =
+          ((unsigned long long)td.p * td.Ny * td.Ks + td.u0) * td.Kt + td.v0;  // elements
+      c.out_run0 = out_depth + run0 * ES;
+      c.run_stride = (long long)(KK * ES);
+      c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (GE - 1));
+      c.kks = (int)(KK & (GE - 1));
+      c.out_lo = out_depth;
+      c.out_hi = out_depth + (unsigned long long)td.Nx * td.Ny * KK * ES;
+      break;
+    }
+    case 7: {
+      const int t_lo = td.Kt - td.v0 - td.ncols;
+      c.inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
+      c.nkk = (int)(((unsigned long long)td.Ny * KK) & (E - 1));
+      c.ktm = td.Kt & (E - 1);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// The whole context from one thread (used where no warp is at hand).
 __device__ __forceinline__ void make_ctx(TileCtx& c, const TileDesc& td, const unsigned char* stage,
                                          const unsigned char* in_depth, unsigned char* out_depth) {
-  constexpr int E = 16 / ES, SE = 32 / ES;
-  c.stage = stage;
-  c.Nx = td.Nx;
-  c.Ny = td.Ny;
-  c.Ks = td.Ks;
-  c.Kt = td.Kt;
-  c.ncols = td.ncols;
-  c.L = td.nrows * td.ncols;
-  c.P = td.P;
-  c.RP = row_pitch(td.Ny, td.P, ES);
-  c.p = td.p;
-  c.u0 = td.u0;
-  c.v0 = td.v0;
-  const int cs = (td.Ks - 1) / 2, ct = (td.Kt - 1) / 2;
-  c.cb = pos_mod(td.v0 - ct, td.Ny);
-  c.ap0 = pos_mod(td.p + td.u0 - cs, td.Nx);
-  c.s0 = td.Ks - 1 - td.u0;
-  const unsigned long long KK = (unsigned long long)td.Ks * td.Kt;
-  const int t_lo = td.Kt - td.v0 - td.ncols;
-  c.inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
-  c.nkk = (int)(((unsigned long long)td.Ny * KK) & (E - 1));
-  c.ktm = td.Kt & (E - 1);
-  const unsigned long long run0 =
-      ((unsigned long long)td.p * td.Ny * td.Ks + td.u0) * td.Kt + td.v0;  // elements
-  c.out_run0 = out_depth + run0 * ES;
-  c.run_stride = (long long)(KK * ES);
-  c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (SE - 1));
-  c.kks = (int)(KK & (SE - 1));
-  c.sbn = SE % td.Ny;
-  const int ng = (c.L + 2 * SE - 2) / SE;  // sectors per run, any alignment
-  c.ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
-  c.items = ((td.Ny + 3) >> 2) * c.ngc;
-  c.fncols = make_fastdiv(td.ncols);
-  c.fNy = make_fastdiv(td.Ny);
-  c.fNx = make_fastdiv(td.Nx);
-  c.fngc = make_fastdiv(c.ngc);
+  for (int l = 0; l < 8; ++l) make_ctx_lane(c, td, stage, in_depth, out_depth, l);
+}
+
+template <class T>
+__device__ __forceinline__ T smem_load(const TileCtx& c, int idx) {
+#if LFBP_CHECKED
+  if (idx < 0 || (long long)(idx + 1) * (long long)sizeof(T) > c.tile_bytes) {
+    check_fail(1, idx, c.tile_bytes);
+    return (T)0;
+  }
+#endif
+  return lds<T>(c.stage_s + (uint32_t)idx * (uint32_t)sizeof(T));
+}
+
+template <class T, int OFF>
+__device__ __forceinline__ T smem_load_off(const TileCtx& c, uint32_t addr) {
+#if LFBP_CHECKED
+  const long long rel = (long long)addr + OFF - (long long)c.stage_s;
+  if (rel < 0 || rel + (long long)sizeof(T) > c.tile_bytes) {
+    check_fail(1, rel, c.tile_bytes);
+    return (T)0;
+  }
+#endif
+  (void)c;
+  return lds_off<T, OFF>(addr);
+}
+
+__device__ __forceinline__ uint4 pack16(const uint32_t (&v)[4]) {
+  uint4 w;
+  w.x = v[0];
+  w.y = v[1];
+  w.z = v[2];
+  w.w = v[3];
+  return w;
+}
+__device__ __forceinline__ uint4 pack16(const uint16_t (&v)[8]) {
+  uint4 w;
+  w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 16);
+  w.y = (uint32_t)v[2] | ((uint32_t)v[3] << 16);
+  w.z = (uint32_t)v[4] | ((uint32_t)v[5] << 16);
+  w.w = (uint32_t)v[6] | ((uint32_t)v[7] << 16);
+  return w;
+}
+
+__device__ __forceinline__ void store_out16(const TileCtx& c, unsigned char* p, uint4 v) {
+#if LFBP_CHECKED
+  if (p < c.out_lo || p + 16 > c.out_hi || ((uintptr_t)p & 15)) {
+    check_fail(2, (long long)(p - c.out_lo), (long long)(c.out_hi - c.out_lo));
+    return;
+  }
+#endif
+  (void)c;
+  st_global(reinterpret_cast<uint4*>(p), v);
+}
+
+template <class T>
+__device__ __forceinline__ void store_out(const TileCtx& c, T* p, T v) {
+#if LFBP_CHECKED
+  const unsigned char* b = reinterpret_cast<const unsigned char*>(p);
+  if (b < c.out_lo || b + sizeof(T) > c.out_hi || ((uintptr_t)b & (sizeof(T) - 1))) {
+    check_fail(2, (long long)(b - c.out_lo), (long long)(c.out_hi - c.out_lo));
+    return;
+  }
+#endif
+  (void)c;
+  st_global(p, v);
 }
 
 // Shared-memory element index of run-element e of run q, computed from
@@ -429,104 +629,104 @@ __device__ __forceinline__ bool keep_elem(const TileCtx& c, int q, int j, int vl
 }
 
 // Consumer side: gather the tile from the stage through the index map and
-// write its Ny output runs.  `w` is this warp's index among the `nwarps`
-// consumer warps of the CTA.
+// write its Ny output runs with 16-byte stores.  `w` is this warp's index
+// among the `nwarps` consumer warps of the CTA.  Work item = 4 runs x
+// kGroupsPerItem groups; a group is one 128-byte stretch of a run, 16 bytes
+// per lane.  Inside a row, consecutive output elements walk the diagonal
+// b -> b+1 (mod Ny), t -> t-1, i.e. one IMAD per element for the address.
 template <int ES, int MODE>
 __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps, int lane) {
   using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
-  constexpr int SE = 32 / ES, EPL = ES == 4 ? 1 : 2;
-  const T* sm = reinterpret_cast<const T*>(c.stage);
+  constexpr int EPL = 16 / ES;  // elements per lane and group (one 16-byte store)
+  constexpr int GE = 8 * EPL;   // elements per run and group (128 bytes)
   const int r = lane >> 3, k = lane & 7;
   const int Ny = c.Ny, L = c.L, P = c.P, ncols = c.ncols;
+  const uint32_t PES = (uint32_t)P * ES;
   for (int it = w; it < c.items; it += nwarps) {
     const int qb = (int)fdiv((uint32_t)it, c.fngc);
     const int gc = it - qb * c.ngc;
     const int q = qb * 4 + r;
     if (q >= Ny) continue;
-    const int m = (c.om0 + q * c.kks) & (SE - 1);
+    const int m = (c.om0 + q * c.kks) & (GE - 1);
     unsigned char* orow = c.out_run0 + (long long)q * c.run_stride;
-    const int e_begin = gc * (kGroupsPerItem * SE) + k * EPL - m;
-    const int e_last = e_begin + (kGroupsPerItem - 1) * SE + EPL - 1;
-    if (MODE == 0 && e_begin >= 0 && e_last < L) {
-      // fast path: every element of this lane's groups lies inside the run
-      int j, vl, b, a;
-      int idx = src_index<ES>(c, q, e_begin, j, vl, b, a);
-      int base = idx + vl - b * P;  // j*RP + phase_j + ncols - 1
-      int e = e_begin;
-#pragma unroll
-      for (int g = 0; g < kGroupsPerItem; ++g) {
-        const int i0 = base + b * P - vl;
-        LFBP_SMEM_CHECK(i0);
-        const T x0 = sm[i0];
-        if (EPL == 1) {
-          st_global(reinterpret_cast<T*>(orow) + e, x0);
-        } else {
-          int i1;
-          if (vl + 1 < ncols) {
-            const int b1 = b + 1 == Ny ? 0 : b + 1;
-            i1 = base + b1 * P - vl - 1;
-          } else {
-            int j1, vl1, bb, aa;
-            i1 = src_index<ES>(c, q, e + 1, j1, vl1, bb, aa);
-          }
-          LFBP_SMEM_CHECK(i1);
-          const T x1 = sm[i1];
-          st_global(reinterpret_cast<uint32_t*>(orow + (long long)e * ES),
-                    (uint32_t)x0 | ((uint32_t)x1 << 16));
+    int e = gc * (kGroupsPerItem * GE) + k * EPL - m;  // this lane's first element
+    // incremental state at element e: row j, column vl, source segment b, and
+    // X = byte address of (row base + ncols - 1 - vl) - (EPL-1)*ES in shared memory
+    bool have = false;
+    int vl = 0, b = 0;
+    uint32_t X = 0;
+#pragma unroll 1
+    for (int g = 0; g < kGroupsPerItem; ++g, e += GE) {
+      if (e >= L) break;
+      const bool full = e >= 0 && e + EPL <= L;
+      if (MODE == 0 && full && (!have || vl + EPL <= ncols)) {
+        if (!have) {
+          int j, a;
+          const int idx = src_index<ES>(c, q, e, j, vl, b, a);
+          X = c.stage_s + (uint32_t)(idx - b * P - (EPL - 1)) * ES;
+          have = true;
         }
-        e += SE;
-        vl += SE;
-        b += c.sbn;
-        if (b >= Ny) b -= Ny;
-        if (vl >= ncols && g + 1 < kGroupsPerItem) {
-          idx = src_index<ES>(c, q, e, j, vl, b, a);
-          base = idx + vl - b * P;
+        if (vl + EPL <= ncols) {
+          T v[EPL];
+          int bb = b;
+          static_for<0, EPL>([&](auto ic) {
+            constexpr int i = decltype(ic)::value;
+            v[i] = smem_load_off<T, (EPL - 1 - i) * ES>(c, (uint32_t)bb * PES + X);
+            bb = bb + 1 == Ny ? 0 : bb + 1;
+          });
+          store_out16(c, orow + (long long)e * ES, pack16(v));
+        } else {
+          T v[EPL];
+#pragma unroll
+          for (int i = 0; i < EPL; ++i) {
+            int jj, vv, bb, aa;
+            v[i] = smem_load<T>(c, src_index<ES>(c, q, e + i, jj, vv, bb, aa));
+          }
+          store_out16(c, orow + (long long)e * ES, pack16(v));
+        }
+      } else {
+        // run ends (partial groups) and the paper-window masks: element by element
+#pragma unroll
+        for (int i = 0; i < EPL; ++i) {
+          const int ee = e + i;
+          if (ee < 0 || ee >= L) continue;
+          int jj, vv, bb, aa;
+          T x = smem_load<T>(c, src_index<ES>(c, q, ee, jj, vv, bb, aa));
+          if (!keep_elem<MODE>(c, q, jj, vv, bb, aa)) x = 0;
+          store_out(c, reinterpret_cast<T*>(orow) + ee, x);
         }
       }
-    } else {
-      // checked path: run ends, and the paper-window masks
-#pragma unroll 1
-      for (int g = 0; g < kGroupsPerItem; ++g) {
-#pragma unroll
-        for (int h = 0; h < EPL; ++h) {
-          const int e = e_begin + g * SE + h;
-          if (e < 0 || e >= L) continue;
-          int j, vl, b, a;
-          const int idx = src_index<ES>(c, q, e, j, vl, b, a);
-          LFBP_SMEM_CHECK(idx);
-          T x = sm[idx];
-          if (!keep_elem<MODE>(c, q, j, vl, b, a)) x = 0;
-          st_global(reinterpret_cast<T*>(orow) + e, x);
-        }
+      if (have) {  // advance the state by one group
+        vl += GE;
+        b += c.sbn;
+        if (b >= Ny) b -= Ny;
+        if (vl >= ncols)
+          have = false;  // next row: start again from scratch
+        else
+          X -= GE * ES;
       }
     }
   }
 }
 
-template <int ES>
-__device__ __forceinline__ void gather_tile_es(const TileDesc& td, const unsigned char* stage,
-                                               const unsigned char* in_depth,
-                                               unsigned char* out_depth, int w, int nwarps,
-                                               int lane) {
-  TileCtx c;
-  make_ctx<ES>(c, td, stage, in_depth, out_depth);
-  const int mode = (td.flags >> 1) & 3;
-  if (mode == 0)
-    gather_tile<ES, 0>(c, w, nwarps, lane);
-  else if (mode == 1)
-    gather_tile<ES, 1>(c, w, nwarps, lane);
-  else
-    gather_tile<ES, 2>(c, w, nwarps, lane);
-}
-
-__device__ __forceinline__ void gather_tile_any(const TileDesc& td, const unsigned char* stage,
-                                                const unsigned char* in_depth,
-                                                unsigned char* out_depth, int w, int nwarps,
-                                                int lane) {
-  if (td.flags & 1)
-    gather_tile_es<2>(td, stage, in_depth, out_depth, w, nwarps, lane);
-  else
-    gather_tile_es<4>(td, stage, in_depth, out_depth, w, nwarps, lane);
+// Consumer side, given the tile's context (in shared memory).
+__device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane) {
+  const TileCtx c = cs;  // into registers, once per tile
+  if (c.es == 4) {
+    if (c.mode == 0)
+      gather_tile<4, 0>(c, w, nwarps, lane);
+    else if (c.mode == 1)
+      gather_tile<4, 1>(c, w, nwarps, lane);
+    else
+      gather_tile<4, 2>(c, w, nwarps, lane);
+  } else {
+    if (c.mode == 0)
+      gather_tile<2, 0>(c, w, nwarps, lane);
+    else if (c.mode == 1)
+      gather_tile<2, 1>(c, w, nwarps, lane);
+    else
+      gather_tile<2, 2>(c, w, nwarps, lane);
+  }
 }
 
 }  // namespace lfbp

@@ -86,6 +86,17 @@ static inline void count_store(const unsigned char* p, size_t n) {
   for (size_t i = 0; i < n; ++i) g_counts[(p - g_out) + i]++;
 }
 template <class T>
+static inline T lds(uint32_t addr) {
+  if ((size_t)addr + sizeof(T) > g_stage_bytes) err("lds outside stage", addr, (long long)g_stage_bytes);
+  T v;
+  std::memcpy(&v, g_stage + addr, sizeof(T));
+  return v;
+}
+template <class T, int OFF>
+static inline T lds_off(uint32_t addr) {
+  return lds<T>(addr + OFF);
+}
+template <class T>
 static inline void st_global(T* p, T v) {
   if ((uintptr_t)p & (sizeof(T) - 1)) err("store misaligned", (long long)((uintptr_t)p & 15), (long long)sizeof(T));
   count_store((unsigned char*)p, sizeof(T));
@@ -158,9 +169,11 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
           if (g_arrive != 1) err("producer arrivals != 1", g_arrive, 0);
           const int nwarps = nthr;  // here: number of consumer warps
+          TileCtx ctx;
+          make_ctx(ctx, td, stage.data(), in_depth, out_depth);
           for (int w = 0; w < nwarps; ++w)
             for (int lane = 0; lane < 32; ++lane)
-              gather_tile_any(td, stage.data(), in_depth, out_depth, w, nwarps, lane);
+              gather_tile_ctx(ctx, w, nwarps, lane);
           ++tiles;
           copied += g_copied;
           if (g_errors) break;

@@ -219,3 +219,21 @@ def test_host_to_host_pipeline(lf):
         lf.sync_status()
         _assert_same_bits(out, oracle.transpose(H.numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt),
                           f"host pipeline {name}")
+
+
+def test_tuner_then_batched(lf, tmp_path, monkeypatch):
+    """The autotuner picks a shape from its grid; batched calls stay bit-exact after it."""
+    monkeypatch.setenv("LFBP_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    shapes = [(5, 5, [15, 25], [15, 25], torch.float32), (19, 19, [57, 95], [57, 95], torch.float16)]
+    plans = [lf.Plan(a, b, c, d, t) for a, b, c, d, t in shapes]
+    Hs = [_random_bits(p.elems, p.dtype, 40 + i) for i, p in enumerate(plans)]
+    tb, cps, st = lf.tune_batched(plans, Hs, reps=1)
+    assert tb in (16384, 24576, 32768, 49152) and cps in (2, 3, 4)
+    assert (tmp_path / "tune.txt").read_text().strip()
+    for rep in range(2):
+        outs = lf.backproject_batched(plans, Hs)
+        for p, H, o in zip(plans, Hs, outs):
+            _assert_same_bits(o, oracle.transpose(H.cpu().numpy(), p.Nx, p.Ny, p.Ks, p.Kt), "tuned")
+    # a second process-level tune reads the cache instead of timing
+    assert lf.tune_batched(plans, Hs, reps=1) == (tb, cps, st)
+    lf.sync_status()
