@@ -135,6 +135,35 @@ int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* d
                              void* const* dHp, void* cuda_stream);
 
 /*
+ * lfbp_backproject_batched without any device allocation (the paper has no
+ * counterpart; this is a deployment aid).  Some callers cannot allocate
+ * device memory on their own: a host application that hands out all device
+ * memory from its own pool, or one that forbids cudaMalloc once its run has
+ * started (allocation can synchronise the device and fail under memory
+ * pressure at the worst moment).  This entry point keeps the persistent
+ * kernel's work list in a fixed array of device memory that is part of the
+ * library image: 262,144 tile descriptors (8 MiB), held on every GPU that
+ * loads the library until the process exits.  A batch that needs more tiles
+ * (even with 48 KiB tiles) is rejected with LFBP_ERR_BAD_SHAPE before any work
+ * is queued.  The call never calls cudaMalloc or cudaFree and builds no CUDA
+ * graph; it launches the kernel directly on cuda_stream.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and reads device attributes; make that first call
+ * before any stream capture.  All calls share the one array, which keeps the
+ * work list of the last call: when the plans differ from the previous call
+ * on this device, the new list is copied in, in stream order, before the
+ * launch (nothing in the array has to start at zero: the kernel reads only
+ * the entries the current list occupies).  Calls whose work overlaps on the
+ * GPU -- on different streams, or from threads that do not order their
+ * streams -- race on the array and may map with the wrong list; keep such
+ * calls on one stream or order them with events.  Arguments, layout and
+ * results are those of lfbp_backproject_batched.
+ */
+int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* const* dH,
+                                     void* const* dHp, void* cuda_stream);
+
+/*
  * Autotuner for lfbp_backproject_batched: times a small grid of launch shapes
  * (shared-memory bytes per tile in {16, 24, 32, 48} KiB x persistent CTAs per
  * SM in {2, 3, 4}) on the given buffers with CUDA events (reps timed launches

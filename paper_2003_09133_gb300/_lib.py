@@ -38,6 +38,7 @@ SIGNATURES = {
     "lfbp_backproject_batched": ([_I, _P, _P, _P, _P], _I),
     "lfbp_adjoint": ([_P, _P, _P, _P], _I),
     "lfbp_tune_batched": ([_I, _P, _P, _P, _P, _I, _P], _I),
+    "lfbp_backproject_batched_noalloc": ([_I, _P, _P, _P, _P], _I),
     "lfbp_backproject_volume": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_forward_project": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_backproject_volume_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),

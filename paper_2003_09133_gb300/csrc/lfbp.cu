@@ -656,6 +656,131 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   return LFBP_OK;
 }
 
+// ------------------------------------------------------- no-allocation path --
+// For callers that must not allocate device memory themselves or through this
+// library (for instance code that owns a fixed memory pool, or a host
+// framework that forbids cudaMalloc during its run), lfbp_backproject_batched_
+// noalloc keeps the persistent kernel's work list in this file-scope device
+// array instead of a cudaMalloc'd buffer.  Every GPU that loads the library
+// holds the array until the process exits.
+constexpr int kNoAllocMaxTiles = 262144;  // 8 MiB of 32-byte tile descriptors
+static __device__ __align__(256) TileDesc g_noalloc_tiles[kNoAllocMaxTiles];
+
+// Per device: the array's device address (from cudaGetSymbolAddress) and
+// which work list it holds now.
+struct NoAllocDev {
+  int dev = -1;
+  TileDesc* d_tiles = nullptr;
+  int sms = 0, optin = 0;
+  std::vector<unsigned long long> uids;  // plans of the list in the array
+  int tile_bytes = 0, ntiles = 0, stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
+};
+std::vector<std::unique_ptr<NoAllocDev>> g_noalloc;  // guarded by g_mu
+
+// Set-up, once per device, with that device current: the host-side name of
+// the array is not a device address, so ask the runtime for it.
+int noalloc_setup(int dev, NoAllocDev** out) {
+  for (auto& d : g_noalloc)
+    if (d->dev == dev) {
+      *out = d.get();
+      return LFBP_OK;
+    }
+  std::unique_ptr<NoAllocDev> nd(new NoAllocDev());
+  nd->dev = dev;
+  cudaError_t e = cudaGetSymbolAddress((void**)&nd->d_tiles, g_noalloc_tiles);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(work list array)");
+  int d2 = 0;
+  int rc = device_props(&d2, &nd->sms, &nd->optin);
+  if (rc) return rc;
+  *out = nd.get();
+  g_noalloc.push_back(std::move(nd));
+  return LFBP_OK;
+}
+
+int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, void* const* out,
+                        cudaStream_t st) {
+  if (n < 0 || n > kMaxBatch) return fail(LFBP_ERR_INVALID, "batch size must be in [0, 64]");
+  if (n == 0) return LFBP_OK;
+  if (!plans || !in || !out) return fail(LFBP_ERR_NULL, "NULL array argument");
+  for (int i = 0; i < n; ++i) {
+    int rc = check_buffers(plans[i], in[i], out[i]);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      const size_t bi = plans[i]->off.back() * plans[i]->es;
+      const size_t bk = plans[k]->off.back() * plans[k]->es;
+      if (bi && bk && overlaps(out[i], bi, in[k], bk))
+        return fail(LFBP_ERR_ALIAS, "an output overlaps an input");
+      if (k != i && bi && bk && overlaps(out[i], bi, out[k], bk))
+        return fail(LFBP_ERR_ALIAS, "two outputs overlap");
+    }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  NoAllocDev* nd = nullptr;
+  int rc = noalloc_setup(dev, &nd);
+  if (rc) return rc;
+  // the default tile size, or larger tiles when the list would not fit
+  Tuning tu = default_tuning();
+  long long need = 0;
+  for (int target : {tu.tile_bytes, 49152}) {
+    tu.tile_bytes = target;
+    need = 0;
+    for (int i = 0; i < n; ++i) {
+      const std::vector<DepthTiling>& tl = plan_tiling(plans[i], target);
+      for (int z = 0; z < plans[i]->Nz; ++z) need += (long long)plans[i]->Nx * tl[z].nU * tl[z].nV;
+    }
+    if (need <= kNoAllocMaxTiles) break;
+  }
+  if (need > kNoAllocMaxTiles) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg),
+                  "the batch needs %lld tiles; the no-allocation path holds at most %d",
+                  need, kNoAllocMaxTiles);
+    return fail(LFBP_ERR_BAD_SHAPE, msg);
+  }
+  if (need == 0) return LFBP_OK;
+  bool loaded = nd->tile_bytes == tu.tile_bytes && same_uids(nd->uids, n, plans);
+  if (!loaded) {
+    std::vector<TileDesc> tiles;
+    tiles.reserve((size_t)need);
+    int max_tile = 0;
+    build_tiles(n, plans, tu.tile_bytes, tiles, &max_tile);
+    const int stage_bytes = (max_tile + 127) & ~127;
+    const int per_cta_budget = std::min(nd->optin, (227 * 1024) / tu.ctas_per_sm - 1024);
+    int nst = per_cta_budget / (stage_bytes + kInfoBytes + 16);
+    if (nst < 2) nst = std::min(2, nd->optin / (stage_bytes + kInfoBytes + 16));
+    if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
+    // stream-ordered: the kernels of earlier calls on this stream have read
+    // the previous list before this copy overwrites it
+    if ((e = cudaMemcpyAsync(nd->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(work list)");
+    nd->uids.clear();
+    for (int i = 0; i < n; ++i) nd->uids.push_back(plans[i]->uid);
+    nd->tile_bytes = tu.tile_bytes;
+    nd->ntiles = (int)tiles.size();
+    nd->stage_bytes = stage_bytes;
+    nd->nstages = nst;
+    nd->smem = persistent_smem_bytes(stage_bytes, nst);
+    nd->grid = std::max(1, std::min(nd->sms * tu.ctas_per_sm, nd->ntiles));
+  }
+  if ((rc = ensure_smem_attr((const void*)k_gather_persistent, nd->smem))) return rc;
+  BatchPtrs np;
+  std::memset(&np, 0, sizeof(np));
+  for (int i = 0; i < n; ++i) {
+    np.in[i] = (const unsigned char*)in[i];
+    np.out[i] = (unsigned char*)out[i];
+    np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
+  }
+  k_gather_persistent<<<nd->grid, kPersistentThreads, nd->smem, st>>>(np, nd->d_tiles, nd->ntiles,
+                                                                      nd->stage_bytes, nd->nstages);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
+  return LFBP_OK;
+}
+
 // ------------------------------------------------------------------ tuner --
 // Shape signature of a list of plans (for the tuning cache file).
 std::string plans_signature(int dev, int n, const lfbp_plan* plans) {
@@ -892,6 +1017,11 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream) {
   return run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);
+}
+
+int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* const* dH,
+                                     void* const* dHp, void* cuda_stream) {
+  return run_batched_noalloc(n, plans, dH, dHp, (cudaStream_t)cuda_stream);
 }
 
 int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
