@@ -201,7 +201,9 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       }
       const unsigned char* info = info_base + (size_t)s * kInfoBytes;
       if (*reinterpret_cast<const int*>(info) != 0) break;
-      gather_tile_ctx(*reinterpret_cast<const TileCtx*>(info + 16), cw, kConsumerWarps, lane);
+      // rotate the item-to-warp assignment by the tile's item count
+      const TileCtx& tc = *reinterpret_cast<const TileCtx*>(info + 16);
+      gather_tile_ctx(tc, cw, kConsumerWarps, lane, (it * tc.items) % kConsumerWarps);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
     }

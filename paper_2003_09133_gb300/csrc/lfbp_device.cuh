@@ -36,7 +36,7 @@ namespace lfbp {
 
 constexpr int kMaxBatch = 64;       // arrays per batched launch
 constexpr int kStatusTimeout = -7;  // LFBP_ERR_TIMEOUT
-constexpr int kGroupsPerItem = 8;   // sectors per run handled by one consumer work item
+constexpr int kGroupsPerItem = 4;   // 128-byte groups per run handled by one consumer work item
 
 // One tile, self-contained (32 bytes).
 struct TileDesc {
@@ -450,6 +450,7 @@ struct alignas(16) TileCtx {
   int om0;   // absolute element index of run q = 0, mod 128/es
   int kks;   // (Ks*Kt) mod 128/es
   int sbn;   // (128/es) mod Ny
+  int cmn;   // ncols mod Ny
   int ngc;   // work items per run
   int items;
   int es, mode;
@@ -491,6 +492,7 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
     case 2:
       c.fNy = make_fastdiv(td.Ny);
       c.sbn = GE % td.Ny;
+      c.cmn = td.ncols % td.Ny;
       break;
     case 3:
       c.fNx = make_fastdiv(td.Nx);
@@ -630,19 +632,27 @@ __device__ __forceinline__ bool keep_elem(const TileCtx& c, int q, int j, int vl
 
 // Consumer side: gather the tile from the stage through the index map and
 // write its Ny output runs with 16-byte stores.  `w` is this warp's index
-// among the `nwarps` consumer warps of the CTA.  Work item = 4 runs x
-// kGroupsPerItem groups; a group is one 128-byte stretch of a run, 16 bytes
-// per lane.  Inside a row, consecutive output elements walk the diagonal
-// b -> b+1 (mod Ny), t -> t-1, i.e. one IMAD per element for the address.
+// among the `nwarps` consumer warps of the CTA; `rot` rotates the item-to-warp
+// assignment from tile to tile so that the warps share the remainder items.
+// Work item = 4 runs x kGroupsPerItem groups; a group is one 128-byte stretch
+// of a run, 16 bytes per lane.  Inside a row, consecutive output elements walk
+// the diagonal b -> b+1 (mod Ny), t -> t-1 of the stage: one IMAD per element
+// for the address.  Every path keeps the walk's state (row j, cell a, column
+// vl, segment b, row base) incrementally; only an item's start is computed
+// with divisions.
 template <int ES, int MODE>
-__device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps, int lane) {
+__device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps, int lane,
+                                            int rot) {
   using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+  constexpr int E = 16 / ES;
   constexpr int EPL = 16 / ES;  // elements per lane and group (one 16-byte store)
   constexpr int GE = 8 * EPL;   // elements per run and group (128 bytes)
   const int r = lane >> 3, k = lane & 7;
-  const int Ny = c.Ny, L = c.L, P = c.P, ncols = c.ncols;
+  const int Ny = c.Ny, Nx = c.Nx, L = c.L, P = c.P, ncols = c.ncols, RP = c.RP;
   const uint32_t PES = (uint32_t)P * ES;
-  for (int it = w; it < c.items; it += nwarps) {
+  int first = (w - rot) % nwarps;
+  if (first < 0) first += nwarps;
+  for (int it = first; it < c.items; it += nwarps) {
     const int qb = (int)fdiv((uint32_t)it, c.fngc);
     const int gc = it - qb * c.ngc;
     const int q = qb * 4 + r;
@@ -650,82 +660,89 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
     const int m = (c.om0 + q * c.kks) & (GE - 1);
     unsigned char* orow = c.out_run0 + (long long)q * c.run_stride;
     int e = gc * (kGroupsPerItem * GE) + k * EPL - m;  // this lane's first element
-    // incremental state at element e: row j, column vl, source segment b, and
-    // X = byte address of (row base + ncols - 1 - vl) - (EPL-1)*ES in shared memory
-    bool have = false;
-    int vl = 0, b = 0;
-    uint32_t X = 0;
+    const int pos = e < 0 ? 0 : e;
+    if (pos >= L) continue;
+    // walk state at element `pos`
+    int j, vl, b, a;
+    int rb = src_index<ES>(c, q, pos, j, vl, b, a);  // = row base + b*P - vl
+    rb += vl - b * P;                                 // row base: j*RP + phase_j + ncols - 1
+    const int bq0 = (int)fmod_((uint32_t)(q + c.cb), c.fNy);  // segment of column 0
 #pragma unroll 1
     for (int g = 0; g < kGroupsPerItem; ++g, e += GE) {
       if (e >= L) break;
-      const bool full = e >= 0 && e + EPL <= L;
-      if (MODE == 0 && full && (!have || vl + EPL <= ncols)) {
-        if (!have) {
-          int j, a;
-          const int idx = src_index<ES>(c, q, e, j, vl, b, a);
-          X = c.stage_s + (uint32_t)(idx - b * P - (EPL - 1)) * ES;
-          have = true;
-        }
-        if (vl + EPL <= ncols) {
-          T v[EPL];
-          int bb = b;
-          static_for<0, EPL>([&](auto ic) {
-            constexpr int i = decltype(ic)::value;
-            v[i] = smem_load_off<T, (EPL - 1 - i) * ES>(c, (uint32_t)bb * PES + X);
-            bb = bb + 1 == Ny ? 0 : bb + 1;
-          });
-          store_out16(c, orow + (long long)e * ES, pack16(v));
-        } else {
-          T v[EPL];
-#pragma unroll
-          for (int i = 0; i < EPL; ++i) {
-            int jj, vv, bb, aa;
-            v[i] = smem_load<T>(c, src_index<ES>(c, q, e + i, jj, vv, bb, aa));
-          }
-          store_out16(c, orow + (long long)e * ES, pack16(v));
-        }
+      const int i0 = e < 0 ? -e : 0;  // first element of the group inside the run
+      const bool allv = i0 == 0 && e + EPL <= L;
+      T v[EPL];
+      if (MODE == 0 && allv && vl + EPL <= ncols) {
+        // whole group inside one row and inside the run
+        const uint32_t X = c.stage_s + (uint32_t)(rb - vl - (EPL - 1)) * ES;
+        int bb = b;
+        static_for<0, EPL>([&](auto ic) {
+          constexpr int ii = decltype(ic)::value;
+          v[ii] = smem_load_off<T, (EPL - 1 - ii) * ES>(c, (uint32_t)bb * PES + X);
+          bb = bb + 1 == Ny ? 0 : bb + 1;
+        });
+        store_out16(c, orow + (long long)e * ES, pack16(v));
       } else {
-        // run ends (partial groups) and the paper-window masks: element by element
+        // row crossings, run ends, masks: element by element, same walk
+        int tv = vl, tb = b, tj = j, ta = a, trb = rb;
 #pragma unroll
-        for (int i = 0; i < EPL; ++i) {
-          const int ee = e + i;
-          if (ee < 0 || ee >= L) continue;
-          int jj, vv, bb, aa;
-          T x = smem_load<T>(c, src_index<ES>(c, q, ee, jj, vv, bb, aa));
-          if (!keep_elem<MODE>(c, q, jj, vv, bb, aa)) x = 0;
-          store_out(c, reinterpret_cast<T*>(orow) + ee, x);
+        for (int ii = 0; ii < EPL; ++ii) {
+          v[ii] = 0;
+          if (ii < i0 || e + ii >= L) continue;
+          T x = smem_load<T>(c, trb + tb * P - tv);
+          if (!keep_elem<MODE>(c, q, tj, tv, tb, ta)) x = 0;
+          v[ii] = x;
+          if (!allv) store_out(c, reinterpret_cast<T*>(orow) + (e + ii), x);
+          ++tv;
+          tb = tb + 1 == Ny ? 0 : tb + 1;
+          if (tv == ncols) {  // next row
+            tv = 0;
+            ++tj;
+            ta = ta + 1 == Nx ? 0 : ta + 1;
+            trb = tj * RP + ((c.inm + ta * c.nkk + (c.s0 - tj) * c.ktm) & (E - 1)) + ncols - 1;
+            tb = bq0;
+          }
         }
+        if (allv) store_out16(c, orow + (long long)e * ES, pack16(v));
       }
-      if (have) {  // advance the state by one group
-        vl += GE;
-        b += c.sbn;
-        if (b >= Ny) b -= Ny;
-        if (vl >= ncols)
-          have = false;  // next row: start again from scratch
-        else
-          X -= GE * ES;
+      // move the walk to the next group's first element
+      const int d = e < 0 ? e + GE : GE;
+      vl += d;
+      b += d == GE ? c.sbn : (int)fmod_((uint32_t)d, c.fNy);
+      if (b >= Ny) b -= Ny;
+      if (vl >= ncols) {
+        do {
+          vl -= ncols;
+          ++j;
+          a = a + 1 == Nx ? 0 : a + 1;
+          b -= c.cmn;
+          if (b < 0) b += Ny;
+        } while (vl >= ncols);
+        rb = j * RP + ((c.inm + a * c.nkk + (c.s0 - j) * c.ktm) & (E - 1)) + ncols - 1;
       }
     }
   }
 }
 
 // Consumer side, given the tile's context (in shared memory).
-__device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane) {
+__device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane,
+                                                int rot = 0) {
   const TileCtx c = cs;  // into registers, once per tile
   if (c.es == 4) {
     if (c.mode == 0)
-      gather_tile<4, 0>(c, w, nwarps, lane);
+      gather_tile<4, 0>(c, w, nwarps, lane, rot);
     else if (c.mode == 1)
-      gather_tile<4, 1>(c, w, nwarps, lane);
+      gather_tile<4, 1>(c, w, nwarps, lane, rot);
     else
-      gather_tile<4, 2>(c, w, nwarps, lane);
+      gather_tile<4, 2>(c, w, nwarps, lane, rot);
   } else {
     if (c.mode == 0)
-      gather_tile<2, 0>(c, w, nwarps, lane);
+      gather_tile<2, 0>(c, w, nwarps, lane, rot);
     else if (c.mode == 1)
-      gather_tile<2, 1>(c, w, nwarps, lane);
+      gather_tile<2, 1>(c, w, nwarps, lane, rot);
     else
-      gather_tile<2, 2>(c, w, nwarps, lane);
+      gather_tile<2, 2>(c, w, nwarps, lane, rot);
   }
 }
 

@@ -173,7 +173,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           make_ctx(ctx, td, stage.data(), in_depth, out_depth);
           for (int w = 0; w < nwarps; ++w)
             for (int lane = 0; lane < 32; ++lane)
-              gather_tile_ctx(ctx, w, nwarps, lane);
+              gather_tile_ctx(ctx, w, nwarps, lane, (int)((tiles * (unsigned long long)ctx.items) % nwarps));
           ++tiles;
           copied += g_copied;
           if (g_errors) break;
