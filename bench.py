@@ -377,7 +377,9 @@ def run_ours(args):
     t_batched, best_batched, clocks = timed(step_batched, args.steps, args.warmup, clocks=True)
     t_plain, best_plain, _ = timed(step_plain, max(3, args.steps // 4), max(3, args.warmup))
 
-    # end to end through the public API: pinned host H -> device -> H' -> pinned host
+    # end to end through the C-ABI with host buffers: pinned host H -> device ->
+    # H' -> pinned host, the copies of one chunk of depths overlapping the map
+    # of the previous chunk (lfbp_backproject_array_host)
     e2e = None
     if not args.no_e2e:
         hosts = [h.cpu().pin_memory() for h in Hs]
@@ -385,11 +387,8 @@ def run_ours(args):
         dev_in = [torch.empty_like(h) for h in Hs]
 
         def step_e2e():
-            for hi, di in zip(hosts, dev_in):
-                di.copy_(hi, non_blocking=True)
-            lf.backproject_batched(plans, dev_in, outs)
-            for do, ho in zip(outs, host_out):
-                ho.copy_(do, non_blocking=True)
+            for p, hi, ho, di, do in zip(plans, hosts, host_out, dev_in, outs):
+                lf.backproject_array_host(p, hi, ho, work=(di, do))
 
         n_e2e = max(3, min(args.steps, 20))
         t_e2e, _, _ = timed(step_e2e, n_e2e, 2)
