@@ -424,6 +424,8 @@ def run_ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_extra and args.workload == "highres" and args.dtype in (None, "f32"):
+        line["extra"] = _extra_forms(lf, plans, specs, Hs, outs, timed, args, world)
     if rank == 0 and not args.no_cpu_baseline:
         Hh = [h.cpu().numpy() for h in Hs]
         line["cpu_baseline"] = _cpu_oracle_rate(specs, Hh, args.dtype)
@@ -433,6 +435,45 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
+    """The fp16-stored copy of the same array, and the ragged 16-array batch:
+    batched persistent form next to the plain per-depth form."""
+    import torch
+    import lfgen
+    res = {}
+    steps = max(3, args.steps // 4)
+    # fp16 storage of the same values (round to nearest even)
+    p16 = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float16) for s in specs]
+    h16 = [h.half() for h in Hs]
+    o16 = [torch.empty_like(h) for h in h16]
+    nb = sum(2 * h.numel() * 2 for h in h16)
+    tb, _, _ = timed(lambda: lf.backproject_batched(p16, h16, o16), steps, 3)
+    tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(p16, h16, o16)],
+                     steps, 3)
+    res["highres_fp16"] = {"batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
+                           "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
+                           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+    del h16, o16
+    torch.cuda.empty_cache()
+    # the ragged batch: 16 arrays, mixed fp32 / fp16, one persistent launch
+    rspecs = lfgen.config_specs("ragged")
+    rplans = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, s.torch_dtype) for s in rspecs]
+    rH = [lfgen.generate(s, device="cuda") for s in rspecs]
+    rO = [torch.empty_like(h) for h in rH]
+    nb = sum(2 * h.numel() * h.element_size() for h in rH)
+    tb, _, _ = timed(lambda: lf.backproject_batched(rplans, rH, rO), steps, 3)
+    tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(rplans, rH, rO)],
+                     steps, 3)
+    res["ragged"] = {"arrays": len(rspecs), "bytes_per_step": nb,
+                     "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
+                     "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
+                     "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
+                     "plain_launches_per_step": sum(s.Nz for s in rspecs)}
+    del rH, rO
+    torch.cuda.empty_cache()
+    return res
 
 
 def main(argv=None):
@@ -447,6 +488,8 @@ def main(argv=None):
     ap.add_argument("--depth-stride", type=int, default=1,
                     help="keep every k-th depth only (smaller case of the same shapes)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the fp16 copy and the ragged batch beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:

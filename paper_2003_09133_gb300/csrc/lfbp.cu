@@ -3,7 +3,7 @@
 // Kernels (see lfbp_device.cuh for the tile and the index map):
 //   k_gather_depth       one tile per CTA, one launch per depth (the plain form)
 //   k_gather_persistent  persistent CTAs over a ragged work list of all depths
-//                        of all arrays; one producer warp streams tiles into a
+//                        of all arrays; producer warps stream tiles into a
 //                        ring of shared-memory stages with TMA bulk copies,
 //                        consumer warps gather and store (the batched form)
 // and the C-ABI of include/lfbp.h.
@@ -30,8 +30,9 @@ __device__ int g_status;
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
+constexpr int kProducerWarps = 1;  // warps sharing each tile's bulk copies
 constexpr int kConsumerWarps = 8;
-constexpr int kPersistentThreads = 32 * (1 + kConsumerWarps);
+constexpr int kPersistentThreads = 32 * (kProducerWarps + kConsumerWarps);
 constexpr int kInfoBytes = 256;  // per-stage slot for the tile descriptor and context
 static_assert(sizeof(TileDesc) + sizeof(TileCtx) <= kInfoBytes, "stage info too large");
 constexpr int kStatusBadLaunch = -9;  // LFBP_ERR_INVALID: launched with too little shared memory
@@ -83,14 +84,16 @@ __global__ void __launch_bounds__(kPlainThreads)
   td.ncols = (unsigned short)min(V, (int)base.Kt - v0);
 
   const uint32_t b = smem_addr(bar);
+  constexpr int kWarps = kPlainThreads / 32;
   if (tid == 0) {
     abort_flag = 0;
-    mbar_init(b, 1);
+    mbar_init(b, kWarps);
     fence_mbar_init();
   }
   if (warp == 1 && lane < 8) make_ctx_lane(*ctx, td, stage, in_depth, out_depth, lane);
   __syncthreads();
-  if (warp == 0) issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane);
+  // every warp issues a share of the tile's copies, then all wait for them
+  issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane, warp, kWarps);
   if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
     set_status(kStatusTimeout);
     abort_flag = 1;
@@ -105,8 +108,10 @@ __global__ void __launch_bounds__(kPlainThreads)
 // grid = SMs * ctas_per_sm; block = kPersistentThreads.  CTA c takes tiles
 // c, c + grid, c + 2 grid, ... (consecutive tiles are neighbours in memory, so
 // the tiles in flight at any time cover one contiguous stretch of the work
-// list).  Warp 0 produces: it prefetches the next descriptor, waits for a free
-// stage, and issues the stage's bulk copies; warps 1..8 consume.
+// list).  Warps 0 .. kProducerWarps-1 produce: each prefetches the next
+// descriptor, waits for a free stage and issues its share of the stage's bulk
+// copies (warp 0 also writes the stage's tile context); the other warps
+// consume.
 // smem: [nstages x stage_bytes][nstages x descriptor][full[nstages]][empty[nstages]]
 __global__ void __launch_bounds__(kPersistentThreads, 3)
     k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
@@ -126,15 +131,15 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < nstages; ++s) {
-      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&full[s]), kProducerWarps);
       mbar_init(smem_addr(&empty[s]), kConsumerWarps);
     }
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == 0) {
-    // ---- producer warp
+  if (warp < kProducerWarps) {
+    // ---- producer warps
     int it = 0;
     int t = blockIdx.x;
     TileDesc td;
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       }
       if (t >= ntiles) {
         if (lane == 0) {
-          *reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes) = 1;  // end of work
+          if (warp == 0) *reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes) = 1;  // end of work
           mbar_arrive(fb);
         }
         ++it;
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       const unsigned char* in_arr = ptrs.in[td.arr];
       const unsigned char* in_depth = in_arr + td.off_bytes;
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
-      {
+      if (warp == 0) {
         unsigned char* info = info_base + (size_t)s * kInfoBytes;
         if (lane == 0) *reinterpret_cast<int*>(info) = 0;
         if (lane < 8)
@@ -174,10 +179,12 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
                         in_depth, ptrs.out[td.arr] + td.off_bytes, lane);
       }
       __syncwarp();
-      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane);
+      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
+                       kProducerWarps);
       td = next;
     }
-    // make sure no copy into this CTA's shared memory is still in flight
+    // make sure no copy into this CTA's shared memory is still in flight (the
+    // full barriers count the bytes of every producer warp's copies)
     if (lane == 0) {
       const int armed = it;  // stages armed: iterations 0..it-1
       for (int s = 0; s < nstages && s < armed; ++s) {
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
     }
   } else {
     // ---- consumer warps
-    const int cw = warp - 1;
+    const int cw = warp - kProducerWarps;
     for (int it = 0;; ++it) {
       const int s = it % nstages;
       const uint32_t par = (uint32_t)((it / nstages) & 1);

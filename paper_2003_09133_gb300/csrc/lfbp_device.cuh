@@ -338,14 +338,18 @@ __device__ __forceinline__ int pos_mod(int x, int n) {
 }
 
 // Producer side: issue the bulk copies of the tile's input segments into the
-// stage.  Called by all 32 lanes of one warp; lane i takes slots i, i+32, ...
-// (slot = j*Ny + b).  Each lane registers the bytes of its own copies on
-// `bar` before issuing them, and lane 0 arrives after every lane is done.
-// The last <16 bytes of an array that a 16-byte-widened copy would over-read
-// are copied with ordinary loads instead.
+// stage.  Called by all 32 lanes of each of `np` warps; lane i of warp pw
+// (0 <= pw < np) takes slots pw*32 + i, pw*32 + i + 32*np, ... (slot = j*Ny + b).
+// A warp's bulk copies are accepted one lane at a time, so the copies of a
+// tile with many short segments are spread over several warps.  Each lane
+// registers the bytes of its own copies on `bar` before issuing them, and lane
+// 0 of each warp arrives once after its lanes are done (`bar` counts np
+// arrivals).  The last <16 bytes of an array that a 16-byte-widened copy
+// would over-read are copied with ordinary loads instead.
 __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsigned char* in_depth,
                                                  const unsigned char* in_safe_end,
-                                                 unsigned char* stage, uint32_t bar, int lane) {
+                                                 unsigned char* stage, uint32_t bar, int lane,
+                                                 int pw, int np) {
   const int es = (td.flags & 1) ? 2 : 4, E = 16 / es;
   const int Nx = td.Nx, Ny = td.Ny, Ks = td.Ks, Kt = td.Kt, P = td.P;
   const int RP = row_pitch(Ny, P, es);
@@ -364,8 +368,9 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
 #endif
   // slot i = (row j, segment b): row j reads H[a_j][b][s_j][t_lo..], with
   // a_j = (p + u0 + j - c_s) mod Nx and s_j = Ks - 1 - u0 - j
+  const int slot0 = pw * 32 + lane, slot_step = 32 * np;
   uint32_t my_bytes = 0;
-  for (int i = lane; i < nslots; i += 32) {
+  for (int i = slot0; i < nslots; i += slot_step) {
     const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
     const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
     const unsigned long long seg =
@@ -379,7 +384,7 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
   }
   if (my_bytes) mbar_expect_tx(bar, my_bytes);
   bool fixed = false;
-  for (int i = lane; i < nslots; i += 32) {
+  for (int i = slot0; i < nslots; i += slot_step) {
     const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
     const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
     const unsigned long long seg0 =

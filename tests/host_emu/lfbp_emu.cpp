@@ -2,7 +2,7 @@
 //
 // Compiles the device tile functions of lfbp_device.cuh as ordinary C++ with
 // checked stand-ins for the GPU primitives, and runs every tile of a plan
-// sequentially (producer lanes 0..31, then consumer threads) so that the
+// sequentially (the lanes of 1, 2, 3 or 8 producer warps, then consumer threads) so that the
 // CPU tests can check, before any GPU run, that
 //   * every bulk copy is 16-byte aligned, a multiple of 16 bytes, reads only
 //     inside the input array and writes only inside its stage,
@@ -164,10 +164,15 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           g_expect = g_copied = g_arrive = 0;
           const unsigned char* in_depth = in + base.off_bytes;
           unsigned char* out_depth = out + base.off_bytes;
-          for (int lane = 0; lane < 32; ++lane)
-            issue_tile_loads(td, in_depth, safe_end, stage.data(), 0, lane);
+          // the copies of a tile are shared by np producer warps; cycle np
+          // through the counts the kernels use
+          static const int kNp[4] = {1, 2, 3, 8};
+          const int np = kNp[tiles % 4];
+          for (int pw = 0; pw < np; ++pw)
+            for (int lane = 0; lane < 32; ++lane)
+              issue_tile_loads(td, in_depth, safe_end, stage.data(), 0, lane, pw, np);
           if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
-          if (g_arrive != 1) err("producer arrivals != 1", g_arrive, 0);
+          if (g_arrive != (unsigned long long)np) err("producer arrivals != producer warps", g_arrive, np);
           const int nwarps = nthr;  // here: number of consumer warps
           TileCtx ctx;
           make_ctx(ctx, td, stage.data(), in_depth, out_depth);
