@@ -183,6 +183,30 @@ def grad_hp_points(f: np.ndarray, r: np.ndarray, Nx, Ny, Ks, Kt, pts: np.ndarray
     return out
 
 
+def rl_step(H: np.ndarray, Hp: np.ndarray, Nx, Ny, Ks, Kt, g: np.ndarray, f: np.ndarray,
+            norm: np.ndarray = None) -> np.ndarray:
+    """One Richardson-Lucy update, Eq. (2), in FP64:
+
+        g_next = g / (H' 1) * [H' (f / (H g))]
+
+    The forward projection H g (Eq. 1) is compared with the measured image f
+    by an elementwise quotient, the quotient is backprojected with H', and the
+    estimate is scaled by it and divided by the backprojection of a ones
+    image.  The paper is silent on zeros; readings: a pixel where H g = 0
+    contributes 0 to the quotient, and a voxel where H' 1 = 0 gets 0.  ``norm``
+    (H' 1 over the W_x x W_y sensor, [Nz][Wx][Wy]) may be passed in.
+    """
+    g = np.asarray(g, dtype=np.float64)
+    f = np.asarray(f, dtype=np.float64)
+    fe = forward(H, Nx, Ny, Ks, Kt, g)
+    r = np.divide(f, fe, out=np.zeros_like(fe), where=fe != 0)
+    bp = backproject(Hp, Nx, Ny, Ks, Kt, r)
+    if norm is None:
+        norm = backproject(Hp, Nx, Ny, Ks, Kt, np.ones_like(f))
+    scaled = np.divide(g, norm, out=np.zeros_like(g), where=norm != 0)
+    return scaled * bp
+
+
 # --------------------------------------------------------------------------
 # numpy constructions used as independent pins
 # --------------------------------------------------------------------------

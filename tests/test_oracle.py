@@ -284,3 +284,68 @@ def test_grad_points_match_full():
         want.append(full[off[z] + ((p * Ny + q) * Ks[z] + u) * Kt[z] + v])
     got = oracle.grad_hp_points(f, r, Nx, Ny, Ks, Kt, np.array(pts))
     np.testing.assert_allclose(got, want, rtol=1e-14, atol=1e-14)
+
+
+# ---------------------------------------------------------------- Eq. (2) --
+
+def _rl_case(seed=13):
+    """Two depths with different cut-outs, a non-negative volume and image."""
+    Nx, Ny, Ks, Kt = 3, 3, [9, 3], [9, 3]
+    rng = np.random.default_rng(seed)
+    Hz = [rng.uniform(0, 1, (Nx, Ny, k, t)) for k, t in zip(Ks, Kt)]
+    H = np.concatenate([h.reshape(-1) for h in Hz])
+    Mx = My = 4
+    W = Mx * Nx
+    g = rng.uniform(0.1, 1, (len(Ks), W, W))
+    f = rng.uniform(0.1, 1, (W, W))
+    return Nx, Ny, Ks, Kt, Hz, H, g, f, Mx, My
+
+
+def test_rl_step_matches_dense_matrix():
+    """Eq. (2) against the dense measurement matrix A = [A_0 | A_1] (pattern
+    placement, zero outside the sensor): g' = g / (A^T 1) * A^T (f / (A g))."""
+    Nx, Ny, Ks, Kt, Hz, H, g, f, Mx, My = _rl_case()
+    A = np.concatenate([oracle.measurement_matrix(h, Mx, My, periodic=False) for h in Hz], axis=1)
+    fe = A @ g.reshape(-1)
+    r = f.reshape(-1) / fe
+    want = g.reshape(-1) / (A.T @ np.ones(A.shape[0])) * (A.T @ r)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    got = oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, g, f)
+    np.testing.assert_allclose(got.reshape(-1), want, rtol=1e-12, atol=0)
+
+
+def test_rl_step_fixed_point_and_flux():
+    """f = H g*  makes g* a fixed point of Eq. (2); and every update conserves
+    sum_X (H'1)(X) g'(X) = sum_S f(S) (over pixels where H g > 0)."""
+    Nx, Ny, Ks, Kt, Hz, H, g, f, Mx, My = _rl_case(14)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    g_true = g.copy()
+    g_true[:, ::3, ::2] = 0.0  # some empty voxels
+    f_true = oracle.forward(H, Nx, Ny, Ks, Kt, g_true)
+    got = oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, g_true, f_true)
+    np.testing.assert_allclose(got, g_true, rtol=1e-12, atol=1e-14)
+    norm = oracle.backproject(Hp, Nx, Ny, Ks, Kt, np.ones_like(f))
+    g1 = oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, g, f)
+    assert abs(np.sum(norm * g1) - np.sum(f)) <= 1e-12 * np.sum(f)
+
+
+def test_rl_step_homogeneity_and_zeros():
+    """Eq. (2) is linear in f and invariant to scaling g; zero voxels stay zero;
+    pixels with H g = 0 and voxels with H' 1 = 0 follow the stated readings."""
+    Nx, Ny, Ks, Kt, Hz, H, g, f, Mx, My = _rl_case(15)
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Kt)
+    g1 = oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, g, f)
+    np.testing.assert_allclose(oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, g, 2.5 * f), 2.5 * g1,
+                               rtol=1e-13)
+    np.testing.assert_allclose(oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, 3.0 * g, f), g1, rtol=1e-13)
+    assert (g1 >= 0).all()
+    gz = g.copy()
+    gz[1] = 0.0
+    assert (oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, gz, f)[1] == 0).all()
+    # an all-zero volume: H g = 0 everywhere, the quotient is 0, so is g'
+    assert (oracle.rl_step(H, Hp, Nx, Ny, Ks, Kt, np.zeros_like(g), f) == 0).all()
+    # a depth whose PSF is zero: H' 1 = 0 there, g' = 0 there
+    H0 = H.copy()
+    H0[Nx * Ny * Ks[0] * Kt[0]:] = 0.0
+    Hp0 = oracle.transpose(H0, Nx, Ny, Ks, Kt)
+    assert (oracle.rl_step(H0, Hp0, Nx, Ny, Ks, Kt, g, f)[1] == 0).all()

@@ -127,3 +127,42 @@ def test_unmutated_passes(tmp_path):
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_is_caught(tmp_path, name):
     assert not _pins_pass(_build_variant(tmp_path, name))
+
+
+# ------------------------------------------------- Eq. (2) composition slips --
+
+def _rl_variant(kind):
+    """oracle.rl_step with one plausible slip in how Eq. (2) is composed."""
+    def step(H, Hp, Nx, Ny, Ks, Kt, g, f):
+        fe = oracle.forward(H, Nx, Ny, Ks, Kt, g)
+        r = fe / f if kind == "quotient_inverted" else f / fe
+        bp_op = H if kind == "backproject_with_H" else Hp
+        bp = oracle.backproject(bp_op, Nx, Ny, Ks, Kt, r)
+        if kind == "no_normaliser":
+            return g * bp
+        norm = oracle.backproject(Hp, Nx, Ny, Ks, Kt, np.ones_like(f))
+        if kind == "normaliser_of_H":
+            norm = oracle.backproject(H, Nx, Ny, Ks, Kt, np.ones_like(f))
+        return g / norm * bp
+    return step
+
+
+@pytest.mark.parametrize("kind", ["quotient_inverted", "backproject_with_H", "no_normaliser",
+                                  "normaliser_of_H"])
+def test_rl_composition_slip_is_caught(kind):
+    """The dense-matrix pin of Eq. (2) rejects each slip (and accepts the oracle)."""
+    Nx, Ny, K = 3, 3, 9
+    rng = np.random.default_rng(16)
+    Hz = rng.uniform(0, 1, (Nx, Ny, K, K))
+    H = Hz.reshape(-1)
+    Mx = My = 4
+    W = Mx * Nx
+    g = rng.uniform(0.1, 1, (1, W, W))
+    f = rng.uniform(0.1, 1, (W, W))
+    A = oracle.measurement_matrix(Hz, Mx, My, periodic=False)
+    want = g.reshape(-1) / (A.T @ np.ones(A.shape[0])) * (A.T @ (f.reshape(-1) / (A @ g.reshape(-1))))
+    Hp = oracle.transpose(H, Nx, Ny, [K], [K])
+    ok = oracle.rl_step(H, Hp, Nx, Ny, [K], [K], g, f).reshape(-1)
+    np.testing.assert_allclose(ok, want, rtol=1e-12)
+    bad = _rl_variant(kind)(H, Hp, Nx, Ny, [K], [K], g, f).reshape(-1)
+    assert not np.allclose(bad, want, rtol=1e-6)
