@@ -4,7 +4,7 @@
  * Builds the backprojection array H' from the shift-variant light-field PSF
  * array H as the pure re-arrangement derived in Eberhart, "Efficient
  * computation of backprojection arrays for 3D light field deconvolution"
- * (arXiv 2003.09133), Sec. 3, Eqs. (4)-(9): per depth, a flip of the pixel
+ * (arXiv 2003.09133), Sec. 4, Eqs. (4)-(9): per depth, a flip of the pixel
  * axes of each cut-out combined with a cyclic exchange of the source
  * positions of the elementary cell.
  *
@@ -12,7 +12,7 @@
  * array, depth-major and ragged in depth.  Depth z holds Nx*Ny*Ks[z]*Kt[z]
  * elements in row-major [a][b][s][t] order and starts at element
  * lfbp_plan_depth_offset(plan, z).  In H, (a, b) is the source position in
- * the elementary cell (the paper's x, y; Sec. 2.1, Sec. 3) and (s, t) the
+ * the elementary cell (the paper's x, y; Sec. 2.1, Sec. 4) and (s, t) the
  * pixel of the voxel-centred cut-out (the paper's s, t).  In H', (a, b) is
  * the pixel position inside the lenslet (the paper's x', y') and (s, t) the
  * voxel of the pixel-centred window (the paper's s', t').  The paper's x
@@ -22,7 +22,7 @@
  *     H'[p][q][u][v] = H[(p+u-c_s) mod Nx][(q+v-c_t) mod Ny][Ks-1-u][Kt-1-v]
  * which is the transpose of the measurement operator of Eq. (1) stored
  * pixel-centred.  It is a permutation of each depth and its own inverse
- * (Sec. 3: processing H' gives back H).  Element values are moved as raw
+ * (Sec. 4: processing H' gives back H).  Element values are moved as raw
  * bits (fp32 or fp16 storage); no arithmetic is done on them.
  *
  * LFBP_MAP_PAPER_WINDOW reproduces the loop ranges of Eqs. (4)-(9) literally
@@ -67,7 +67,7 @@ typedef struct lfbp_plan_s* lfbp_plan; /* opaque; owned by the library */
 
 /*
  * Square elementary cell (Nx = Ny = Nnum, Ks = Kt = Kz[z]).  Nnum and every
- * Kz[z] must be odd and >= 1 (Sec. 3: n_x, n_y odd; odd n_s makes Eq. (8) a
+ * Kz[z] must be odd and >= 1 (Sec. 4: n_x, n_y odd; odd n_s makes Eq. (8) a
  * flip, see lfbp_plan_create2).  Kz is copied.  Nz = 0 makes an empty plan.
  * On success *out receives a plan to be released with lfbp_plan_destroy.
  */
@@ -75,8 +75,8 @@ int lfbp_plan_create(lfbp_plan* out, int Nnum, int Nz, const int* Kz, lfbp_dtype
                      lfbp_mode mode);
 
 /*
- * General cell (Sec. 3: "separate treatment of x and y ... allows
- * non-symmetric cases with n_x != n_y", e.g. hexagonal MLAs): Nx x Ny source
+ * General cell (Sec. 4: the x and y axes are mapped independently, so the
+ * cell may be non-square, n_x != n_y, as for hexagonal MLAs): Nx x Ny source
  * positions, per-depth cut-outs of Ks[z] x Kt[z] pixels.  All odd and >= 1;
  * Nx, Ny <= 1023 and Ks, Kt <= 16383.  Even cut-out sizes are rejected
  * (LFBP_ERR_BAD_SHAPE): Eq. (8) then drops one pixel row and the map is not
@@ -95,7 +95,7 @@ size_t lfbp_plan_depth_offset(lfbp_plan p, int z);
 int lfbp_plan_esize(lfbp_plan p);
 
 /*
- * H -> H' with one kernel launch per depth (Sec. 3: the z-planes are
+ * H -> H' with one kernel launch per depth (Sec. 4: the z-planes are
  * independent).  dH, dHp: device buffers of lfbp_plan_elems(p) elements,
  * 16-byte aligned, not overlapping (in-place is rejected with
  * LFBP_ERR_ALIAS).  The plan's mode selects the full transpose or the
@@ -107,7 +107,7 @@ int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_st
  * H -> H' from host memory to host memory.  The host->device copy of one
  * chunk of depths, the map of the previous chunk (one launch per depth) and
  * the device->host copy of the chunk before overlap on two library-owned
- * helper streams and the caller's stream (Sec. 3: the z-planes are
+ * helper streams and the caller's stream (Sec. 4: the z-planes are
  * independent, so each chunk is mapped as soon as it has arrived).
  * H_host, Hp_host: host buffers of lfbp_plan_elems(p) elements, not
  * overlapping; page-locked (pinned) memory is needed for the copies to run
@@ -182,7 +182,7 @@ int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void
  * Adjoint of the plan's map, applied to a gradient with respect to H'
  * (dHp_grad) to give the gradient with respect to H (dH_grad).  For
  * LFBP_MAP_TRANSPOSE the map is its own inverse and its own adjoint
- * (Sec. 3, reversibility), so this is the same gather; for
+ * (Sec. 4, reversibility), so this is the same gather; for
  * LFBP_MAP_PAPER_WINDOW it gathers the unmasked entries and writes zeros
  * where the forward map dropped an entry.  Buffers as for
  * lfbp_backproject_array.
@@ -221,6 +221,55 @@ int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, i
  */
 int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
                                  void* dHp_grad, void* cuda_stream);
+
+/*
+ * The same backprojection g = H' f as lfbp_backproject_volume, read straight
+ * from H without building H' (Sec. 4's map substituted into the sum; for the
+ * in-loop PSF updates of Sec. 3.1, where H' would otherwise be rebuilt every
+ * iteration):
+ *   g[z][X][Y] = sum_{s,t} f[X+s-c_s][Y+t-c_t] * H_z[X mod Nx][Y mod Ny][s][t]
+ * dH: H in the plan's layout (LFBP_F32 plans); df: [Wx][Wy]; dg: [Nz][Wx][Wy]
+ * output.  Equal to lfbp_backproject_volume on the mapped array up to the
+ * order of the fp32 sums.  Requires Kt <= 3072.
+ */
+int lfbp_backproject_volume_from_h(lfbp_plan p, const void* dH, const float* df, int Wx, int Wy,
+                                   float* dg, void* cuda_stream);
+
+/*
+ * One Richardson-Lucy update (Eq. 2):
+ *   g_next = g / (H' 1) * [H' (f / (H g))]
+ * The forward projection H g (as lfbp_forward_project) goes into dwork, is
+ * replaced there by the quotient f / (H g) -- 0 where H g = 0 --, and the
+ * quotient is backprojected with H' (as lfbp_backproject_volume); the
+ * backprojection kernel's epilogue forms g / norm * sum (0 where norm = 0).
+ * dH: H; dHp: H' = the plan's map of H (LFBP_F32 plan, transpose mode);
+ * dnorm: H' 1 as [Nz][Wx][Wy] (lfbp_rl_normaliser); df: the measured image
+ * [Wx][Wy]; dg: the estimate [Nz][Wx][Wy]; dg_next: the update, same shape --
+ * it may be dg itself (every output reads only its own g), but must not
+ * overlap any other buffer; dwork: Wx*Wy floats of caller-owned scratch.
+ * fp32 sums in a fixed order (deterministic).  Requires Kt <= 3072.
+ */
+int lfbp_rl_step(lfbp_plan p, const void* dH, const void* dHp, const float* dnorm,
+                 const float* df, int Wx, int Wy, const float* dg, float* dg_next, float* dwork,
+                 void* cuda_stream);
+
+/*
+ * The update of lfbp_rl_step with H' never built: the backprojection reads H
+ * directly (as lfbp_backproject_volume_from_h).  For estimates whose PSF
+ * changes every iteration (Sec. 3.1: physics-updated or blind
+ * deconvolution).  Arguments as for lfbp_rl_step without dHp.
+ */
+int lfbp_rl_step_fused(lfbp_plan p, const void* dH, const float* dnorm, const float* df, int Wx,
+                       int Wy, const float* dg, float* dg_next, float* dwork, void* cuda_stream);
+
+/*
+ * The normaliser of Eq. 2, H' 1: the backprojection of a ones image on the
+ * Wx x Wy sensor, into dnorm ([Nz][Wx][Wy]).  With dHp != NULL it uses H'
+ * (lfbp_backproject_volume), else H directly (lfbp_backproject_volume_from_h).
+ * dwork: Wx*Wy floats of scratch (filled with ones).
+ */
+int lfbp_rl_normaliser(lfbp_plan p, const void* dH, const void* dHp, int Wx, int Wy, float* dnorm,
+                       float* dwork, void* cuda_stream);
 
 /*
  * Synchronise the stream, then return and clear the library's device status

@@ -46,7 +46,7 @@ __all__ = [
 class ArraySpec:
     """Shape and recipe of one ragged PSF array.
 
-    Nx, Ny: lenslet-cell sizes (odd, paper Sec. 3 requires odd n_x, n_y).
+    Nx, Ny: lenslet-cell sizes (odd, paper Sec. 4 requires odd n_x, n_y).
     Ks, Kt: per-depth cut-out sizes in pixels along s and t (odd).
     radius: per-depth spot radius r_z in lenslets.
     dtype: "f32" or "f16" storage.

@@ -106,7 +106,7 @@ def transpose_adjoint(dHp: np.ndarray, Nx: int, Ny: int, Ks, Kt=None, nthreads: 
 
 
 def paper_window(H: np.ndarray, Nx: int, Ny: int, Ks, Kt=None) -> np.ndarray:
-    """Eqs. (4)-(9) with the paper's loop ranges (Sec. 3); unreached entries are 0."""
+    """Eqs. (4)-(9) with the paper's loop ranges (Sec. 4); unreached entries are 0."""
     Kt = Ks if Kt is None else Kt
     H = np.ascontiguousarray(H)
     out = np.empty_like(H)

@@ -15,16 +15,18 @@
  * paper's (x, y) dimensions -- and (s, t) the pixel inside the voxel-centred
  * cut-out.  For H', (a, b) is the pixel position inside the lenslet -- the
  * paper's (x', y') -- and (s, t) the voxel inside the pixel-centred window,
- * the paper's (s', t') (Sec. 3, Fig. 6: "the physical meaning of the
- * dimensions has been swapped").  The paper's x pairs with s and y with t.
+ * the paper's (s', t'): the two arrays have the same shape, with the roles
+ * of the cell and pixel dimensions exchanged (Sec. 3, Fig. 6).  The paper's x
+ * pairs with s and y with t.
  *
  * Functions and the passage each follows:
  *   oracle_transpose        H' as the transpose of the measurement operator of
- *                           Eq. (1) (Sec. 2.1 forward model, Sec. 3 "groups
- *                           together contributions to single image pixels").
+ *                           Eq. (1) (Sec. 2.1 forward model; Sec. 3: H'
+ *                           collects, per sensor pixel, the weights of the
+ *                           voxels that reach it).
  *   oracle_transpose_adjoint  the adjoint (scatter) of that permutation.
  *   oracle_paper_window     Eqs. (4)-(9) evaluated in the paper's 1-based
- *                           notation and loop ranges (Sec. 3, Fig. 10).
+ *                           notation and loop ranges (Sec. 4, Fig. 10).
  *   oracle_forward_f64      f = H g, Eq. (1): copies of the cut-outs of H,
  *                           scaled by the voxel values, summed on the sensor.
  *   oracle_backproject_f64  g = H' f, the backprojection used in Eq. (2).
@@ -144,7 +146,7 @@ int oracle_transpose(const void* H, void* Hp, int esize, int Nx, int Ny, int Nz,
  * Adjoint of oracle_transpose as a linear map on arrays: every output element
  * of the transpose is a copy of one input element, so the adjoint scatters
  * each element of dHp back to the H position it was copied from.  Used for
- * the gradient with respect to H of a loss on H' (Sec. 3 notes the mapping
+ * the gradient with respect to H of a loss on H' (Sec. 4 notes the mapping
  * is reversible, which the tests check separately).
  */
 int oracle_transpose_adjoint(const void* dHp, void* dH, int esize, int Nx, int Ny, int Nz,

@@ -42,6 +42,10 @@ SIGNATURES = {
     "lfbp_backproject_volume": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_forward_project": ([_P, _P, _P, _I, _I, _P, _P], _I),
     "lfbp_backproject_volume_grad": ([_P, _P, _P, _I, _I, _P, _P], _I),
+    "lfbp_backproject_volume_from_h": ([_P, _P, _P, _I, _I, _P, _P], _I),
+    "lfbp_rl_step": ([_P, _P, _P, _P, _P, _I, _I, _P, _P, _P, _P], _I),
+    "lfbp_rl_step_fused": ([_P, _P, _P, _P, _I, _I, _P, _P, _P, _P], _I),
+    "lfbp_rl_normaliser": ([_P, _P, _P, _I, _I, _P, _P, _P], _I),
     "lfbp_sync_status": ([_P], _I),
     "lfbp_last_error": ([], ctypes.c_char_p),
     "lfbp_version": ([], ctypes.c_char_p),
@@ -318,6 +322,76 @@ def backproject_volume_grad(plan: Plan, f: torch.Tensor, grad_g: torch.Tensor,
         _check(plan._lib.lfbp_backproject_volume_grad(plan.handle, f.data_ptr(), grad_g.data_ptr(),
                                                       Wx, Wy, out.data_ptr(), _stream_ptr(stream)),
                "lfbp_backproject_volume_grad")
+    return out
+
+
+def backproject_volume_from_h(plan: Plan, H: torch.Tensor, f: torch.Tensor,
+                              out: torch.Tensor = None, stream=None):
+    """g = H' f read straight from H, H' never built (``lfbp_backproject_volume_from_h``)."""
+    _check_tensor(plan, H, "H")
+    Wx, Wy = f.shape
+    _check_f32(f, (Wx, Wy), "f")
+    if out is None:
+        out = torch.empty((plan.Nz, Wx, Wy), dtype=torch.float32, device=f.device)
+    _check_f32(out, (plan.Nz, Wx, Wy), "out")
+    with torch.cuda.device(f.device):
+        _check(plan._lib.lfbp_backproject_volume_from_h(plan.handle, H.data_ptr(), f.data_ptr(),
+                                                        Wx, Wy, out.data_ptr(),
+                                                        _stream_ptr(stream)),
+               "lfbp_backproject_volume_from_h")
+    return out
+
+
+def rl_normaliser(plan: Plan, H: torch.Tensor, Hp: torch.Tensor = None, Wx: int = None,
+                  Wy: int = None, out: torch.Tensor = None, work: torch.Tensor = None,
+                  stream=None):
+    """H' 1 on a Wx x Wy sensor (``lfbp_rl_normaliser``); with Hp None, from H directly."""
+    _check_tensor(plan, H, "H")
+    if Hp is not None:
+        _check_tensor(plan, Hp, "Hp")
+    dev = H.device
+    if out is None:
+        out = torch.empty((plan.Nz, Wx, Wy), dtype=torch.float32, device=dev)
+    _check_f32(out, (plan.Nz, Wx, Wy), "out")
+    if work is None:
+        work = torch.empty((Wx, Wy), dtype=torch.float32, device=dev)
+    _check_f32(work, (Wx, Wy), "work")
+    with torch.cuda.device(dev):
+        _check(plan._lib.lfbp_rl_normaliser(plan.handle, H.data_ptr(),
+                                            Hp.data_ptr() if Hp is not None else None, Wx, Wy,
+                                            out.data_ptr(), work.data_ptr(), _stream_ptr(stream)),
+               "lfbp_rl_normaliser")
+    return out
+
+
+def rl_step(plan: Plan, H: torch.Tensor, Hp: torch.Tensor, norm: torch.Tensor, f: torch.Tensor,
+            g: torch.Tensor, out: torch.Tensor = None, work: torch.Tensor = None, stream=None):
+    """One Richardson-Lucy update, Eq. (2) (``lfbp_rl_step``; with Hp None
+    ``lfbp_rl_step_fused``, H' never built).  ``out`` may be ``g`` itself."""
+    _check_tensor(plan, H, "H")
+    Wx, Wy = f.shape
+    _check_f32(f, (Wx, Wy), "f")
+    _check_f32(g, (plan.Nz, Wx, Wy), "g")
+    _check_f32(norm, (plan.Nz, Wx, Wy), "norm")
+    if out is None:
+        out = torch.empty_like(g)
+    _check_f32(out, (plan.Nz, Wx, Wy), "out")
+    if work is None:
+        work = torch.empty((Wx, Wy), dtype=torch.float32, device=f.device)
+    _check_f32(work, (Wx, Wy), "work")
+    with torch.cuda.device(f.device):
+        if Hp is not None:
+            _check_tensor(plan, Hp, "Hp")
+            _check(plan._lib.lfbp_rl_step(plan.handle, H.data_ptr(), Hp.data_ptr(),
+                                          norm.data_ptr(), f.data_ptr(), Wx, Wy, g.data_ptr(),
+                                          out.data_ptr(), work.data_ptr(), _stream_ptr(stream)),
+                   "lfbp_rl_step")
+        else:
+            _check(plan._lib.lfbp_rl_step_fused(plan.handle, H.data_ptr(), norm.data_ptr(),
+                                                f.data_ptr(), Wx, Wy, g.data_ptr(),
+                                                out.data_ptr(), work.data_ptr(),
+                                                _stream_ptr(stream)),
+                   "lfbp_rl_step_fused")
     return out
 
 

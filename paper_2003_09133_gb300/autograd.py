@@ -1,7 +1,7 @@
 """H -> H' as a differentiable operation.
 
 Forward runs ``lfbp_backproject_array``; backward runs ``lfbp_adjoint``, the
-adjoint gather (for the full transpose the map is its own inverse, Sec. 3,
+adjoint gather (for the full transpose the map is its own inverse, Sec. 4,
 so the gradient is moved, never summed: no atomics).  This lets a loss on
 backprojected volumes be differentiated with respect to the PSF array H,
 as iterative PSF updates (Sec. 3.1) would need.

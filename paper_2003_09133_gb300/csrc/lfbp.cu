@@ -21,6 +21,7 @@
 
 #include "lfbp.h"
 #include "lfbp_device.cuh"
+#include "lfbp_project.h"
 
 namespace lfbp {
 
@@ -30,17 +31,20 @@ __device__ int g_status;
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
-constexpr int kProducerWarps = 1;  // warps sharing each tile's bulk copies
-constexpr int kConsumerWarps = 8;
+constexpr int kProducerWarps = 2;  // warps sharing each tile's bulk copies
+constexpr int kConsumerWarps = 7;
 constexpr int kPersistentThreads = 32 * (kProducerWarps + kConsumerWarps);
-constexpr int kInfoBytes = 256;  // per-stage slot for the tile descriptor and context
-static_assert(sizeof(TileDesc) + sizeof(TileCtx) <= kInfoBytes, "stage info too large");
+// Per-stage info slot: [16 B: end flag (persistent) or mbarrier (plain)]
+// [TileCtx][row-base table: kMaxTileRows + 1 ints]
+constexpr int kCtxBytes = (int)((sizeof(TileCtx) + 15) / 16 * 16);
+constexpr int kTabBytes = (4 * (kMaxTileRows + 1) + 15) / 16 * 16;
+constexpr int kInfoBytes = 16 + kCtxBytes + kTabBytes;
 constexpr int kStatusBadLaunch = -9;  // LFBP_ERR_INVALID: launched with too little shared memory
 
 // Dynamic shared memory of the plain kernel for a stage of `stage_bytes`:
-// [stage][mbarrier, 16 B][TileCtx].
+// [stage][mbarrier, 16 B][TileCtx][row-base table].
 __host__ __device__ constexpr int plain_smem_bytes(int stage_bytes) {
-  return stage_bytes + 16 + kInfoBytes;
+  return stage_bytes + kInfoBytes;
 }
 // ... and of the persistent kernel: [stages][per-stage info][full, empty barriers].
 __host__ __device__ constexpr int persistent_smem_bytes(int stage_bytes, int nstages) {
@@ -59,7 +63,7 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, c
 // grid = (nV, Nx, nU) tiles of one depth; block = kPlainThreads; one tile per
 // CTA.  `base` carries the depth's shape, pitch and flags; the CTA fills in
 // its own p, u0, v0, nrows, ncols.
-// smem: [stage: tile bytes][mbarrier][TileCtx]
+// smem: [stage: tile bytes][mbarrier][TileCtx][row-base table]
 __global__ void __launch_bounds__(kPlainThreads)
     k_gather_depth(TileDesc base, const unsigned char* __restrict__ in_depth,
                    const unsigned char* in_safe_end, unsigned char* __restrict__ out_depth, int J,
@@ -68,6 +72,7 @@ __global__ void __launch_bounds__(kPlainThreads)
   unsigned char* stage = smem;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes);
   TileCtx* ctx = reinterpret_cast<TileCtx*>(smem + stage_bytes + 16);
+  int* tab = reinterpret_cast<int*>(smem + stage_bytes + 16 + kCtxBytes);
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (dynamic_smem_size() < (uint32_t)plain_smem_bytes(stage_bytes)) {
@@ -90,10 +95,14 @@ __global__ void __launch_bounds__(kPlainThreads)
     mbar_init(b, kWarps);
     fence_mbar_init();
   }
-  if (warp == 1 && lane < 8) make_ctx_lane(*ctx, td, stage, in_depth, out_depth, lane);
   __syncthreads();
-  // every warp issues a share of the tile's copies, then all wait for them
+  // every warp issues a share of the tile's copies; the tile context is built
+  // while they are in flight; then all wait for them
   issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane, warp, kWarps);
+  __syncwarp();
+  if (lane == 0) mbar_arrive(b);
+  if (warp == 1 && lane < 8) make_ctx_lane(*ctx, td, stage, in_depth, out_depth, tab, lane);
+  __syncthreads();
   if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
     set_status(kStatusTimeout);
     abort_flag = 1;
@@ -118,7 +127,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
                         const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
                         int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
-  unsigned char* info_base = smem + (size_t)nstages * stage_bytes;  // per stage: flag, TileCtx
+  unsigned char* info_base = smem + (size_t)nstages * stage_bytes;  // per stage: flag, TileCtx, table
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * (stage_bytes + kInfoBytes));
   uint64_t* empty = full + nstages;
   __shared__ int abort_flag;
@@ -171,16 +180,19 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       const unsigned char* in_arr = ptrs.in[td.arr];
       const unsigned char* in_depth = in_arr + td.off_bytes;
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
+      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
+                       kProducerWarps);
+      // the tile context is built while the copies are in flight
       if (warp == 0) {
         unsigned char* info = info_base + (size_t)s * kInfoBytes;
         if (lane == 0) *reinterpret_cast<int*>(info) = 0;
         if (lane < 8)
           make_ctx_lane(*reinterpret_cast<TileCtx*>(info + 16), td, smem + (size_t)s * stage_bytes,
-                        in_depth, ptrs.out[td.arr] + td.off_bytes, lane);
+                        in_depth, ptrs.out[td.arr] + td.off_bytes,
+                        reinterpret_cast<int*>(info + 16 + kCtxBytes), lane);
       }
       __syncwarp();
-      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
-                       kProducerWarps);
+      if (lane == 0) mbar_arrive(fb);
       td = next;
     }
     // make sure no copy into this CTA's shared memory is still in flight (the
@@ -208,9 +220,10 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       }
       const unsigned char* info = info_base + (size_t)s * kInfoBytes;
       if (*reinterpret_cast<const int*>(info) != 0) break;
-      // rotate the item-to-warp assignment by the tile's item count
+      // rotate the step-to-warp assignment by the tile's step count
       const TileCtx& tc = *reinterpret_cast<const TileCtx*>(info + 16);
-      gather_tile_ctx(tc, cw, kConsumerWarps, lane, (it * tc.items) % kConsumerWarps);
+      const int nsteps = tc.fast ? tc.nunits : tc.items;
+      gather_tile_ctx(tc, cw, kConsumerWarps, lane, (it * nsteps) % kConsumerWarps);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
     }
@@ -220,13 +233,6 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
 }  // namespace lfbp
 
 // ====================================================================== host
-namespace lfbp {
-int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, const float* in,
-                             int Wx, int Wy, float* out, int accumulate, cudaStream_t st);
-int launch_backproject_grad(const float* f, const float* dg, int Nx, int Ny, int Ks, int Kt,
-                            int Wx, int Wy, float* dA, cudaStream_t st);
-}  // namespace lfbp
-
 using namespace lfbp;
 
 struct lfbp_plan_s {
@@ -1102,6 +1108,107 @@ int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgra
                                 Wx, Wy, out + p->off[z], (cudaStream_t)cuda_stream))
       return fail(LFBP_ERR_CUDA, "k_backproject_grad launch failed");
   }
+  return LFBP_OK;
+}
+
+int lfbp_backproject_volume_from_h(lfbp_plan p, const void* dH, const float* df, int Wx, int Wy,
+                                   float* dg, void* cuda_stream) {
+  int rc = check_projector(p, dH, df, dg, Wx, Wy, (size_t)(p ? p->Nz : 0) * Wx * Wy * 4);
+  if (rc) return rc;
+  if (overlaps(df, (size_t)Wx * Wy * 4, dg, (size_t)p->Nz * Wx * Wy * 4))
+    return fail(LFBP_ERR_ALIAS, "output overlaps an input");
+  const float* h = (const float*)dH;
+  for (int z = 0; z < p->Nz; ++z) {
+    if (launch_projector(1, kEpiStore, h + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z], df, Wx, Wy,
+                         dg + (size_t)z * Wx * Wy, nullptr, nullptr, (cudaStream_t)cuda_stream))
+      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
+  }
+  return LFBP_OK;
+}
+
+namespace {
+
+bool misaligned4(const void* a) { return ((uintptr_t)a & 3) != 0; }
+
+// One Richardson-Lucy update (Eq. 2); dHp == nullptr: backprojection from H.
+int rl_step_impl(lfbp_plan p, const void* dH, const void* dHp, const float* dnorm,
+                 const float* df, int Wx, int Wy, const float* dg, float* dg_next, float* dwork,
+                 cudaStream_t st) {
+  int rc = check_projector(p, dH, df, dwork, Wx, Wy, (size_t)Wx * Wy * 4);
+  if (rc) return rc;
+  if (!dnorm || !dg || !dg_next) return fail(LFBP_ERR_NULL, "buffer pointer is NULL");
+  if (misaligned4(dnorm) || misaligned4(dg) || misaligned4(dg_next) || misaligned4(dHp))
+    return fail(LFBP_ERR_ALIGN, "buffers must be 4-byte aligned");
+  const size_t img = (size_t)Wx * Wy * 4, vol = (size_t)p->Nz * img, hb = p->off.back() * 4;
+  // the scratch image overlaps nothing; the new estimate overlaps nothing but
+  // (exactly) the old one
+  const void* reads[] = {df, dnorm, dg, dHp};
+  const size_t rbytes[] = {img, vol, vol, hb};
+  for (int i = 0; i < 4; ++i)
+    if (reads[i] && overlaps(reads[i], rbytes[i], dwork, img))
+      return fail(LFBP_ERR_ALIAS, "dwork overlaps another buffer");
+  if (overlaps(dwork, img, dg_next, vol)) return fail(LFBP_ERR_ALIAS, "dwork overlaps dg_next");
+  if (overlaps(dH, hb, dg_next, vol) || (dHp && overlaps(dHp, hb, dg_next, vol)) ||
+      overlaps(dnorm, vol, dg_next, vol) || overlaps(df, img, dg_next, vol))
+    return fail(LFBP_ERR_ALIAS, "dg_next overlaps an input");
+  if ((const void*)dg != (const void*)dg_next && overlaps(dg, vol, dg_next, vol))
+    return fail(LFBP_ERR_ALIAS, "dg_next overlaps dg without being dg");
+  const float* h = (const float*)dH;
+  const float* hp = (const float*)dHp;
+  // H g, summed over depths in order
+  if (p->Nz == 0) {
+    cudaError_t e = cudaMemsetAsync(dwork, 0, img, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  }
+  for (int z = 0; z < p->Nz; ++z)
+    if (launch_projector(0, z ? kEpiAccumulate : kEpiStore, h + p->off[z], p->Nx, p->Ny, p->Ks[z],
+                         p->Kt[z], dg + (size_t)z * Wx * Wy, Wx, Wy, dwork, nullptr, nullptr, st))
+      return fail(LFBP_ERR_CUDA, "forward projection launch failed");
+  // f / (H g)
+  if (launch_rl_quotient(df, dwork, (long long)Wx * Wy, st))
+    return fail(LFBP_ERR_CUDA, "k_rl_quotient launch failed");
+  // g / (H'1) * H' (f / (H g)), depth by depth
+  for (int z = 0; z < p->Nz; ++z) {
+    const size_t o = (size_t)z * Wx * Wy;
+    if (launch_projector(hp ? 0 : 1, kEpiRL, (hp ? hp : h) + p->off[z], p->Nx, p->Ny, p->Ks[z],
+                         p->Kt[z], dwork, Wx, Wy, dg_next + o, dg + o, dnorm + o, st))
+      return fail(LFBP_ERR_CUDA, "backprojection launch failed");
+  }
+  return LFBP_OK;
+}
+
+}  // namespace
+
+int lfbp_rl_step(lfbp_plan p, const void* dH, const void* dHp, const float* dnorm,
+                 const float* df, int Wx, int Wy, const float* dg, float* dg_next, float* dwork,
+                 void* cuda_stream) {
+  if (!dHp) return fail(LFBP_ERR_NULL, "dHp is NULL (lfbp_rl_step_fused needs no H')");
+  return rl_step_impl(p, dH, dHp, dnorm, df, Wx, Wy, dg, dg_next, dwork,
+                      (cudaStream_t)cuda_stream);
+}
+
+int lfbp_rl_step_fused(lfbp_plan p, const void* dH, const float* dnorm, const float* df, int Wx,
+                       int Wy, const float* dg, float* dg_next, float* dwork, void* cuda_stream) {
+  return rl_step_impl(p, dH, nullptr, dnorm, df, Wx, Wy, dg, dg_next, dwork,
+                      (cudaStream_t)cuda_stream);
+}
+
+int lfbp_rl_normaliser(lfbp_plan p, const void* dH, const void* dHp, int Wx, int Wy, float* dnorm,
+                       float* dwork, void* cuda_stream) {
+  const void* A = dHp ? dHp : dH;
+  int rc = check_projector(p, A, dwork, dnorm, Wx, Wy, (size_t)(p ? p->Nz : 0) * Wx * Wy * 4);
+  if (rc) return rc;
+  const size_t img = (size_t)Wx * Wy * 4;
+  if (overlaps(dwork, img, dnorm, (size_t)p->Nz * img))
+    return fail(LFBP_ERR_ALIAS, "dwork overlaps dnorm");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (launch_fill(dwork, (long long)Wx * Wy, 1.0f, st))
+    return fail(LFBP_ERR_CUDA, "k_fill launch failed");
+  const float* a = (const float*)A;
+  for (int z = 0; z < p->Nz; ++z)
+    if (launch_projector(dHp ? 0 : 1, kEpiStore, a + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z],
+                         dwork, Wx, Wy, dnorm + (size_t)z * Wx * Wy, nullptr, nullptr, st))
+      return fail(LFBP_ERR_CUDA, "backprojection launch failed");
   return LFBP_OK;
 }
 

@@ -1,6 +1,6 @@
 // Device building blocks of the H -> H' gather (sm_103a).
 //
-// The map of one depth (Sec. 3, Eqs. 4-9, as a full permutation):
+// The map of one depth (Sec. 4, Eqs. 4-9, as a full permutation):
 //     H'[p][q][u][v] = H[(p+u-c_s) mod Nx][(q+v-c_t) mod Ny][Ks-1-u][Kt-1-v]
 // factorises into a row part acting on (a, s) and a column part acting on
 // (b, t).  An output "row" (p, u) is Ny runs of Kt contiguous elements (one
@@ -24,10 +24,14 @@
 // picks the one with the fewest shared-memory bank conflicts for the gather's
 // access pattern (choose_pitch).
 //
-// GATHER.  Each consumer warp instruction serves 4 output runs q..q+3 with 8
-// lanes each: 8 consecutive fp32 elements, or 8 consecutive fp16 pairs, i.e.
-// one aligned 32-byte sector per run.  The four runs sit at different 16-byte
-// phases in shared memory, which spreads a warp's loads over the banks.
+// GATHER.  The output runs of a tile are cut into aligned 128-byte lines; a
+// consumer warp step covers 4 consecutive lines (of one run, or straddling
+// two), each lane one 16-byte chunk: 4 fp32 or 8 fp16 consecutive output
+// elements, written with one 16-byte store.  Inside a row, consecutive output
+// elements are diagonal neighbours (b+1, t-1) in the stage, one slot pitch
+// minus one element apart, so a chunk's shared-memory addresses follow from
+// its first one by adding that stride, corrected where the chunk wraps from
+// segment Ny-1 to 0 or crosses into the next row (branch-free selects).
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -37,6 +41,8 @@ namespace lfbp {
 constexpr int kMaxBatch = 64;       // arrays per batched launch
 constexpr int kStatusTimeout = -7;  // LFBP_ERR_TIMEOUT
 constexpr int kGroupsPerItem = 4;   // 128-byte groups per run handled by one consumer work item
+                                    // (element-walk path)
+constexpr int kMaxTileRows = 64;    // rows per tile (bounds the per-tile row-base table)
 
 // One tile, self-contained (32 bytes).
 struct TileDesc {
@@ -81,41 +87,41 @@ __host__ __device__ inline int row_pitch(int Ny, int P, int es) {
 }
 
 // ------------------------------------------------------------ host planning --
+// Element order of a lane's chunk in its loads: fp32 lanes whose lane bit 1
+// is set load the two halves swapped, which spreads the diagonal's addresses
+// over more banks (the diagonal stride P-1 is a multiple of 4 for the odd K
+// of the map, so chunks of consecutive lanes otherwise meet in few banks).
+__host__ __device__ inline int chunk_swap(int es, int lane) {
+  return (es == 4 && ((lane >> 1) & 1)) ? 2 : 0;
+}
+
 // Shared-memory bank wavefronts of the gather for one slot pitch P, averaged
-// over pseudo-random run phases and positions (the phases depend on buffer
-// addresses unknown at planning time).  Mirrors the consumer's lane mapping.
+// over pseudo-random segment phases and positions (they depend on buffer
+// addresses unknown at planning time).  Mirrors the consumer's lane mapping:
+// lane l of a warp step takes the chunk of elements e0 + l*EPL .. of one row.
 inline double pitch_cost(int Ny, int Ks, int Kt, int ncols, int es, int P) {
-  const int epl = 16 / es, SE = 8 * epl, E = 16 / es;
-  const long long KK = (long long)Ks * Kt;
-  const int ct = (Kt - 1) / 2;
-  const int cb = ((0 - ct) % Ny + Ny) % Ny;
+  const int epl = 16 / es, E = 16 / es;
+  (void)Ks;
+  (void)Kt;
   uint32_t rng = 0x9e3779b9u ^ (uint32_t)((uint32_t)P * 2654435761u);
   long long total = 0;
   int count = 0;
   for (int trial = 0; trial < 48; ++trial) {
     rng = rng * 1664525u + 1013904223u;
-    const int q0 = (int)((rng >> 8) % (uint32_t)Ny);
-    rng = rng * 1664525u + 1013904223u;
-    const int out0 = (int)((rng >> 8) % 4096u);
+    const int b0 = (int)((rng >> 8) % (uint32_t)Ny);
     rng = rng * 1664525u + 1013904223u;
     const int R = (int)((rng >> 8) % 64u) * E + (int)((rng >> 20) % (uint32_t)E);
     rng = rng * 1664525u + 1013904223u;
-    const int ngroups = lfbp_max(1, ncols / SE);
-    const int g = (int)((rng >> 8) % (uint32_t)ngroups);
+    const int e0 = (int)((rng >> 8) % (uint32_t)lfbp_max(1, ncols - 32 * epl));
     for (int sub = 0; sub < epl; ++sub) {
       long long words[32];
       int n = 0;
-      for (int r = 0; r < 4; ++r) {
-        const int q = q0 + r;
-        if (q >= Ny) continue;
-        const int m = (int)((out0 + (long long)q * KK) % SE);
-        for (int k = 0; k < 8; ++k) {
-          const int vl = g * SE + k * epl + sub - m;
-          if (vl < 0 || vl >= ncols) continue;
-          const int b = (int)(((long long)q + cb + vl) % Ny);
-          const long long idx = (long long)R + (long long)b * P + ncols - 1 - vl;
-          words[n++] = (idx * es) / 4;
-        }
+      for (int l = 0; l < 32; ++l) {
+        const int vl = e0 + l * epl + (sub ^ chunk_swap(es, l));
+        if (vl >= ncols) continue;
+        const int b = (b0 + vl) % Ny;
+        const long long idx = (long long)R + (long long)b * P + ncols - 1 - vl;
+        words[n++] = (idx * es) / 4;
       }
       int worst = 0;
       for (int bank = 0; bank < 32; ++bank) {
@@ -171,7 +177,7 @@ inline DepthTiling tile_depth(int Ny, int Ks, int Kt, int es, int target) {
   if (row <= target) {
     d.V = Kt;
     d.nV = 1;
-    const int J = lfbp_max(1, lfbp_min(Ks, target / row));
+    const int J = lfbp_max(1, lfbp_min(lfbp_min(Ks, kMaxTileRows), target / row));
     d.nU = (Ks + J - 1) / J;
     d.J = (Ks + d.nU - 1) / d.nU;
   } else {
@@ -337,19 +343,20 @@ __device__ __forceinline__ int pos_mod(int x, int n) {
   return r < 0 ? r + n : r;
 }
 
-// Producer side: issue the bulk copies of the tile's input segments into the
-// stage.  Called by all 32 lanes of each of `np` warps; lane i of warp pw
+// Producer side: the bulk copies of the tile's input segments into the stage.
+// Shared by all 32 lanes of each of `np` warps; lane i of warp pw
 // (0 <= pw < np) takes slots pw*32 + i, pw*32 + i + 32*np, ... (slot = j*Ny + b).
 // A warp's bulk copies are accepted one lane at a time, so the copies of a
-// tile with many short segments are spread over several warps.  Each lane
-// registers the bytes of its own copies on `bar` before issuing them, and lane
-// 0 of each warp arrives once after its lanes are done (`bar` counts np
-// arrivals).  The last <16 bytes of an array that a 16-byte-widened copy
-// would over-read are copied with ordinary loads instead.
-__device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsigned char* in_depth,
-                                                 const unsigned char* in_safe_end,
-                                                 unsigned char* stage, uint32_t bar, int lane,
-                                                 int pw, int np) {
+// tile with many short segments can be spread over several warps.
+// tile_copies(..., count_only = true) returns the bytes this lane's copies
+// bring in (for the barrier's expected transaction count) without issuing
+// them; with count_only = false it issues them.  The last <16 bytes of an
+// array that a 16-byte-widened copy would over-read are copied with ordinary
+// loads instead.
+__device__ __forceinline__ uint32_t tile_copies(const TileDesc& td, const unsigned char* in_depth,
+                                                const unsigned char* in_safe_end,
+                                                unsigned char* stage, uint32_t bar, int lane,
+                                                int pw, int np, bool count_only) {
   const int es = (td.flags & 1) ? 2 : 4, E = 16 / es;
   const int Nx = td.Nx, Ny = td.Ny, Ks = td.Ks, Kt = td.Kt, P = td.P;
   const int RP = row_pitch(Ny, P, es);
@@ -370,19 +377,21 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
   // a_j = (p + u0 + j - c_s) mod Nx and s_j = Ks - 1 - u0 - j
   const int slot0 = pw * 32 + lane, slot_step = 32 * np;
   uint32_t my_bytes = 0;
-  for (int i = slot0; i < nslots; i += slot_step) {
-    const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
-    const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
-    const unsigned long long seg =
-        (unsigned long long)a * NKK + (unsigned long long)b * KK +
-        (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
-    const uintptr_t src = (uintptr_t)(in_depth + seg * es);
-    const uintptr_t lo = src & ~(uintptr_t)15;
-    uintptr_t hi = (src + seg_bytes + 15) & ~(uintptr_t)15;
-    if (hi > (uintptr_t)in_safe_end) hi = (uintptr_t)in_safe_end;
-    if (hi > lo) my_bytes += (uint32_t)(hi - lo);
+  if (count_only) {
+    for (int i = slot0; i < nslots; i += slot_step) {
+      const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
+      const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
+      const unsigned long long seg =
+          (unsigned long long)a * NKK + (unsigned long long)b * KK +
+          (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
+      const uintptr_t src = (uintptr_t)(in_depth + seg * es);
+      const uintptr_t lo = src & ~(uintptr_t)15;
+      uintptr_t hi = (src + seg_bytes + 15) & ~(uintptr_t)15;
+      if (hi > (uintptr_t)in_safe_end) hi = (uintptr_t)in_safe_end;
+      if (hi > lo) my_bytes += (uint32_t)(hi - lo);
+    }
+    return my_bytes;
   }
-  if (my_bytes) mbar_expect_tx(bar, my_bytes);
   bool fixed = false;
   for (int i = slot0; i < nslots; i += slot_step) {
     const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
@@ -428,9 +437,24 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
     if (hi > lo) bulk_g2s(smem_addr(dst), (const void*)lo, (uint32_t)(hi - lo), bar);
   }
   if (fixed) fence_proxy_async_smem();
-  __syncwarp();
-  if (lane == 0) mbar_arrive(bar);
+  return 0;
 }
+
+#ifndef LFBP_HOST_EMULATION
+// One warp's share of the tile's copies: the bytes of all its lanes are
+// registered on `bar` with one expect_tx, then the copies are issued.  The
+// caller arrives on `bar` afterwards (once per warp).
+__device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsigned char* in_depth,
+                                                 const unsigned char* in_safe_end,
+                                                 unsigned char* stage, uint32_t bar, int lane,
+                                                 int pw, int np) {
+  const uint32_t mine = tile_copies(td, in_depth, in_safe_end, stage, bar, lane, pw, np, true);
+  const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0 && total) mbar_expect_tx(bar, total);
+  __syncwarp();
+  tile_copies(td, in_depth, in_safe_end, stage, bar, lane, pw, np, false);
+}
+#endif
 
 // Tile constants derived from the descriptor: computed once per tile by the
 // eight lanes of one warp (make_ctx_lane) into shared memory, and copied into
@@ -456,22 +480,49 @@ struct alignas(16) TileCtx {
   int kks;   // (Ks*Kt) mod 128/es
   int sbn;   // (128/es) mod Ny
   int cmn;   // ncols mod Ny
-  int ngc;   // work items per run
+  int ngc;   // work items per run (element-walk path)
   int items;
   int es, mode;
-  FastDiv fncols, fNy, fNx, fngc;
+  // chunk path
+  uint32_t tab_s;  // shared-memory address of the row-base table: nrows + 1 ints
+  int nrows;
+  int rb0;         // row base of row 0 (elements): R_0 + ncols - 1
+  int cbb;         // cb plus a multiple of Ny that is >= 128/es
+  int ngm;         // 128-byte lines per run (any alignment), at least 2
+  int nunits;      // warp steps of the tile: ceil(Ny * ngm / 4)
+  uint32_t D;      // bytes between diagonal neighbours: (P - 1) * es
+  uint32_t W;      // bytes of Ny slots: Ny * P * es
+  int fast;        // 1: chunk path (mode 0, ncols >= 16/es, Ny >= 16/es)
+  FastDiv fncols, fNy, fNx, fngc, fngm;
 };
+
+// Row base of tile row j (elements): the stage index of element t_lo + ncols - 1
+// of segment (j, 0), i.e. j*RP + R_j + ncols - 1 with R_j the 16-byte phase of
+// that segment's first element.  Row j of segment b then holds output column
+// vl at  row_base(j) + b*P - vl.  Defined for j = nrows as well (the entry
+// past the last row is read but never dereferenced).
+__device__ __forceinline__ int row_base(const TileDesc& td, const unsigned char* in_depth, int j) {
+  const int ES = (td.flags & 1) ? 2 : 4, E = 16 / ES;
+  const long long KK = (long long)td.Ks * td.Kt;
+  const int a = pos_mod((int)td.p + (int)td.u0 + j - (td.Ks - 1) / 2, td.Nx);
+  const long long t_lo = (long long)td.Kt - td.v0 - td.ncols;
+  const long long seg0 = (long long)a * td.Ny * KK + (long long)(td.Ks - 1 - td.u0 - j) * td.Kt + t_lo;
+  const int ph = (int)(((long long)((uintptr_t)in_depth / ES) + seg0) & (E - 1));
+  return j * row_pitch(td.Ny, td.P, ES) + ph + td.ncols - 1;
+}
 
 // Lane `lane` (0..7) of a warp fills its share of the tile context; the
 // shares are independent, so the eight lanes run the divisions in parallel.
+// `tab` (shared memory, kMaxTileRows + 1 ints) receives the row-base table.
 __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
                                               const unsigned char* stage,
                                               const unsigned char* in_depth,
-                                              unsigned char* out_depth, int lane) {
+                                              unsigned char* out_depth, int* tab, int lane) {
   const int ES = (td.flags & 1) ? 2 : 4;
   const int E = 16 / ES, GE = 128 / ES;  // GE: elements per run per gather group
   const unsigned long long KK = (unsigned long long)td.Ks * td.Kt;
   const int L = td.nrows * td.ncols;
+  for (int j = lane; j <= td.nrows; j += 8) tab[j] = row_base(td, in_depth, j);
   switch (lane) {
     case 0:
       c.es = ES;
@@ -490,9 +541,15 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       c.u0 = td.u0;
       c.v0 = td.v0;
       c.s0 = td.Ks - 1 - td.u0;
+      c.nrows = td.nrows;
+      c.tab_s = smem_addr(tab);
+      c.fast = c.mode == 0 && td.ncols >= E && td.Ny >= E;
       break;
     case 1:
       c.fncols = make_fastdiv(td.ncols);
+      c.rb0 = row_base(td, in_depth, 0);
+      c.D = (uint32_t)(td.P - 1) * ES;
+      c.W = (uint32_t)td.Ny * td.P * ES;
       break;
     case 2:
       c.fNy = make_fastdiv(td.Ny);
@@ -508,10 +565,14 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       c.ngc = ngc;
       c.items = ((td.Ny + 3) >> 2) * ngc;
       c.fngc = make_fastdiv(ngc);
+      c.ngm = ng < 2 ? 2 : ng;
+      c.nunits = (td.Ny * c.ngm + 3) >> 2;
+      c.fngm = make_fastdiv(c.ngm);
       break;
     }
     case 5:
       c.cb = pos_mod((int)td.v0 - (td.Kt - 1) / 2, td.Ny);
+      c.cbb = c.cb + ((GE + td.Ny - 1) / td.Ny) * td.Ny;
       c.ap0 = pos_mod((int)td.p + (int)td.u0 - (td.Ks - 1) / 2, td.Nx);
       break;
     case 6: {
@@ -539,8 +600,9 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
 
 // The whole context from one thread (used where no warp is at hand).
 __device__ __forceinline__ void make_ctx(TileCtx& c, const TileDesc& td, const unsigned char* stage,
-                                         const unsigned char* in_depth, unsigned char* out_depth) {
-  for (int l = 0; l < 8; ++l) make_ctx_lane(c, td, stage, in_depth, out_depth, l);
+                                         const unsigned char* in_depth, unsigned char* out_depth,
+                                         int* tab) {
+  for (int l = 0; l < 8; ++l) make_ctx_lane(c, td, stage, in_depth, out_depth, tab, l);
 }
 
 template <class T>
@@ -635,8 +697,120 @@ __device__ __forceinline__ bool keep_elem(const TileCtx& c, int q, int j, int vl
   return as >= hx && as <= c.Ks - 1 + hx && bt >= hy && bt <= c.Kt - 1 + hy;
 }
 
-// Consumer side: gather the tile from the stage through the index map and
-// write its Ny output runs with 16-byte stores.  `w` is this warp's index
+// n / d for d >= 2 (no special case for d = 1); exact while n*d < 2^32.
+__device__ __forceinline__ uint32_t fdiv2(uint32_t n, FastDiv f) { return __umulhi(n, f.m); }
+__device__ __forceinline__ uint32_t fmod2(uint32_t n, FastDiv f) { return n - fdiv2(n, f) * f.d; }
+
+template <class T>
+__device__ __forceinline__ T smem_load_at(const TileCtx& c, uint32_t addr) {
+#if LFBP_CHECKED
+  const long long rel = (long long)addr - (long long)c.stage_s;
+  if (rel < 0 || rel + (long long)sizeof(T) > c.tile_bytes) {
+    check_fail(1, rel, c.tile_bytes);
+    return (T)0;
+  }
+#endif
+  (void)c;
+  return lds<T>(addr);
+}
+
+// Entry j (0 <= j <= nrows) of the tile's row-base table.
+__device__ __forceinline__ int tab_load(const TileCtx& c, int j) {
+#if LFBP_CHECKED
+  if (j < 0 || j > c.nrows) {
+    check_fail(5, j, c.nrows);
+    return 0;
+  }
+#endif
+  return (int)lds<uint32_t>(c.tab_s + 4u * (uint32_t)j);
+}
+
+// Consumer side, chunk path (transpose mode, ncols >= 16/es, Ny >= 16/es).
+// The tile's Ny runs are cut into ngm aligned 128-byte lines each (lines past
+// a run's end are skipped); warp step u covers lines 4u .. 4u+3 of the
+// flattened (run, line) sequence, 8 lanes per line, one 16-byte chunk per
+// lane.  Chunk element k of run element e + k sits in row j, column vl + k
+// (or, past the row end, in row j+1), segment b + k mod Ny:
+//     address = A + k*D - W*[k >= Ny - b]                 (same row)
+//             = B + k*D - W*[k >= kx + Ny - bq0]          (next row, k >= kx)
+// with D the diagonal stride, W the bytes of Ny slots, kx = ncols - vl and bq0
+// the segment of column 0.  At most one wrap and one row crossing fall in a
+// chunk because Ny and ncols are at least its element count.  Chunks cut by
+// a run's ends store element by element.  `rot` rotates the step-to-warp
+// assignment from tile to tile so that the warps share the remainder steps.
+template <int ES, bool ONEROW>
+__device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarps, int lane,
+                                              int rot) {
+  using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
+  constexpr int EPL = 16 / ES;  // elements per chunk
+  constexpr int GE = 8 * EPL;   // elements per 128-byte line
+  const int r = lane >> 3;
+  const int lane_el = (lane & 7) * EPL;
+  const int sw = chunk_swap(ES, lane);  // load order: element k ^ sw
+  const int Ny = c.Ny, L = c.L, ncols = c.ncols, P = c.P;
+  const uint32_t D = c.D, W = c.W;
+  int first = (w - rot) % nwarps;
+  if (first < 0) first += nwarps;
+  for (int u = first; u < c.nunits; u += nwarps) {
+    const int f = u * 4 + r;
+    const int q = (int)fdiv2((uint32_t)f, c.fngm);
+    if (q >= Ny) continue;
+    const int g = f - q * c.ngm;
+    const int m = (c.om0 + q * c.kks) & (GE - 1);  // run q's first element within its line
+    const int e = g * GE + lane_el - m;            // run element of chunk element 0
+    if (e >= L || e <= -EPL) continue;
+    unsigned char* dst = c.out_run0 + (long long)q * c.run_stride + (long long)e * ES;
+    int vl = e, rbj = c.rb0, kx = EPL, kw2 = 0;
+    uint32_t B = 0;
+    if (!ONEROW) {
+      const int j = e > 0 ? (int)fdiv2((uint32_t)e, c.fncols) : 0;
+      vl = e - j * ncols;
+      rbj = tab_load(c, j);
+      const int rbn = tab_load(c, j + 1);
+      kx = ncols - vl;
+      int bq0 = q + c.cb;
+      if (bq0 >= Ny) bq0 -= Ny;
+      B = c.stage_s + (uint32_t)(rbn + bq0 * P) * ES - (uint32_t)kx * D;
+      kw2 = kx + Ny - bq0;
+    }
+    const int b = (int)fmod2((uint32_t)(q + c.cbb + vl), c.fNy);
+    const int kw = Ny - b;
+    const uint32_t A = c.stage_s + (uint32_t)(rbj + b * P - vl) * ES;
+    auto addr_of = [&](int kk) -> uint32_t {
+      if (ONEROW) return A + (uint32_t)kk * D - (kk >= kw ? W : 0u);
+      const bool nxt = kk >= kx;
+      const uint32_t base = nxt ? B : A;
+      const int wk = nxt ? kw2 : kw;
+      return base + (uint32_t)kk * D - (kk >= wk ? W : 0u);
+    };
+    if (e >= 0 && e + EPL <= L) {
+      T v[EPL];
+      static_for<0, EPL>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = smem_load_at<T>(c, addr_of(k ^ sw));
+      });
+      if (ES == 4) {  // back into element order
+        T o[EPL];
+#pragma unroll
+        for (int i = 0; i < EPL; ++i) o[i] = sw ? v[i ^ 2] : v[i];
+        store_out16(c, dst, pack16(o));
+      } else {
+        store_out16(c, dst, pack16(v));
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < EPL; ++k) {
+        const int kk = k ^ sw;
+        if (e + kk < 0 || e + kk >= L) continue;
+        store_out(c, reinterpret_cast<T*>(dst) + kk, smem_load_at<T>(c, addr_of(kk)));
+      }
+    }
+  }
+}
+
+// Consumer side, element-walk path (paper-window modes, and tiles whose rows
+// or cells are shorter than a chunk): gather the tile from the stage through
+// the index map and write its Ny output runs with 16-byte stores.  `w` is this warp's index
 // among the `nwarps` consumer warps of the CTA; `rot` rotates the item-to-warp
 // assignment from tile to tile so that the warps share the remainder items.
 // Work item = 4 runs x kGroupsPerItem groups; a group is one 128-byte stretch
@@ -734,6 +908,20 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
 __device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane,
                                                 int rot = 0) {
   const TileCtx c = cs;  // into registers, once per tile
+  if (c.fast) {
+    if (c.es == 4) {
+      if (c.nrows == 1)
+        gather_chunks<4, true>(c, w, nwarps, lane, rot);
+      else
+        gather_chunks<4, false>(c, w, nwarps, lane, rot);
+    } else {
+      if (c.nrows == 1)
+        gather_chunks<2, true>(c, w, nwarps, lane, rot);
+      else
+        gather_chunks<2, false>(c, w, nwarps, lane, rot);
+    }
+    return;
+  }
   if (c.es == 4) {
     if (c.mode == 0)
       gather_tile<4, 0>(c, w, nwarps, lane, rot);

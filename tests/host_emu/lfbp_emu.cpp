@@ -34,6 +34,11 @@ size_t g_out_bytes = 0;
 unsigned char* g_counts = nullptr;
 unsigned char* g_stage = nullptr;
 size_t g_stage_bytes = 0;
+// the tile's row-base table: a second shared-memory region, mapped to
+// emulated addresses kTabBase + byte offset
+constexpr uint32_t kTabBase = 0x40000000u;
+unsigned char* g_tab = nullptr;
+size_t g_tab_bytes = 0;
 unsigned long long g_expect = 0, g_copied = 0, g_arrive = 0;
 long g_errors = 0;
 char g_msg[512] = {0};
@@ -60,6 +65,7 @@ static inline unsigned short __ldg(const unsigned short* p) {
 namespace lfbp {
 static inline uint32_t smem_addr(const void* p) {
   const unsigned char* c = (const unsigned char*)p;
+  if (c >= g_tab && c < g_tab + g_tab_bytes) return kTabBase + (uint32_t)(c - g_tab);
   if (c < g_stage || c > g_stage + g_stage_bytes) err("smem_addr outside stage", c - g_stage, 0);
   return (uint32_t)(c - g_stage);
 }
@@ -87,8 +93,20 @@ static inline void count_store(const unsigned char* p, size_t n) {
 }
 template <class T>
 static inline T lds(uint32_t addr) {
-  if ((size_t)addr + sizeof(T) > g_stage_bytes) err("lds outside stage", addr, (long long)g_stage_bytes);
   T v;
+  if (addr >= kTabBase) {
+    const size_t off = addr - kTabBase;
+    if (off + sizeof(T) > g_tab_bytes || (off & 3)) {
+      err("lds outside the row-base table", (long long)off, (long long)g_tab_bytes);
+      return (T)0;
+    }
+    std::memcpy(&v, g_tab + off, sizeof(T));
+    return v;
+  }
+  if ((size_t)addr + sizeof(T) > g_stage_bytes || (addr & (sizeof(T) - 1))) {
+    err("lds outside stage or misaligned", addr, (long long)g_stage_bytes);
+    return (T)0;
+  }
   std::memcpy(&v, g_stage + addr, sizeof(T));
   return v;
 }
@@ -113,7 +131,8 @@ extern "C" const char* emu_message() { return g_msg; }
 
 // Runs every tile of every depth of one array through the tile code.
 // Returns the number of violations (0 = clean); stats[0] = tiles, stats[1] =
-// bytes copied by bulk copies, stats[2] = max tile bytes.  nthr = consumer warps.
+// bytes copied by bulk copies, stats[2] = max tile bytes, stats[3] = tiles
+// that took the chunk path.  nthr = consumer warps.
 extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned char* counts,
                         int Nx, int Ny, int Nz, const int* Ks, const int* Kt, int es, int mode,
                         int target, int nthr, unsigned long long* stats) {
@@ -131,7 +150,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
   g_out_bytes = total;
   g_counts = counts;
   const unsigned char* safe_end = in + (total & ~(size_t)15);
-  unsigned long long tiles = 0, copied = 0, maxb = 0;
+  unsigned long long tiles = 0, copied = 0, maxb = 0, nfast = 0;
   for (int z = 0; z < Nz && g_errors == 0; ++z) {
     DepthTiling d = tile_depth(Ny, Ks[z], Kt[z], es, target);
     if ((unsigned long long)d.max_tile_bytes > maxb) maxb = d.max_tile_bytes;
@@ -170,15 +189,25 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           const int np = kNp[tiles % 4];
           for (int pw = 0; pw < np; ++pw)
             for (int lane = 0; lane < 32; ++lane)
-              issue_tile_loads(td, in_depth, safe_end, stage.data(), 0, lane, pw, np);
+              g_expect += tile_copies(td, in_depth, safe_end, stage.data(), 0, lane, pw, np, true);
+          for (int pw = 0; pw < np; ++pw)
+            for (int lane = 0; lane < 32; ++lane)
+              tile_copies(td, in_depth, safe_end, stage.data(), 0, lane, pw, np, false);
           if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
-          if (g_arrive != (unsigned long long)np) err("producer arrivals != producer warps", g_arrive, np);
           const int nwarps = nthr;  // here: number of consumer warps
           TileCtx ctx;
-          make_ctx(ctx, td, stage.data(), in_depth, out_depth);
+          // table entries past nrows stay poisoned: reading them is an error
+          std::vector<int> tab(kMaxTileRows + 1, 0x7f7f7f7f);
+          g_tab = (unsigned char*)tab.data();
+          g_tab_bytes = (size_t)(td.nrows + 1) * sizeof(int);
+          make_ctx(ctx, td, stage.data(), in_depth, out_depth, tab.data());
+          nfast += ctx.fast ? 1 : 0;
           for (int w = 0; w < nwarps; ++w)
             for (int lane = 0; lane < 32; ++lane)
-              gather_tile_ctx(ctx, w, nwarps, lane, (int)((tiles * (unsigned long long)ctx.items) % nwarps));
+              gather_tile_ctx(ctx, w, nwarps, lane,
+                              (int)((tiles * (unsigned long long)(ctx.fast ? ctx.nunits : ctx.items)) % nwarps));
+          g_tab = nullptr;  // the table dies with this tile
+          g_tab_bytes = 0;
           ++tiles;
           copied += g_copied;
           if (g_errors) break;
@@ -188,6 +217,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
     stats[0] = tiles;
     stats[1] = copied;
     stats[2] = maxb;
+    stats[3] = nfast;
   }
   return g_errors;
 }

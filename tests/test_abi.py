@@ -45,7 +45,7 @@ def _plan(lib, Nx, Ny, Ks, Kt, dt=0, mode=0):
 
 
 @pytest.mark.parametrize("args,code", [
-    ((4, 5, [15], [15]), -1),      # even Nx (Sec. 3 requires odd n_x)
+    ((4, 5, [15], [15]), -1),      # even Nx (Sec. 4 requires odd n_x)
     ((5, 6, [15], [15]), -1),      # even Ny
     ((5, 5, [14], [15]), -1),      # even Ks
     ((5, 5, [15], [0]), -1),       # Kt < 1
@@ -105,6 +105,29 @@ def test_buffer_validation_before_any_launch(lib):
                                         ctypes.cast(outs, P), None) == -9
     assert lib.lfbp_backproject_batched(0, None, None, None, None) == 0
     lib.lfbp_plan_destroy(h)
+
+
+def test_rl_step_validation_before_any_launch(lib):
+    """Eq. (2) entry points reject bad arguments before touching the GPU."""
+    rc, h = _plan(lib, 3, 3, [9], [9])
+    assert rc == 0
+    W = 12
+    img, vol = W * W * 4, W * W * 4
+    H, Hp, norm, f, g, out, work = (0x10000000 + i * 0x01000000 for i in range(7))
+    assert lib.lfbp_rl_step(h, H, None, norm, f, W, W, g, out, work, None) == -2
+    assert lib.lfbp_rl_step_fused(None, H, norm, f, W, W, g, out, work, None) == -2
+    assert lib.lfbp_rl_step_fused(h, H, norm, f, 0, W, g, out, work, None) == -1
+    assert lib.lfbp_rl_step_fused(h, H, norm, f, W, W, g, out, None, None) == -2
+    assert lib.lfbp_rl_step_fused(h, H, norm + 2, f, W, W, g, out, work, None) == -3
+    assert lib.lfbp_rl_step_fused(h, H, norm, f, W, W, g, out, out + 64, None) == -4
+    assert lib.lfbp_rl_step_fused(h, H, norm, f, W, W, g, g + 4, work, None) == -4
+    assert lib.lfbp_rl_step_fused(h, H, norm, f, W, W, g, norm, work, None) == -4
+    assert lib.lfbp_rl_normaliser(h, H, None, W, W, norm, norm + 8, None) == -4
+    rc, h16 = _plan(lib, 3, 3, [9], [9], 1)
+    assert lib.lfbp_rl_step_fused(h16, H, norm, f, W, W, g, out, work, None) == -5
+    assert lib.lfbp_backproject_volume_from_h(h16, H, f, W, W, g, None) == -5
+    lib.lfbp_plan_destroy(h)
+    lib.lfbp_plan_destroy(h16)
 
 
 def test_python_binding_refuses_without_library(monkeypatch, tmp_path):

@@ -52,7 +52,7 @@ SHAPES = [
     (9, 13, [27, 3, 1], [39, 13, 5]),
     (51, 51, [153], [153]),           # rows larger than one stage: column-split tiles
     (31, 31, [249], [249]),
-    (95, 55, [181], [181]),           # the non-square R29 cell shape (Sec. 4)
+    (95, 55, [181], [181]),           # the non-square R29 cell shape (Table 1, Sec. 5)
     (11, 11, [89], [89]),             # K not a multiple of N (Table 1 shapes)
 ]
 

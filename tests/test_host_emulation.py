@@ -51,7 +51,7 @@ def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=8):
     counts = np.zeros(nbytes, dtype=np.uint8)
     ks = np.asarray(Ks, dtype=np.int32)
     kt = np.asarray(Kt, dtype=np.int32)
-    stats = np.zeros(3, dtype=np.uint64)
+    stats = np.zeros(4, dtype=np.uint64)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     nerr = emu.emu_run(p(hin), p(out), p(counts), Nx, Ny, len(ks), p(ks), p(kt), es, mode,
                        target, nthr, p(stats))
@@ -95,6 +95,9 @@ def test_tiles_transpose(emu, shape, dtype):
     got, stats = _run(emu, H, Nx, Ny, Ks, Kt, 0, target)
     want = oracle.transpose(H, Nx, Ny, Ks, Kt)
     np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+    # the chunk path takes every tile whose rows and cells are at least a chunk long
+    if Ny >= 16 // H.itemsize and min(Kt) >= 16 // H.itemsize and target >= 32768:
+        assert stats[3] == stats[0]
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float16])

@@ -5,7 +5,7 @@ Each pin targets a plausible mistake: a hand evaluation of Eqs. (4)-(9)
 matrix built by pattern placement and transposed by numpy (wrong pairing of
 axes, wrong centring, non-square mix-ups), closed special cases (N = 1 is a
 180-degree kernel rotation, shift-invariant PSFs), invariants the paper
-states (reversibility, Sec. 3; summed slices rotated by 180 degrees, Sec. 3),
+states (reversibility, Sec. 4; summed slices rotated by 180 degrees, Sec. 4),
 the adjoint identity of the projectors and central finite differences.
 """
 import os
@@ -120,7 +120,7 @@ def test_paper_window_is_masked_transpose(Nx, Ny, Ks, Kt):
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float16, np.float64, np.uint8])
 def test_involution_and_adjoint(dtype):
-    """Reversibility (Sec. 3): mapping H' again returns H; the adjoint is the map."""
+    """Reversibility (Sec. 4): mapping H' again returns H; the adjoint is the map."""
     Nx, Ny, Ks, Kt = 5, 3, [15, 5, 9], [9, 3, 21]
     n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
     rng = np.random.default_rng(3)
@@ -135,7 +135,7 @@ def test_involution_and_adjoint(dtype):
 
 
 def test_multisets_and_summed_slices():
-    """Each depth's values are preserved; Sec. 3's summed-slice identity holds."""
+    """Each depth's values are preserved; Sec. 4's summed-slice identity holds."""
     spec = lfgen.config_specs("tiny")[0]
     H = lfgen.generate(spec).numpy()
     Hp = oracle.transpose(H, spec.Nx, spec.Ny, spec.Ks, spec.Kt)
