@@ -473,7 +473,53 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                      "plain_launches_per_step": sum(s.Nz for s in rspecs)}
     del rH, rO
     torch.cuda.empty_cache()
+    res["rl_step"] = _rl_extra(lf, timed, steps)
     return res
+
+
+def _fp32_fma_peak_tflops():
+    """Nominal fp32 CUDA-core peak: 152 SMs x 128 FMA lanes x 2 FLOP x max SM clock."""
+    return 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def _rl_extra(lf, timed, steps):
+    """One Richardson-Lucy update (Eq. 2) on the differentiation workload (N = 11,
+    21 depths, K up to 99, a 704 x 704 raw image): with H' (lfbp_rl_step) and with
+    H' never built (lfbp_rl_step_fused), and H' rebuilt + update as an in-loop PSF
+    update would need.  FLOP = 2 per product; products counted exactly (taps
+    inside the sensor), forward and backprojection."""
+    import torch
+    import lfgen
+    spec = lfgen.config_specs("autograd")[0]
+    W = 64 * spec.Nx
+    plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32)
+    H = lfgen.generate(spec, device="cuda")
+    Hp = lf.backproject_array(plan, H)
+    f = torch.from_numpy(lfgen.raw_image(64, spec.Nx, 19).astype("float32")).cuda()
+    g = torch.ones((spec.Nz, W, W), device="cuda")
+    out = torch.empty_like(g)
+    work = torch.empty((W, W), device="cuda")
+    norm = lf.rl_normaliser(plan, H, Hp, W, W)
+    norm_h = lf.rl_normaliser(plan, H, None, W, W)
+
+    def axis(K):
+        c = (K - 1) // 2
+        return sum(max(0, W - abs(s - c)) for s in range(K))
+    products = 2 * sum(axis(a) * axis(b) for a, b in zip(spec.Ks, spec.Kt))
+    n = max(3, steps // 4)
+    t_hp, _, _ = timed(lambda: lf.rl_step(plan, H, Hp, norm, f, g, out=out, work=work), n, 3)
+    t_fu, _, _ = timed(lambda: lf.rl_step(plan, H, None, norm_h, f, g, out=out, work=work), n, 3)
+    t_rb, _, _ = timed(lambda: (lf.backproject_array(plan, H, Hp),
+                                lf.rl_step(plan, H, Hp, norm, f, g, out=out, work=work)), n, 3)
+    peak = _fp32_fma_peak_tflops()
+    gf = lambda ms: round(2 * products / (ms * 1e-3) / 1e9, 1)
+    return {"workload": "autograd: N=11, 21 depths, K_z 33..99, 704 x 704 image, fp32",
+            "products_per_step": products,
+            "with_hprime_ms": round(t_hp, 4), "with_hprime_GFLOPs": gf(t_hp),
+            "fused_ms": round(t_fu, 4), "fused_GFLOPs": gf(t_fu),
+            "rebuild_hprime_plus_step_ms": round(t_rb, 4),
+            "fp32_peak_TFLOPs": round(peak, 1), "peak_kind": "nominal 152 SM x 128 FMA x 2.07 GHz",
+            "frac_fused": round(gf(t_fu) / (peak * 1e3), 4)}
 
 
 def main(argv=None):
