@@ -87,14 +87,6 @@ __host__ __device__ inline int row_pitch(int Ny, int P, int es) {
 }
 
 // ------------------------------------------------------------ host planning --
-// Element order of a lane's chunk in its loads: fp32 lanes whose lane bit 1
-// is set load the two halves swapped, which spreads the diagonal's addresses
-// over more banks (the diagonal stride P-1 is a multiple of 4 for the odd K
-// of the map, so chunks of consecutive lanes otherwise meet in few banks).
-__host__ __device__ inline int chunk_swap(int es, int lane) {
-  return (es == 4 && ((lane >> 1) & 1)) ? 2 : 0;
-}
-
 // Shared-memory bank wavefronts of the gather for one slot pitch P, averaged
 // over pseudo-random segment phases and positions (they depend on buffer
 // addresses unknown at planning time).  Mirrors the consumer's lane mapping:
@@ -117,7 +109,7 @@ inline double pitch_cost(int Ny, int Ks, int Kt, int ncols, int es, int P) {
       long long words[32];
       int n = 0;
       for (int l = 0; l < 32; ++l) {
-        const int vl = e0 + l * epl + (sub ^ chunk_swap(es, l));
+        const int vl = e0 + l * epl + sub;
         if (vl >= ncols) continue;
         const int b = (b0 + vl) % Ny;
         const long long idx = (long long)R + (long long)b * P + ncols - 1 - vl;
@@ -465,7 +457,7 @@ struct alignas(16) TileCtx {
   uint32_t stage_s;         // shared-memory address of the stage
   int tile_bytes;           // bytes of the tile's stage
   unsigned char* out_run0;  // byte address of run q = 0 at (u0, v0)
-  long long run_stride;     // bytes between runs q and q+1
+  uint32_t run_stride;      // bytes between runs q and q+1 (Ks*Kt*es < 2^32)
   unsigned char* out_lo;    // the depth's output bytes [out_lo, out_hi)
   unsigned char* out_hi;
   int Nx, Ny, Ks, Kt, ncols, L, P, RP;
@@ -487,6 +479,8 @@ struct alignas(16) TileCtx {
   uint32_t tab_s;  // shared-memory address of the row-base table: nrows + 1 ints
   int nrows;
   int rb0;         // row base of row 0 (elements): R_0 + ncols - 1
+  uint32_t A0;     // stage_s + rb0 * es
+  uint32_t PES;    // P * es
   int cbb;         // cb plus a multiple of Ny that is >= 128/es
   int ngm;         // 128-byte lines per run (any alignment), at least 2
   int nunits;      // warp steps of the tile: ceil(Ny * ngm / 4)
@@ -548,6 +542,8 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
     case 1:
       c.fncols = make_fastdiv(td.ncols);
       c.rb0 = row_base(td, in_depth, 0);
+      c.A0 = smem_addr(stage) + (uint32_t)c.rb0 * ES;
+      c.PES = (uint32_t)td.P * ES;
       c.D = (uint32_t)(td.P - 1) * ES;
       c.W = (uint32_t)td.Ny * td.P * ES;
       break;
@@ -579,7 +575,7 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       const unsigned long long run0 =
           ((unsigned long long)td.p * td.Ny * td.Ks + td.u0) * td.Kt + td.v0;  // elements
       c.out_run0 = out_depth + run0 * ES;
-      c.run_stride = (long long)(KK * ES);
+      c.run_stride = (uint32_t)(KK * ES);
       c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (GE - 1));
       c.kks = (int)(KK & (GE - 1));
       c.out_lo = out_depth;
@@ -738,6 +734,58 @@ __device__ __forceinline__ int tab_load(const TileCtx& c, int j) {
 // chunk because Ny and ncols are at least its element count.  Chunks cut by
 // a run's ends store element by element.  `rot` rotates the step-to-warp
 // assignment from tile to tile so that the warps share the remainder steps.
+// Stage addresses of one chunk of the chunk path: chunk element 0 is run
+// element e of run q.  A, kwA: address of element 0 and the first element that
+// wraps from segment Ny-1 to 0 (same row); B, kwB: the same for the elements
+// k >= kx of the next row (kx = EPL when the chunk stays in one row).
+struct ChunkAddr {
+  uint32_t A, B;
+  int kwA, kx, kwB;
+};
+
+template <int ES, bool ONEROW>
+__device__ __forceinline__ ChunkAddr chunk_addr(const TileCtx& c, int q, int e) {
+  constexpr int EPL = 16 / ES;
+  ChunkAddr s;
+  const int Ny = c.Ny;
+  s.kx = EPL;
+  s.kwB = EPL;
+  s.B = 0;
+  if (ONEROW) {
+    const int b = (int)fmod2((uint32_t)(q + c.cbb + e), c.fNy);
+    s.A = c.A0 + (uint32_t)b * c.PES - (uint32_t)e * ES;
+    s.kwA = Ny - b;
+  } else {
+    const int j = e > 0 ? (int)fdiv2((uint32_t)e, c.fncols) : 0;
+    const int vl = e - j * c.ncols;
+    const int rbj = tab_load(c, j);
+    const int rbn = tab_load(c, j + 1);
+    const int b = (int)fmod2((uint32_t)(q + c.cbb + vl), c.fNy);
+    s.A = c.stage_s + (uint32_t)(rbj + b * c.P - vl) * ES;
+    s.kwA = Ny - b;
+    s.kx = c.ncols - vl;
+    int bq0 = q + c.cb;
+    if (bq0 >= Ny) bq0 -= Ny;
+    s.B = c.stage_s + (uint32_t)(rbn + bq0 * c.P) * ES - (uint32_t)s.kx * c.D;
+    s.kwB = s.kx + Ny - bq0;
+  }
+  return s;
+}
+
+// stage address of chunk element k
+template <bool ONEROW>
+__device__ __forceinline__ uint32_t chunk_elem(const TileCtx& c, const ChunkAddr& s, int k) {
+  if (ONEROW) {
+    uint32_t a = s.A + (uint32_t)k * c.D;
+    if (k >= s.kwA) a -= c.W;
+    return a;
+  }
+  const bool nxt = k >= s.kx;
+  uint32_t a = (nxt ? s.B : s.A) + (uint32_t)k * c.D;
+  if (k >= (nxt ? s.kwB : s.kwA)) a -= c.W;
+  return a;
+}
+
 template <int ES, bool ONEROW>
 __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarps, int lane,
                                               int rot) {
@@ -746,11 +794,12 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
   constexpr int GE = 8 * EPL;   // elements per 128-byte line
   const int r = lane >> 3;
   const int lane_el = (lane & 7) * EPL;
-  const int sw = chunk_swap(ES, lane);  // load order: element k ^ sw
-  const int Ny = c.Ny, L = c.L, ncols = c.ncols, P = c.P;
-  const uint32_t D = c.D, W = c.W;
+  const int Ny = c.Ny, L = c.L;
   int first = (w - rot) % nwarps;
   if (first < 0) first += nwarps;
+  // Chunks cut by a run's end: one-row tiles store them element by element in
+  // the step that meets them; multi-row tiles leave them to an edge pass after
+  // the loop (measured: each is the faster choice for its kind of tile).
   for (int u = first; u < c.nunits; u += nwarps) {
     const int f = u * 4 + r;
     const int q = (int)fdiv2((uint32_t)f, c.fngm);
@@ -758,52 +807,49 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
     const int g = f - q * c.ngm;
     const int m = (c.om0 + q * c.kks) & (GE - 1);  // run q's first element within its line
     const int e = g * GE + lane_el - m;            // run element of chunk element 0
-    if (e >= L || e <= -EPL) continue;
-    unsigned char* dst = c.out_run0 + (long long)q * c.run_stride + (long long)e * ES;
-    int vl = e, rbj = c.rb0, kx = EPL, kw2 = 0;
-    uint32_t B = 0;
-    if (!ONEROW) {
-      const int j = e > 0 ? (int)fdiv2((uint32_t)e, c.fncols) : 0;
-      vl = e - j * ncols;
-      rbj = tab_load(c, j);
-      const int rbn = tab_load(c, j + 1);
-      kx = ncols - vl;
-      int bq0 = q + c.cb;
-      if (bq0 >= Ny) bq0 -= Ny;
-      B = c.stage_s + (uint32_t)(rbn + bq0 * P) * ES - (uint32_t)kx * D;
-      kw2 = kx + Ny - bq0;
-    }
-    const int b = (int)fmod2((uint32_t)(q + c.cbb + vl), c.fNy);
-    const int kw = Ny - b;
-    const uint32_t A = c.stage_s + (uint32_t)(rbj + b * P - vl) * ES;
-    auto addr_of = [&](int kk) -> uint32_t {
-      if (ONEROW) return A + (uint32_t)kk * D - (kk >= kw ? W : 0u);
-      const bool nxt = kk >= kx;
-      const uint32_t base = nxt ? B : A;
-      const int wk = nxt ? kw2 : kw;
-      return base + (uint32_t)kk * D - (kk >= wk ? W : 0u);
-    };
-    if (e >= 0 && e + EPL <= L) {
+    const bool whole = e >= 0 && e + EPL <= L;
+    if (ONEROW ? (e >= L || e <= -EPL) : !whole) continue;
+    unsigned char* dst =
+        c.out_run0 + (unsigned long long)(uint32_t)q * c.run_stride + (long long)e * ES;
+    const ChunkAddr s = chunk_addr<ES, ONEROW>(c, q, e);
+    if (whole) {
       T v[EPL];
       static_for<0, EPL>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        v[k] = smem_load_at<T>(c, addr_of(k ^ sw));
+        v[k] = smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k));
       });
-      if (ES == 4) {  // back into element order
-        T o[EPL];
-#pragma unroll
-        for (int i = 0; i < EPL; ++i) o[i] = sw ? v[i ^ 2] : v[i];
-        store_out16(c, dst, pack16(o));
-      } else {
-        store_out16(c, dst, pack16(v));
-      }
+      store_out16(c, dst, pack16(v));
     } else {
 #pragma unroll
       for (int k = 0; k < EPL; ++k) {
-        const int kk = k ^ sw;
-        if (e + kk < 0 || e + kk >= L) continue;
-        store_out(c, reinterpret_cast<T*>(dst) + kk, smem_load_at<T>(c, addr_of(kk)));
+        if (e + k < 0 || e + k >= L) continue;
+        store_out(c, reinterpret_cast<T*>(dst) + k,
+                  smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
       }
+    }
+  }
+  if (ONEROW) return;
+  // edge pass: the first and the last chunk of every run where a run end cuts
+  // them, element by element; edge chunk i goes to the warp whose rotated
+  // index is i mod nwarps, so each warp takes at most a few of them
+  for (int i = first + nwarps * lane; i < 2 * Ny; i += 32 * nwarps) {
+    const int q = i >> 1;
+    const int m = (c.om0 + q * c.kks) & (GE - 1);
+    const int e0 = -(m & (EPL - 1));  // start of the chunk holding run element 0
+    int e = e0;
+    if (i & 1) {
+      e = e0 + (((L - 1 - e0) / EPL) * EPL);  // chunk holding the run's last element
+      if (e + EPL <= L || e == e0) continue;   // whole, or the same chunk as the first
+    } else if (e0 == 0 && EPL <= L) {
+      continue;  // the first chunk is whole
+    }
+    unsigned char* dst =
+        c.out_run0 + (unsigned long long)(uint32_t)q * c.run_stride + (long long)e * ES;
+    const ChunkAddr s = chunk_addr<ES, ONEROW>(c, q, e);
+#pragma unroll
+    for (int k = 0; k < EPL; ++k) {
+      if (e + k < 0 || e + k >= L) continue;
+      store_out(c, reinterpret_cast<T*>(dst) + k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
     }
   }
 }
