@@ -44,10 +44,14 @@ def _peaks():
 
 
 def _kernel_source_sha():
+    """Hash of the gather kernels' source: lfbp_device.cuh and the device part
+    of lfbp.cu (everything before its host section)."""
     h = hashlib.sha256()
-    for f in ("lfbp.cu", "lfbp_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2003_09133_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_2003_09133_gb300", "csrc")
+    with open(os.path.join(csrc, "lfbp_device.cuh"), "rb") as fh:
+        h.update(fh.read())
+    with open(os.path.join(csrc, "lfbp.cu"), "rb") as fh:
+        h.update(fh.read().split(b"// ====================================================================== host")[0])
     return h.hexdigest()[:16]
 
 
