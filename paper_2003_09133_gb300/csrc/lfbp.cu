@@ -1061,6 +1061,35 @@ int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_st
   return run_plain(p, dHp_grad, dH_grad, mode, (cudaStream_t)cuda_stream);
 }
 
+namespace {
+
+// A projection over all depths of the plan as output-cell sums (see
+// lfbp_project.h): `mapped` reads the weights through the map of A.  Depths
+// whose cut-out exceeds the phase kernel's sizes take the direct kernel,
+// which reads the unmapped array `A_direct` with source-cell patterns.
+int project(lfbp_plan p, const float* A, int mapped, const float* A_direct, int direct_out_cell,
+            const float* in, long long in_zs, float* out, long long out_zs, const float* g,
+            const float* norm, int Wx, int Wy, int sum_depths, int epi, cudaStream_t st) {
+  std::vector<long long> off(p->Nz);
+  for (int z = 0; z < p->Nz; ++z) off[z] = (long long)p->off[z];
+  const int rc = launch_phase_projection(A, mapped, p->Nx, p->Ny, p->Nz, off.data(), p->Ks.data(),
+                                         p->Kt.data(), in, in_zs, out, out_zs, g, norm, Wx, Wy,
+                                         sum_depths, epi, st);
+  if (rc == 0) return LFBP_OK;
+  if (rc != -1) return fail(LFBP_ERR_CUDA, "k_phase_conv launch failed");
+  for (int z = 0; z < p->Nz; ++z) {
+    const int e = sum_depths ? (z ? kEpiAccumulate : epi) : epi;
+    const long long o = sum_depths ? 0 : (long long)z * out_zs;
+    if (launch_projector(direct_out_cell, e, A_direct + p->off[z], p->Nx, p->Ny, p->Ks[z],
+                         p->Kt[z], in + (long long)z * in_zs, Wx, Wy, out + o, g ? g + o : nullptr,
+                         norm ? norm + o : nullptr, st))
+      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
+  }
+  return LFBP_OK;
+}
+
+}  // namespace
+
 int lfbp_backproject_volume(lfbp_plan p, const void* dHp, const float* df, int Wx, int Wy,
                             float* dg, void* cuda_stream) {
   int rc = check_projector(p, dHp, df, dg, Wx, Wy, (size_t)(p ? p->Nz : 0) * Wx * Wy * 4);
@@ -1068,12 +1097,9 @@ int lfbp_backproject_volume(lfbp_plan p, const void* dHp, const float* df, int W
   if (overlaps(df, (size_t)Wx * Wy * 4, dg, (size_t)p->Nz * Wx * Wy * 4))
     return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   const float* hp = (const float*)dHp;
-  for (int z = 0; z < p->Nz; ++z) {
-    if (launch_shift_variant_sum(hp + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z], df, Wx, Wy,
-                                 dg + (size_t)z * Wx * Wy, 0, (cudaStream_t)cuda_stream))
-      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
-  }
-  return LFBP_OK;
+  // weights H[p][q] = the map of H' (its own inverse)
+  return project(p, hp, 1, hp, 0, df, 0, dg, (long long)Wx * Wy, nullptr, nullptr, Wx, Wy, 0,
+                 kEpiStore, (cudaStream_t)cuda_stream);
 }
 
 int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, int Wy, float* df,
@@ -1086,14 +1112,11 @@ int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, i
   if (p->Nz == 0) {
     cudaError_t e = cudaMemsetAsync(df, 0, (size_t)Wx * Wy * 4, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    return LFBP_OK;
   }
-  for (int z = 0; z < p->Nz; ++z) {
-    if (launch_shift_variant_sum(h + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z],
-                                 dg + (size_t)z * Wx * Wy, Wx, Wy, df, z > 0,
-                                 (cudaStream_t)cuda_stream))
-      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
-  }
-  return LFBP_OK;
+  // weights H'[p][q] = the map of H; depths summed in order
+  return project(p, h, 1, h, 0, dg, (long long)Wx * Wy, df, 0, nullptr, nullptr, Wx, Wy, 1,
+                 kEpiStore, (cudaStream_t)cuda_stream);
 }
 
 int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
@@ -1118,12 +1141,8 @@ int lfbp_backproject_volume_from_h(lfbp_plan p, const void* dH, const float* df,
   if (overlaps(df, (size_t)Wx * Wy * 4, dg, (size_t)p->Nz * Wx * Wy * 4))
     return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   const float* h = (const float*)dH;
-  for (int z = 0; z < p->Nz; ++z) {
-    if (launch_projector(1, kEpiStore, h + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z], df, Wx, Wy,
-                         dg + (size_t)z * Wx * Wy, nullptr, nullptr, (cudaStream_t)cuda_stream))
-      return fail(LFBP_ERR_CUDA, "k_shift_variant_sum launch failed");
-  }
-  return LFBP_OK;
+  return project(p, h, 0, h, 1, df, 0, dg, (long long)Wx * Wy, nullptr, nullptr, Wx, Wy, 0,
+                 kEpiStore, (cudaStream_t)cuda_stream);
 }
 
 namespace {
@@ -1155,26 +1174,22 @@ int rl_step_impl(lfbp_plan p, const void* dH, const void* dHp, const float* dnor
     return fail(LFBP_ERR_ALIAS, "dg_next overlaps dg without being dg");
   const float* h = (const float*)dH;
   const float* hp = (const float*)dHp;
-  // H g, summed over depths in order
+  const long long W2 = (long long)Wx * Wy;
+  // H g, summed over depths in order (weights: the map of H, or H' itself)
   if (p->Nz == 0) {
     cudaError_t e = cudaMemsetAsync(dwork, 0, img, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  } else {
+    rc = hp ? project(p, hp, 0, h, 0, dg, W2, dwork, 0, nullptr, nullptr, Wx, Wy, 1, kEpiStore, st)
+            : project(p, h, 1, h, 0, dg, W2, dwork, 0, nullptr, nullptr, Wx, Wy, 1, kEpiStore, st);
+    if (rc) return rc;
   }
-  for (int z = 0; z < p->Nz; ++z)
-    if (launch_projector(0, z ? kEpiAccumulate : kEpiStore, h + p->off[z], p->Nx, p->Ny, p->Ks[z],
-                         p->Kt[z], dg + (size_t)z * Wx * Wy, Wx, Wy, dwork, nullptr, nullptr, st))
-      return fail(LFBP_ERR_CUDA, "forward projection launch failed");
   // f / (H g)
-  if (launch_rl_quotient(df, dwork, (long long)Wx * Wy, st))
+  if (launch_rl_quotient(df, dwork, W2, st))
     return fail(LFBP_ERR_CUDA, "k_rl_quotient launch failed");
-  // g / (H'1) * H' (f / (H g)), depth by depth
-  for (int z = 0; z < p->Nz; ++z) {
-    const size_t o = (size_t)z * Wx * Wy;
-    if (launch_projector(hp ? 0 : 1, kEpiRL, (hp ? hp : h) + p->off[z], p->Nx, p->Ny, p->Ks[z],
-                         p->Kt[z], dwork, Wx, Wy, dg_next + o, dg + o, dnorm + o, st))
-      return fail(LFBP_ERR_CUDA, "backprojection launch failed");
-  }
-  return LFBP_OK;
+  // g / (H'1) * H' (f / (H g)), depth by depth (weights: H, or the map of H')
+  return hp ? project(p, hp, 1, hp, 0, dwork, 0, dg_next, W2, dg, dnorm, Wx, Wy, 0, kEpiRL, st)
+            : project(p, h, 0, h, 1, dwork, 0, dg_next, W2, dg, dnorm, Wx, Wy, 0, kEpiRL, st);
 }
 
 }  // namespace
@@ -1205,11 +1220,8 @@ int lfbp_rl_normaliser(lfbp_plan p, const void* dH, const void* dHp, int Wx, int
   if (launch_fill(dwork, (long long)Wx * Wy, 1.0f, st))
     return fail(LFBP_ERR_CUDA, "k_fill launch failed");
   const float* a = (const float*)A;
-  for (int z = 0; z < p->Nz; ++z)
-    if (launch_projector(dHp ? 0 : 1, kEpiStore, a + p->off[z], p->Nx, p->Ny, p->Ks[z], p->Kt[z],
-                         dwork, Wx, Wy, dnorm + (size_t)z * Wx * Wy, nullptr, nullptr, st))
-      return fail(LFBP_ERR_CUDA, "backprojection launch failed");
-  return LFBP_OK;
+  return project(p, a, dHp ? 1 : 0, a, dHp ? 0 : 1, dwork, 0, dnorm, (long long)Wx * Wy, nullptr,
+                 nullptr, Wx, Wy, 0, kEpiStore, st);
 }
 
 int lfbp_sync_status(void* cuda_stream) {

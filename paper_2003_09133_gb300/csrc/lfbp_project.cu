@@ -25,7 +25,9 @@
 // results are deterministic (no atomics).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "lfbp_project.h"
 
@@ -105,6 +107,159 @@ __global__ void __launch_bounds__(kSvTI* kSvTJ)
       out[o] = n != 0.f ? (g[o] / n) * acc : 0.f;
     }
   }
+}
+
+// ------------------------------------------------------------- phase conv --
+// The output-cell sum  out(P) = sum_{u,v} in(P + (u,v) - c) * w_{P mod N}[u][v]
+// serves every projection:
+//   backprojection g = H' f:  w_{p,q} = H[p][q]                (read directly)
+//   forward f = H g (Eq. 1):  w_{p,q} = H'[p][q]
+//                            = H[(p+u-c_s) mod Nx][(q+v-c_t) mod Ny][Ks-1-u][Kt-1-v]
+// (the map of Sec. 4 applied while the weights are staged; with H' at hand
+// the roles swap, the map being its own inverse).  So neither projection
+// needs the other array, and a block's weights are one pattern.
+//
+// Block: one output phase (px, py) and a kPcTI x kPcTJ tile of its outputs
+// X = px + Nx*i, Y = py + Ny*j.  The taps split by input phase: u = Nx*sigma + rho,
+// v = Ny*upsilon + tau.  For each (rho, tau) the inputs form a dense subgrid
+//   I(a, b) = in(Nx*(i0+a) + px + rho - c_s, Ny*(j0+b) + py + tau - c_t)
+// and out(i, j) += sum_{sigma,upsilon} I(i-i0+sigma, j-j0+upsilon) * w[Nx sigma+rho][Ny upsilon+tau]:
+// a dense correlation with an at most S x S kernel.  The subgrid tile and the
+// sub-kernel (zero-padded to S x S) are staged in shared memory; each thread
+// accumulates kPcRI x 2 outputs in registers, reusing each loaded input row
+// for every kernel row it meets.  Terms are summed in a fixed order
+// (deterministic); padded taps add exact zeros.
+constexpr int kPcThreads = 256;
+constexpr int kPcRI = 4;                 // output rows per thread
+constexpr int kPcTI = 8 * kPcRI;         // 32 output rows per block (8 warps)
+constexpr int kPcTJ = 64;                // output columns per block (2 per lane)
+constexpr int kPcMaxDepths = 64;
+
+struct PcDepth {
+  long long off;  // element offset of the depth in A
+  int Ks, Kt;
+  int z;          // depth index: in + z*in_zstride, out/g/norm + z*out_zstride
+  int pad;
+};
+
+struct PcArgs {
+  const float* A;
+  const float* in;
+  long long in_zstride;
+  float* out;
+  long long out_zstride;
+  const float* g;
+  const float* norm;
+  int Nx, Ny, Wx, Wy;
+  int nTI, nTJ;
+  int ndepth;
+  int mapped;      // 1: weights through the map (see above)
+  int sum_depths;  // 1: every block sums all depths of d[] into one output
+  int epi;
+  PcDepth d[kPcMaxDepths];
+};
+
+template <int S>
+__global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant__ PcArgs a) {
+  constexpr int S4 = (S + 3) & ~3;         // weight row pitch
+  constexpr int IR = kPcTI + S - 1;        // subgrid rows
+  constexpr int IC = kPcTJ + S;            // subgrid columns (lane cols 2l .. 2l+S)
+  constexpr int ICP = (IC + 1) & ~1;       // even pitch: 8-byte aligned pairs
+  __shared__ __align__(16) float w_s[S * S4];
+  __shared__ __align__(16) float I_s[IR * ICP];
+  const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
+  int t = blockIdx.x;
+  const int tj = t % a.nTJ;
+  t /= a.nTJ;
+  const int ti = t % a.nTI;
+  t /= a.nTI;
+  const int py = t % Ny, px = t / Ny;
+  const int i0 = ti * kPcTI, j0 = tj * kPcTJ;
+  const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
+  const int a0 = wi * kPcRI, b0 = 2 * lane;
+  float acc[kPcRI][2];
+#pragma unroll
+  for (int i = 0; i < kPcRI; ++i) acc[i][0] = acc[i][1] = 0.f;
+  const int d_lo = a.sum_depths ? 0 : (int)blockIdx.y;
+  const int d_hi = a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
+  for (int di = d_lo; di < d_hi; ++di) {
+    const PcDepth dd = a.d[di];
+    const int Ks = dd.Ks, Kt = dd.Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
+    const float* Az = a.A + dd.off;
+    const float* inz = a.in + (long long)dd.z * a.in_zstride;
+    for (int rho = 0; rho < Nx && rho < Ks; ++rho) {
+      const int Ssig = (Ks - rho + Nx - 1) / Nx;  // sigma with Nx*sigma + rho < Ks
+      const int xoff = px + rho - cs;
+      const int ar = pmod(xoff, Nx);              // mapped weights: source cell row
+      for (int tau = 0; tau < Ny && tau < Kt; ++tau) {
+        const int Sups = (Kt - tau + Ny - 1) / Ny;
+        const int yoff = py + tau - ct;
+        __syncthreads();  // the previous sub-problem is done with shared memory
+        for (int e = tid; e < S * S4; e += kPcThreads) {
+          const int sg = e / S4, up = e - sg * S4;
+          float v = 0.f;
+          if (sg < Ssig && up < Sups) {
+            const int u = Nx * sg + rho, vv = Ny * up + tau;
+            if (a.mapped)
+              v = __ldg(Az + (((size_t)ar * Ny + pmod(yoff, Ny)) * Ks + (Ks - 1 - u)) * Kt +
+                        (Kt - 1 - vv));
+            else
+              v = __ldg(Az + (((size_t)px * Ny + py) * Ks + u) * Kt + vv);
+          }
+          w_s[e] = v;
+        }
+        for (int r = wi; r < IR; r += kPcThreads / 32) {
+          const int x = Nx * (i0 + r) + xoff;
+          const bool xin = x >= 0 && x < Wx;
+          const float* row = inz + (size_t)(xin ? x : 0) * Wy;
+          for (int col = lane; col < ICP; col += 32) {
+            const int y = Ny * (j0 + col) + yoff;
+            I_s[r * ICP + col] = (xin && col < IC && y >= 0 && y < Wy) ? __ldg(row + y) : 0.f;
+          }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kPcRI + S - 1; ++r) {
+          float xv[S + 2];
+          const float* src = I_s + (a0 + r) * ICP + b0;
+#pragma unroll
+          for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
+            const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
+            xv[2 * c2] = p.x;
+            xv[2 * c2 + 1] = p.y;
+          }
+#pragma unroll
+          for (int sg = 0; sg < S; ++sg) {
+            const int ai = r - sg;
+            if (ai < 0 || ai >= kPcRI) continue;
+#pragma unroll
+            for (int up = 0; up < S; ++up) {
+              const float wv = w_s[sg * S4 + up];
+              acc[ai][0] = fmaf(xv[up], wv, acc[ai][0]);
+              acc[ai][1] = fmaf(xv[up + 1], wv, acc[ai][1]);
+            }
+          }
+        }
+      }
+    }
+  }
+  const long long zo = a.sum_depths ? 0 : (long long)a.d[blockIdx.y].z * a.out_zstride;
+#pragma unroll
+  for (int i = 0; i < kPcRI; ++i)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
+      if (X >= Wx || Y >= Wy) continue;
+      const long long o = zo + (long long)X * Wy + Y;
+      if (a.epi == kEpiStore) {
+        a.out[o] = acc[i][c];
+      } else if (a.epi == kEpiAccumulate) {
+        a.out[o] += acc[i][c];
+      } else {
+        const float n = a.norm[o];
+        a.out[o] = n != 0.f ? (a.g[o] / n) * acc[i][c] : 0.f;
+      }
+    }
 }
 
 // Quotient of Eq. 2 in place: r = f / fe where fe != 0, else 0.
@@ -211,6 +366,88 @@ int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, con
                              int Wx, int Wy, float* out, int accumulate, cudaStream_t st) {
   return launch_projector(0, accumulate ? kEpiAccumulate : kEpiStore, A, Nx, Ny, Ks, Kt, in, Wx,
                           Wy, out, nullptr, nullptr, st);
+}
+
+namespace {
+constexpr int kPcSizes[] = {3, 5, 7, 9, 11, 13, 15};  // kernel instances (sub-kernel extent S)
+
+template <int S>
+int launch_pc(const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
+  k_phase_conv<S><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
+int launch_pc_size(int S, const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
+  switch (S) {
+    case 3: return launch_pc<3>(a, nblocks, ny, st);
+    case 5: return launch_pc<5>(a, nblocks, ny, st);
+    case 7: return launch_pc<7>(a, nblocks, ny, st);
+    case 9: return launch_pc<9>(a, nblocks, ny, st);
+    case 11: return launch_pc<11>(a, nblocks, ny, st);
+    case 13: return launch_pc<13>(a, nblocks, ny, st);
+    default: return launch_pc<15>(a, nblocks, ny, st);
+  }
+}
+}  // namespace
+
+int phase_conv_size(int Nx, int Ny, int Ks, int Kt) {
+  const int s = std::max((Ks + Nx - 1) / Nx, (Kt + Ny - 1) / Ny);
+  for (int S : kPcSizes)
+    if (s <= S) return S;
+  return 0;
+}
+
+int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
+                            const long long* off, const int* Ks, const int* Kt, const float* in,
+                            long long in_zstride, float* out, long long out_zstride,
+                            const float* g, const float* norm, int Wx, int Wy, int sum_depths,
+                            int epi, cudaStream_t st) {
+  for (int z = 0; z < Nz; ++z)
+    if (!phase_conv_size(Nx, Ny, Ks[z], Kt[z])) return -1;
+  const int nI = (Wx + Nx - 1) / Nx, nJ = (Wy + Ny - 1) / Ny;
+  PcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.A = A;
+  a.in = in;
+  a.in_zstride = in_zstride;
+  a.out = out;
+  a.out_zstride = out_zstride;
+  a.g = g;
+  a.norm = norm;
+  a.Nx = Nx;
+  a.Ny = Ny;
+  a.Wx = Wx;
+  a.Wy = Wy;
+  a.nTI = (nI + kPcTI - 1) / kPcTI;
+  a.nTJ = (nJ + kPcTJ - 1) / kPcTJ;
+  a.mapped = mapped;
+  a.sum_depths = sum_depths;
+  const long long nblocks = (long long)Nx * Ny * a.nTI * a.nTJ;
+  if (nblocks > 0x7fffffffLL) return -1;
+  bool first = true;
+  for (int S : kPcSizes) {  // one launch per instance size (and per 64 depths)
+    int n = 0;
+    for (int z = 0; z <= Nz; ++z) {
+      const bool take = z < Nz && phase_conv_size(Nx, Ny, Ks[z], Kt[z]) == S;
+      if (take) {
+        a.d[n].off = off[z];
+        a.d[n].Ks = Ks[z];
+        a.d[n].Kt = Kt[z];
+        a.d[n].z = z;
+        ++n;
+      }
+      if (n == kPcMaxDepths || (z == Nz && n > 0)) {
+        a.ndepth = n;
+        // summed depths: the first launch stores (or applies epi), later ones add
+        a.epi = sum_depths ? (first ? epi : kEpiAccumulate) : epi;
+        const int rc = launch_pc_size(S, a, (int)nblocks, sum_depths ? 1 : n, st);
+        if (rc) return rc;
+        first = false;
+        n = 0;
+      }
+    }
+  }
+  return 0;
 }
 
 static unsigned elementwise_blocks(long long n) {

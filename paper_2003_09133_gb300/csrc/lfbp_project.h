@@ -23,6 +23,18 @@ int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, con
 // dA[p][q][u][v] = sum over pixels S of cell (p, q) of f[S] * dg[S + (u-c_s, v-c_t)]
 int launch_backproject_grad(const float* f, const float* dg, int Nx, int Ny, int Ks, int Kt,
                             int Wx, int Wy, float* dA, cudaStream_t st);
+// The output-cell sum out(P) = sum_{u,v} in(P + (u,v) - c) * w_{P mod N}[u][v]
+// over the plan's depths, w = A[p][q] (mapped = 0) or the map of A (mapped = 1:
+// w_{p,q}[u][v] = A[(p+u-c_s) mod Nx][(q+v-c_t) mod Ny][Ks-1-u][Kt-1-v]).
+// Depth z's pattern starts at A + off[z]; its input image at in + z*in_zstride;
+// per-depth outputs at out + z*out_zstride, or, with sum_depths, one output
+// summed over depths in order.  Returns -1 (nothing launched) when a depth's
+// cut-out exceeds 15 cells per axis; the caller then uses launch_projector.
+int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
+                            const long long* off, const int* Ks, const int* Kt, const float* in,
+                            long long in_zstride, float* out, long long out_zstride,
+                            const float* g, const float* norm, int Wx, int Wy, int sum_depths,
+                            int epi, cudaStream_t st);
 // fe_r[i] = f[i] / fe_r[i] where fe_r[i] != 0, else 0 (the quotient of Eq. 2)
 int launch_rl_quotient(const float* f, float* fe_r, long long n, cudaStream_t st);
 int launch_fill(float* x, long long n, float v, cudaStream_t st);
