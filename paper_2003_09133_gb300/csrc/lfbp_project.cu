@@ -119,19 +119,17 @@ __global__ void __launch_bounds__(kSvTI* kSvTJ)
 // the roles swap, the map being its own inverse).  So neither projection
 // needs the other array, and a block's weights are one pattern.
 //
-// Block: one output phase (px, py) and a kPcTI x kPcTJ tile of its outputs
+// Block: one output phase (px, py) and a (8*RI) x kPcTJ tile of its outputs
 // X = px + Nx*i, Y = py + Ny*j.  The taps split by input phase: u = Nx*sigma + rho,
 // v = Ny*upsilon + tau.  For each (rho, tau) the inputs form a dense subgrid
 //   I(a, b) = in(Nx*(i0+a) + px + rho - c_s, Ny*(j0+b) + py + tau - c_t)
 // and out(i, j) += sum_{sigma,upsilon} I(i-i0+sigma, j-j0+upsilon) * w[Nx sigma+rho][Ny upsilon+tau]:
 // a dense correlation with an at most S x S kernel.  The subgrid tile and the
 // sub-kernel (zero-padded to S x S) are staged in shared memory; each thread
-// accumulates kPcRI x 2 outputs in registers, reusing each loaded input row
+// accumulates RI x 2 outputs in registers, reusing each loaded input row
 // for every kernel row it meets.  Terms are summed in a fixed order
 // (deterministic); padded taps add exact zeros.
 constexpr int kPcThreads = 256;
-constexpr int kPcRI = 4;                 // output rows per thread
-constexpr int kPcTI = 8 * kPcRI;         // 32 output rows per block (8 warps)
 constexpr int kPcTJ = 64;                // output columns per block (2 per lane)
 constexpr int kPcMaxDepths = 64;
 
@@ -159,14 +157,39 @@ struct PcArgs {
   PcDepth d[kPcMaxDepths];
 };
 
-template <int S>
+// 4-byte asynchronous copy global -> shared; with valid = false nothing is
+// read and the destination is zero-filled (`src` must still be a valid address).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Sub-problem cursor: depth di, input phase (rho, tau).
+struct PcCursor {
+  int di, rho, tau;
+};
+
+// RI: output rows per thread; the block (8 warps) covers 8*RI rows x 64 columns.
+// The sub-problems (depth, rho, tau) run through a two-buffer pipeline: the
+// copies of the next one are in flight while the current one is computed.
+template <int S, int RI>
 __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant__ PcArgs a) {
-  constexpr int S4 = (S + 3) & ~3;         // weight row pitch
-  constexpr int IR = kPcTI + S - 1;        // subgrid rows
-  constexpr int IC = kPcTJ + S;            // subgrid columns (lane cols 2l .. 2l+S)
-  constexpr int ICP = (IC + 1) & ~1;       // even pitch: 8-byte aligned pairs
-  __shared__ __align__(16) float w_s[S * S4];
-  __shared__ __align__(16) float I_s[IR * ICP];
+  constexpr int TI = 8 * RI;
+  constexpr int S4 = (S + 3) & ~3;   // weight row pitch
+  constexpr int IR = TI + S - 1;     // subgrid rows
+  constexpr int IC = kPcTJ + S;      // subgrid columns (lane cols 2l .. 2l+S)
+  constexpr int ICP = (IC + 1) & ~1; // even pitch: 8-byte aligned pairs
+  __shared__ __align__(16) float w_s[2][S * S4];
+  __shared__ __align__(16) float I_s[2][IR * ICP];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   int t = blockIdx.x;
   const int tj = t % a.nTJ;
@@ -174,78 +197,101 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
   const int ti = t % a.nTI;
   t /= a.nTI;
   const int py = t % Ny, px = t / Ny;
-  const int i0 = ti * kPcTI, j0 = tj * kPcTJ;
+  const int i0 = ti * TI, j0 = tj * kPcTJ;
   const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
-  const int a0 = wi * kPcRI, b0 = 2 * lane;
-  float acc[kPcRI][2];
-#pragma unroll
-  for (int i = 0; i < kPcRI; ++i) acc[i][0] = acc[i][1] = 0.f;
+  const int a0 = wi * RI, b0 = 2 * lane;
   const int d_lo = a.sum_depths ? 0 : (int)blockIdx.y;
   const int d_hi = a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
-  for (int di = d_lo; di < d_hi; ++di) {
-    const PcDepth dd = a.d[di];
+
+  // issue the copies of sub-problem c into buffer buf (one commit group)
+  auto stage = [&](const PcCursor& c, int buf) {
+    const PcDepth dd = a.d[c.di];
     const int Ks = dd.Ks, Kt = dd.Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
     const float* Az = a.A + dd.off;
     const float* inz = a.in + (long long)dd.z * a.in_zstride;
-    for (int rho = 0; rho < Nx && rho < Ks; ++rho) {
-      const int Ssig = (Ks - rho + Nx - 1) / Nx;  // sigma with Nx*sigma + rho < Ks
-      const int xoff = px + rho - cs;
-      const int ar = pmod(xoff, Nx);              // mapped weights: source cell row
-      for (int tau = 0; tau < Ny && tau < Kt; ++tau) {
-        const int Sups = (Kt - tau + Ny - 1) / Ny;
-        const int yoff = py + tau - ct;
-        __syncthreads();  // the previous sub-problem is done with shared memory
-        for (int e = tid; e < S * S4; e += kPcThreads) {
-          const int sg = e / S4, up = e - sg * S4;
-          float v = 0.f;
-          if (sg < Ssig && up < Sups) {
-            const int u = Nx * sg + rho, vv = Ny * up + tau;
-            if (a.mapped)
-              v = __ldg(Az + (((size_t)ar * Ny + pmod(yoff, Ny)) * Ks + (Ks - 1 - u)) * Kt +
-                        (Kt - 1 - vv));
-            else
-              v = __ldg(Az + (((size_t)px * Ny + py) * Ks + u) * Kt + vv);
-          }
-          w_s[e] = v;
-        }
-        for (int r = wi; r < IR; r += kPcThreads / 32) {
-          const int x = Nx * (i0 + r) + xoff;
-          const bool xin = x >= 0 && x < Wx;
-          const float* row = inz + (size_t)(xin ? x : 0) * Wy;
-          for (int col = lane; col < ICP; col += 32) {
-            const int y = Ny * (j0 + col) + yoff;
-            I_s[r * ICP + col] = (xin && col < IC && y >= 0 && y < Wy) ? __ldg(row + y) : 0.f;
-          }
-        }
-        __syncthreads();
+    const int Ssig = (Ks - c.rho + Nx - 1) / Nx, Sups = (Kt - c.tau + Ny - 1) / Ny;
+    const int xoff = px + c.rho - cs, yoff = py + c.tau - ct;
+    const int ar = pmod(xoff, Nx), br = pmod(yoff, Ny);
+    for (int e = tid; e < S * S4; e += kPcThreads) {
+      const int sg = e / S4, up = e - sg * S4;
+      const bool ok = sg < Ssig && up < Sups;
+      const int u = Nx * sg + c.rho, v = Ny * up + c.tau;
+      const float* src =
+          !ok ? a.A
+              : a.mapped ? Az + (((size_t)ar * Ny + br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
+                         : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
+      cp_async4(&w_s[buf][e], src, ok);
+    }
+    for (int r = wi; r < IR; r += kPcThreads / 32) {
+      const int x = Nx * (i0 + r) + xoff;
+      const bool xin = x >= 0 && x < Wx;
+      const float* row = inz + (size_t)(xin ? x : 0) * Wy;
+      for (int col = lane; col < ICP; col += 32) {
+        const int y = Ny * (j0 + col) + yoff;
+        const bool ok = xin && col < IC && y >= 0 && y < Wy;
+        cp_async4(&I_s[buf][r * ICP + col], ok ? row + y : a.in, ok);
+      }
+    }
+    cp_async_commit();
+  };
+  auto advance = [&](PcCursor& c) -> bool {  // next sub-problem; false at the end
+    const PcDepth& dd = a.d[c.di];
+    if (++c.tau < Ny && c.tau < dd.Kt) return true;
+    c.tau = 0;
+    if (++c.rho < Nx && c.rho < dd.Ks) return true;
+    c.rho = 0;
+    return ++c.di < d_hi;
+  };
+
+  float acc[RI][2];
 #pragma unroll
-        for (int r = 0; r < kPcRI + S - 1; ++r) {
-          float xv[S + 2];
-          const float* src = I_s + (a0 + r) * ICP + b0;
+  for (int i = 0; i < RI; ++i) acc[i][0] = acc[i][1] = 0.f;
+  PcCursor cur{d_lo, 0, 0};
+  PcCursor nxt = cur;
+  bool more = advance(nxt);
+  stage(cur, 0);
+  for (int k = 0;; ++k) {
+    const int buf = k & 1;
+    if (more)
+      stage(nxt, buf ^ 1);
+    else
+      cp_async_commit();  // keep the group count uniform
+    cp_async_wait<1>();   // the current buffer has landed (this thread's copies)
+    __syncthreads();      // ... and everybody's
+    const float* Ib = I_s[buf];
+    const float* wb = w_s[buf];
 #pragma unroll
-          for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
-            const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
-            xv[2 * c2] = p.x;
-            xv[2 * c2 + 1] = p.y;
-          }
+    for (int r = 0; r < RI + S - 1; ++r) {
+      float xv[S + 2];
+      const float* src = Ib + (a0 + r) * ICP + b0;
 #pragma unroll
-          for (int sg = 0; sg < S; ++sg) {
-            const int ai = r - sg;
-            if (ai < 0 || ai >= kPcRI) continue;
+      for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
+        const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
+        xv[2 * c2] = p.x;
+        xv[2 * c2 + 1] = p.y;
+      }
 #pragma unroll
-            for (int up = 0; up < S; ++up) {
-              const float wv = w_s[sg * S4 + up];
-              acc[ai][0] = fmaf(xv[up], wv, acc[ai][0]);
-              acc[ai][1] = fmaf(xv[up + 1], wv, acc[ai][1]);
-            }
-          }
+      for (int sg = 0; sg < S; ++sg) {
+        const int ai = r - sg;
+        if (ai < 0 || ai >= RI) continue;
+#pragma unroll
+        for (int up = 0; up < S; ++up) {
+          const float wv = wb[sg * S4 + up];
+          acc[ai][0] = fmaf(xv[up], wv, acc[ai][0]);
+          acc[ai][1] = fmaf(xv[up + 1], wv, acc[ai][1]);
         }
       }
     }
+    __syncthreads();  // buffer buf is free for the copies issued next round
+    if (!more) break;
+    cur = nxt;
+    more = advance(nxt);
   }
+  cp_async_wait<0>();
+
   const long long zo = a.sum_depths ? 0 : (long long)a.d[blockIdx.y].z * a.out_zstride;
 #pragma unroll
-  for (int i = 0; i < kPcRI; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
@@ -373,7 +419,11 @@ constexpr int kPcSizes[] = {3, 5, 7, 9, 11, 13, 15};  // kernel instances (sub-k
 
 template <int S>
 int launch_pc(const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
-  k_phase_conv<S><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
+  // depth sums run one block per output tile: half-height tiles for more blocks
+  if (a.sum_depths)
+    k_phase_conv<S, 2><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
+  else
+    k_phase_conv<S, 4><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
@@ -418,7 +468,8 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   a.Ny = Ny;
   a.Wx = Wx;
   a.Wy = Wy;
-  a.nTI = (nI + kPcTI - 1) / kPcTI;
+  const int TI = sum_depths ? 16 : 32;  // 8 warps x 2 or 4 rows (launch_pc)
+  a.nTI = (nI + TI - 1) / TI;
   a.nTJ = (nJ + kPcTJ - 1) / kPcTJ;
   a.mapped = mapped;
   a.sum_depths = sum_depths;
