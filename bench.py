@@ -378,6 +378,9 @@ def run_ours(args):
         mean = sum(ms) / len(ms)
         return _max_over_ranks(mean, world), min(ms), (sampler.summary() if sampler else None)
 
+    # launch shape of the batched form picked by the library's autotuner
+    # (outside the timed region; later calls with these plans reuse it)
+    tuned = None if args.no_tune else lf.tune_batched(plans, Hs, outs)
     t_batched, best_batched, clocks = timed(step_batched, args.steps, args.warmup, clocks=True)
     t_plain, best_plain, _ = timed(step_plain, max(3, args.steps // 4), max(3, args.warmup))
 
@@ -418,6 +421,7 @@ def run_ours(args):
                      "traffic": traffic["bytes_per_launch"] if traffic else None,
                      "algorithmic_bytes_per_launch": step_bytes},
         "pct_of_8TBps_spec": round(100 * achieved / SPEC_GBS, 2),
+        "launch_shape": _tuned_desc(tuned) or "default (3 CTAs/SM, 32 KB tiles)",
         "elements_per_s": round(world * step_elems / (t_batched * 1e-3), 1),
         "best_ms_per_step": round(best_batched, 4),
         "plain": {"ms_per_step": round(t_plain, 4),
@@ -461,12 +465,38 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                            "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
     del h16, o16
     torch.cuda.empty_cache()
+    # the same array padded centrally to K = K_max at every depth (the dense
+    # form of the workload; centred cropping commutes with the map)
+    if len(specs) == 1:
+        s = specs[0]
+        Km = max(s.Ks)
+        H = Hs[0]
+        dplan = lf.Plan(s.Nx, s.Ny, [Km] * s.Nz, [Km] * s.Nz, torch.float32)
+        Hd = torch.zeros(dplan.elems, dtype=torch.float32, device="cuda")
+        for z in range(s.Nz):
+            k, o = s.Ks[z], (Km - s.Ks[z]) // 2
+            src = H[plans[0].depth_offset(z):plans[0].depth_offset(z + 1)].view(s.Nx, s.Ny, k, k)
+            dst = Hd[dplan.depth_offset(z):dplan.depth_offset(z + 1)].view(s.Nx, s.Ny, Km, Km)
+            dst[:, :, o:o + k, o:o + k] = src
+        Od = torch.empty_like(Hd)
+        nbd = 2 * Hd.numel() * 4
+        dtuned = None if args.no_tune else lf.tune_batched([dplan], [Hd], [Od])
+        tb, _, _ = timed(lambda: lf.backproject_batched([dplan], [Hd], [Od]), steps, 3)
+        tp, _, _ = timed(lambda: lf.backproject_array(dplan, Hd, Od), steps, 3)
+        res["highres_dense"] = {"K": Km, "bytes_per_step": nbd,
+                                "batched_GBps": round(world * nbd / (tb * 1e-3) / 1e9, 1),
+                                "plain_GBps": round(world * nbd / (tp * 1e-3) / 1e9, 1),
+                                "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
+                                "tuned": _tuned_desc(dtuned)}
+        del Hd, Od
+        torch.cuda.empty_cache()
     # the ragged batch: 16 arrays, mixed fp32 / fp16, one persistent launch
     rspecs = lfgen.config_specs("ragged")
     rplans = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, s.torch_dtype) for s in rspecs]
     rH = [lfgen.generate(s, device="cuda") for s in rspecs]
     rO = [torch.empty_like(h) for h in rH]
     nb = sum(2 * h.numel() * h.element_size() for h in rH)
+    rtuned = None if args.no_tune else lf.tune_batched(rplans, rH, rO)
     tb, _, _ = timed(lambda: lf.backproject_batched(rplans, rH, rO), steps, 3)
     tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(rplans, rH, rO)],
                      steps, 3)
@@ -474,11 +504,44 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                      "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
                      "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
                      "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
-                     "plain_launches_per_step": sum(s.Nz for s in rspecs)}
+                     "plain_launches_per_step": sum(s.Nz for s in rspecs),
+                     "tuned": _tuned_desc(rtuned)}
     del rH, rO
     torch.cuda.empty_cache()
     res["rl_step"] = _rl_extra(lf, timed, steps)
+    res["autograd_step"] = _autograd_extra(lf, timed, steps)
     return res
+
+
+def _autograd_extra(lf, timed, steps):
+    """The differentiation workload: L = sum((backproject(H'(H), f) - g_ref)^2),
+    forward and backward with respect to H (map, backprojection, its H'
+    gradient, adjoint map), one step timed end to end on the device."""
+    import torch
+    import lfgen
+    spec = lfgen.config_specs("autograd")[0]
+    W = 64 * spec.Nx
+    plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32)
+    H = lfgen.generate(spec, device="cuda").requires_grad_(True)
+    f = torch.from_numpy(lfgen.raw_image(64, spec.Nx, 19).astype("float32")).cuda()
+    gref = torch.from_numpy(lfgen.blob_volume(W, spec.Nz, 200, 20).astype("float32")).cuda()
+
+    def step():
+        H.grad = None
+        g = lf.backproject_volume(lf.backprojection_array(H, plan), f, plan)
+        loss = ((g - gref) ** 2).sum()
+        loss.backward()
+
+    n = max(3, steps // 8)
+    t, _, _ = timed(step, n, 3)
+    return {"workload": "autograd: N=11, 21 depths, K_z 33..99, 704 x 704 image, 200-blob g_ref",
+            "forward_backward_ms": round(t, 4)}
+
+
+def _tuned_desc(t):
+    if t is None:
+        return None
+    return {"tile_bytes": t[0], "ctas_per_sm": t[1], "stages": t[2] or "as many as fit"}
 
 
 def _fp32_fma_peak_tflops():
@@ -541,6 +604,8 @@ def main(argv=None):
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the fp16 copy and the ragged batch beside the headline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the default launch shape instead of the autotuner's")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
