@@ -606,12 +606,42 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default launch shape instead of the autotuner's")
+    ap.add_argument("--only", choices=["rl", "autograd"], default=None,
+                    help="time only one RL update (Eq. 2) or the autograd step on the "
+                         "differentiation workload and print that (for profiling)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
+
+
+def run_only(args):
+    """One of the extra measurements alone: steps//4 timed repetitions."""
+    import torch
+    import paper_2003_09133_gb300 as lf
+    torch.cuda.set_device(0)
+    lf.load()
+
+    def timed(fn, n, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        lf.sync_status()
+        return a.elapsed_time(b) / n, None, None
+
+    fn = _rl_extra if args.only == "rl" else _autograd_extra
+    print(json.dumps({"only": args.only, **fn(lf, timed, args.steps)}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
