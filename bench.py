@@ -199,10 +199,23 @@ def _cpu_oracle_rate(specs, Hs_host, dtype_override, budget_s=12.0, max_passes=3
             if t_total >= budget_s:
                 break
         passes += 1
+    # the same oracle on one thread, on the first array's middle depth (a few seconds)
+    s, H = specs[0], Hs_host[0]
+    import lfgen
+    off = lfgen.depth_offsets(s)
+    z = s.Nz // 2
+    Hz = np.ascontiguousarray(H[off[z]:off[z + 1]])
+    oracle.threads(1)
+    t0 = time.perf_counter()
+    oracle.transpose(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
+    t1 = time.perf_counter() - t0
+    oracle.threads(cores)
     return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "seconds": round(t_total, 3),
             "sample": f"{done_bytes / 2 / 1e9:.2f} GB of H mapped by oracle.transpose "
-                      f"({passes} pass(es) over {'+'.join(sample_desc)}; C, OpenMP {cores} threads)"}
+                      f"({passes} pass(es) over {'+'.join(sample_desc)}; C, OpenMP {cores} threads)",
+            "single_thread_GBps": round(2 * Hz.nbytes / t1 / 1e9, 3),
+            "single_thread_sample": f"depth {z} of {s.name} (K = {s.Ks[z]}), 1 thread"}
 
 
 def _reference_sample(specs, budget_elems=48_000_000):

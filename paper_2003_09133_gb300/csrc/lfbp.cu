@@ -1126,6 +1126,12 @@ int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgra
   if (overlaps(df, (size_t)Wx * Wy * 4, dHp_grad, p->off.back() * 4))
     return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   float* out = (float*)dHp_grad;
+  std::vector<long long> off(p->Nz);
+  for (int z = 0; z < p->Nz; ++z) off[z] = (long long)p->off[z];
+  const int prc = launch_phase_grad(df, dgrad, p->Nx, p->Ny, p->Nz, off.data(), p->Ks.data(),
+                                    p->Kt.data(), Wx, Wy, out, (cudaStream_t)cuda_stream);
+  if (prc == 0) return LFBP_OK;
+  if (prc != -1) return fail(LFBP_ERR_CUDA, "k_phase_grad launch failed");
   for (int z = 0; z < p->Nz; ++z) {
     if (launch_backproject_grad(df, dgrad + (size_t)z * Wx * Wy, p->Nx, p->Ny, p->Ks[z], p->Kt[z],
                                 Wx, Wy, out + p->off[z], (cudaStream_t)cuda_stream))

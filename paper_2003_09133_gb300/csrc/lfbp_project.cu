@@ -308,6 +308,107 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
     }
 }
 
+// ------------------------------------------------------------- phase grad --
+// dL/dH'_z[p][q][u][v] = sum over pixels S = (p + Nx i, q + Ny j) of f(S) * dg_z(S + (u,v) - c).
+// Split the taps by phase, u = Nx*sigma + rho, v = Ny*upsilon + tau: with
+//   F(i, j) = f(p + Nx i, q + Ny j),  G(a, b) = dg_z(Nx a + p + rho - c_s, Ny b + q + tau - c_t),
+// the S x S outputs of one (rho, tau) are  O[sigma][upsilon] = sum_{i,j} F(i,j) G(i+sigma, j+upsilon).
+// Block: one cell (p, q) of one depth; the cell's pixels in tiles of
+// kGrI x kGrJ.  Per tile F is staged once; per (rho, tau) the G tile is
+// staged and thread (i, sigma) sums its row of products for all upsilon in
+// registers (F and G read in blocks of S columns), then the rows are reduced:
+// a shuffle tree over a warp's 32 rows, then the two warps of each sigma in
+// order (deterministic).  Tiles after the first add to the output.
+constexpr int kGrI = 64, kGrJ = 64;
+
+template <int S>
+__global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcArgs a) {
+  constexpr int JB = (kGrJ + S - 1) / S;       // column blocks of S
+  constexpr int FJ = JB * S;                   // F tile columns (zero-padded)
+  constexpr int GR = kGrI + S - 1;             // G tile rows
+  constexpr int GJ = FJ + S - 1;               // G tile columns
+  // odd row pitches: the 32 lanes of a warp read one column of 32 rows
+  constexpr int FP = FJ | 1, GP = GJ | 1;
+  __shared__ float F_s[kGrI * FP];
+  __shared__ float G_s[GR * GP];
+  __shared__ float part[8][S];
+  const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
+  const int p = blockIdx.x / Ny, q = blockIdx.x % Ny;
+  const PcDepth dd = a.d[blockIdx.y];
+  const int Ks = dd.Ks, Kt = dd.Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
+  const float* f = a.in;
+  const float* dg = a.g + (long long)dd.z * a.out_zstride;
+  float* dA = a.out + dd.off + ((long long)p * Ny + q) * Ks * Kt;
+  const int nI = (Wx - p + Nx - 1) / Nx, nJ = (Wy - q + Ny - 1) / Ny;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  bool first_tile = true;
+  for (int i0 = 0; i0 < nI; i0 += kGrI)
+    for (int j0 = 0; j0 < nJ; j0 += kGrJ) {
+      __syncthreads();
+      for (int e = tid; e < kGrI * FJ; e += 256) {
+        const int i = e / FJ, j = e - i * FJ;
+        const bool ok = i0 + i < nI && j < kGrJ && j0 + j < nJ;
+        F_s[i * FP + j] = ok ? __ldg(f + (size_t)(p + Nx * (i0 + i)) * Wy + (q + Ny * (j0 + j))) : 0.f;
+      }
+      for (int rho = 0; rho < Nx && rho < Ks; ++rho) {
+        const int Ssig = (Ks - rho + Nx - 1) / Nx;
+        for (int tau = 0; tau < Ny && tau < Kt; ++tau) {
+          const int Sups = (Kt - tau + Ny - 1) / Ny;
+          const int xo = p + rho - cs, yo = q + tau - ct;
+          __syncthreads();  // F staged / the previous G and part consumed
+          for (int e = tid; e < GR * GJ; e += 256) {
+            const int r = e / GJ, c = e - r * GJ;
+            const int x = Nx * (i0 + r) + xo, y = Ny * (j0 + c) + yo;
+            G_s[r * GP + c] =
+                (x >= 0 && x < Wx && y >= 0 && y < Wy) ? __ldg(dg + (size_t)x * Wy + y) : 0.f;
+          }
+          __syncthreads();
+          // thread (i, sigma): i = tid % 64 (a warp holds 32 consecutive rows), sigma = round*4 + tid/64
+          for (int s0 = 0; s0 < S; s0 += 4) {
+            const int sg = s0 + (tid >> 6), i = tid & 63;
+            float acc[S];
+#pragma unroll
+            for (int up = 0; up < S; ++up) acc[up] = 0.f;
+            if (sg < S) {
+              const float* Fr = F_s + i * FP;
+              const float* Gr = G_s + (i + sg) * GP;
+              for (int jb = 0; jb < JB; ++jb) {
+                float fv[S], gv[2 * S - 1];
+#pragma unroll
+                for (int k = 0; k < S; ++k) fv[k] = Fr[jb * S + k];
+#pragma unroll
+                for (int k = 0; k < 2 * S - 1; ++k) gv[k] = Gr[jb * S + k];
+#pragma unroll
+                for (int k = 0; k < S; ++k)
+#pragma unroll
+                  for (int up = 0; up < S; ++up) acc[up] = fmaf(fv[k], gv[k + up], acc[up]);
+              }
+            }
+            // rows of the warp: shuffle tree; then the two warps of each sigma
+#pragma unroll
+            for (int up = 0; up < S; ++up) {
+              float v = acc[up];
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+              if (lane == 0) part[warp][up] = v;
+            }
+            __syncthreads();
+            if (tid < 4 * S) {  // (sigma slot, upsilon): warps 2w and 2w+1 hold sigma s0 + w
+              const int w = tid / S, up = tid - w * S, sgo = s0 + w;
+              if (sgo < Ssig && up < Sups) {
+                const float v = part[2 * w][up] + part[2 * w + 1][up];
+                float* o = dA + (size_t)(Nx * sgo + rho) * Kt + (Ny * up + tau);
+                *o = first_tile ? v : *o + v;
+              }
+            }
+            __syncthreads();
+          }
+        }
+      }
+      first_tile = false;
+    }
+}
+
 // Quotient of Eq. 2 in place: r = f / fe where fe != 0, else 0.
 __global__ void k_rl_quotient(const float* __restrict__ f, float* fe_r, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -494,6 +595,51 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         const int rc = launch_pc_size(S, a, (int)nblocks, sum_depths ? 1 : n, st);
         if (rc) return rc;
         first = false;
+        n = 0;
+      }
+    }
+  }
+  return 0;
+}
+
+int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, const long long* off,
+                      const int* Ks, const int* Kt, int Wx, int Wy, float* dA, cudaStream_t st) {
+  for (int z = 0; z < Nz; ++z)
+    if (!phase_conv_size(Nx, Ny, Ks[z], Kt[z])) return -1;
+  if ((long long)Nx * Ny > 0x7fffffffLL) return -1;
+  PcArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.in = f;
+  a.g = dg;
+  a.out_zstride = (long long)Wx * Wy;
+  a.out = dA;
+  a.Nx = Nx;
+  a.Ny = Ny;
+  a.Wx = Wx;
+  a.Wy = Wy;
+  for (int S : kPcSizes) {
+    int n = 0;
+    for (int z = 0; z <= Nz; ++z) {
+      if (z < Nz && phase_conv_size(Nx, Ny, Ks[z], Kt[z]) == S) {
+        a.d[n].off = off[z];
+        a.d[n].Ks = Ks[z];
+        a.d[n].Kt = Kt[z];
+        a.d[n].z = z;
+        ++n;
+      }
+      if (n == kPcMaxDepths || (z == Nz && n > 0)) {
+        a.ndepth = n;
+        const dim3 grid((unsigned)(Nx * Ny), (unsigned)n);
+        switch (S) {
+          case 3: k_phase_grad<3><<<grid, 256, 0, st>>>(a); break;
+          case 5: k_phase_grad<5><<<grid, 256, 0, st>>>(a); break;
+          case 7: k_phase_grad<7><<<grid, 256, 0, st>>>(a); break;
+          case 9: k_phase_grad<9><<<grid, 256, 0, st>>>(a); break;
+          case 11: k_phase_grad<11><<<grid, 256, 0, st>>>(a); break;
+          case 13: k_phase_grad<13><<<grid, 256, 0, st>>>(a); break;
+          default: k_phase_grad<15><<<grid, 256, 0, st>>>(a); break;
+        }
+        if (cudaGetLastError() != cudaSuccess) return -6;
         n = 0;
       }
     }
