@@ -243,10 +243,9 @@ struct lfbp_plan_s {
   int es = 4;
   std::vector<size_t> off;  // Nz + 1
   unsigned long long uid = 0;
-  // per-depth tiling for the tile-size target `tiling_target` (built lazily)
+  // per-depth tilings by tile-size target (built lazily; entries stay put)
   std::mutex mu;
-  int tiling_target = 0;
-  std::vector<lfbp::DepthTiling> tiling;
+  std::map<int, std::vector<lfbp::DepthTiling>> tilings;
 };
 
 namespace {
@@ -325,13 +324,12 @@ int device_props(int* dev, int* sms, int* smem_optin) {
 // Per-depth tiling of a plan for a tile-size target, cached in the plan.
 const std::vector<DepthTiling>& plan_tiling(lfbp_plan p, int target) {
   std::lock_guard<std::mutex> lk(p->mu);
-  if (p->tiling_target != target || (int)p->tiling.size() != p->Nz) {
-    p->tiling.clear();
-    for (int z = 0; z < p->Nz; ++z)
-      p->tiling.push_back(tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, target));
-    p->tiling_target = target;
+  std::vector<DepthTiling>& t = p->tilings[target];
+  if ((int)t.size() != p->Nz) {
+    t.clear();
+    for (int z = 0; z < p->Nz; ++z) t.push_back(tile_depth(p->Ny, p->Ks[z], p->Kt[z], p->es, target));
   }
-  return p->tiling;
+  return t;
 }
 
 TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr) {
@@ -349,12 +347,19 @@ TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr)
 }
 
 // One launch per depth of the plain kernel, for depths [z0, z1).
+// Tile-size target of the plain form: one tile per CTA and no pipeline, so
+// larger tiles than the persistent form's pay (measured on highres: 64 KB
+// 4705 GB/s, 48 KB 4535, 32 KB 4390).
+int plain_tile_bytes() {
+  int t = env_int("LFBP_PLAIN_TILE_BYTES", 65536);
+  return t < 1024 ? 1024 : (t > 65536 ? 65536 : t);
+}
+
 int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int mode, int z0,
                  int z1, cudaStream_t st) {
-  const Tuning tu = default_tuning();
   const size_t arr_bytes = p->off.back() * (size_t)p->es;
   const unsigned char* safe_end = inb + (arr_bytes & ~(size_t)15);
-  const std::vector<DepthTiling>& tl = plan_tiling(p, tu.tile_bytes);
+  const std::vector<DepthTiling>& tl = plan_tiling(p, plain_tile_bytes());
   int max_smem = 0;
   for (int z = z0; z < z1; ++z) max_smem = std::max(max_smem, tl[z].max_tile_bytes);
   int rc = ensure_smem_attr((const void*)k_gather_depth, plain_smem_bytes((max_smem + 15) & ~15));

@@ -83,6 +83,7 @@ SHAPES = [
     (5, 3, [3, 5, 7], [5, 7, 3], 32768),     # rows shorter than a sector
     (3, 3, [1, 1], [1, 1], 32768),
     (17, 17, [255], [255], 32768),
+    (15, 15, [45, 75], [45, 75], 65536),  # the plain form's tile target: up to 64 rows
 ]
 
 
