@@ -433,12 +433,14 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   HostPipe* hp = nullptr;
   if ((rc = get_pipe(dev, &hp))) return rc;
-  // chunks of consecutive depths of at least 32 MB each (fewer, larger copies)
+  // chunks of consecutive depths of at least LFBP_HOST_CHUNK_MB (default 32)
+  // MB each (fewer, larger copies)
+  const size_t chunk_min = (size_t)std::max(1, env_int("LFBP_HOST_CHUNK_MB", 32)) << 20;
   std::vector<int> cut(1, 0);
   size_t acc = 0;
   for (int z = 0; z < p->Nz; ++z) {
     acc += (p->off[z + 1] - p->off[z]) * (size_t)p->es;
-    if (acc >= (32u << 20) || z + 1 == p->Nz) {
+    if (acc >= chunk_min || z + 1 == p->Nz) {
       cut.push_back(z + 1);
       acc = 0;
     }
