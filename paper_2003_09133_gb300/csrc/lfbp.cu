@@ -1188,18 +1188,28 @@ int rl_step_impl(lfbp_plan p, const void* dH, const void* dHp, const float* dnor
   const float* h = (const float*)dH;
   const float* hp = (const float*)dHp;
   const long long W2 = (long long)Wx * Wy;
-  // H g, summed over depths in order (weights: the map of H, or H' itself)
   if (p->Nz == 0) {
     cudaError_t e = cudaMemsetAsync(dwork, 0, img, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    if (launch_rl_quotient(df, dwork, W2, st))
+      return fail(LFBP_ERR_CUDA, "k_rl_quotient launch failed");
+  } else if ((const void*)dg_next != (const void*)dg) {
+    // H g as per-depth partials in dg_next (one block per depth and tile: the
+    // whole GPU busy), then their fixed-order sum and the quotient f / (H g)
+    // into dwork; the update below overwrites the partials after their use
+    rc = hp ? project(p, hp, 0, h, 0, dg, W2, dg_next, W2, nullptr, nullptr, Wx, Wy, 0, kEpiStore, st)
+            : project(p, h, 1, h, 0, dg, W2, dg_next, W2, nullptr, nullptr, Wx, Wy, 0, kEpiStore, st);
+    if (rc) return rc;
+    if (launch_rl_sum_quotient(dg_next, p->Nz, W2, df, dwork, st))
+      return fail(LFBP_ERR_CUDA, "k_rl_sum_quotient launch failed");
   } else {
+    // in place: H g summed over depths inside each block, then f / (H g)
     rc = hp ? project(p, hp, 0, h, 0, dg, W2, dwork, 0, nullptr, nullptr, Wx, Wy, 1, kEpiStore, st)
             : project(p, h, 1, h, 0, dg, W2, dwork, 0, nullptr, nullptr, Wx, Wy, 1, kEpiStore, st);
     if (rc) return rc;
+    if (launch_rl_quotient(df, dwork, W2, st))
+      return fail(LFBP_ERR_CUDA, "k_rl_quotient launch failed");
   }
-  // f / (H g)
-  if (launch_rl_quotient(df, dwork, W2, st))
-    return fail(LFBP_ERR_CUDA, "k_rl_quotient launch failed");
   // g / (H'1) * H' (f / (H g)), depth by depth (weights: H, or the map of H')
   return hp ? project(p, hp, 1, hp, 0, dwork, 0, dg_next, W2, dg, dnorm, Wx, Wy, 0, kEpiRL, st)
             : project(p, h, 0, h, 1, dwork, 0, dg_next, W2, dg, dnorm, Wx, Wy, 0, kEpiRL, st);

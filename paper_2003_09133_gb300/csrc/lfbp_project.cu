@@ -418,6 +418,19 @@ __global__ void k_rl_quotient(const float* __restrict__ f, float* fe_r, long lon
   }
 }
 
+// Sum of per-depth partial forward projections (fixed order z = 0..Nz-1),
+// then the quotient of Eq. 2: r[i] = f[i] / sum_z parts[z][i] (0 where the
+// sum is 0).
+__global__ void k_rl_sum_quotient(const float* __restrict__ parts, int Nz, long long n,
+                                  const float* __restrict__ f, float* __restrict__ r) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float s = 0.f;
+    for (int z = 0; z < Nz; ++z) s += parts[(long long)z * n + i];
+    r[i] = s != 0.f ? f[i] / s : 0.f;
+  }
+}
+
 __global__ void k_fill(float* x, long long n, float v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -654,6 +667,12 @@ static unsigned elementwise_blocks(long long n) {
 
 int launch_rl_quotient(const float* f, float* fe_r, long long n, cudaStream_t st) {
   k_rl_quotient<<<elementwise_blocks(n), 256, 0, st>>>(f, fe_r, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
+int launch_rl_sum_quotient(const float* parts, int Nz, long long n, const float* f, float* r,
+                           cudaStream_t st) {
+  k_rl_sum_quotient<<<elementwise_blocks(n), 256, 0, st>>>(parts, Nz, n, f, r);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 

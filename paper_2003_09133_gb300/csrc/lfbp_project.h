@@ -42,6 +42,9 @@ int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, c
                       const int* Ks, const int* Kt, int Wx, int Wy, float* dA, cudaStream_t st);
 // fe_r[i] = f[i] / fe_r[i] where fe_r[i] != 0, else 0 (the quotient of Eq. 2)
 int launch_rl_quotient(const float* f, float* fe_r, long long n, cudaStream_t st);
+// r[i] = f[i] / sum_{z < Nz} parts[z*n + i] (fixed order; 0 where the sum is 0)
+int launch_rl_sum_quotient(const float* parts, int Nz, long long n, const float* f, float* r,
+                           cudaStream_t st);
 int launch_fill(float* x, long long n, float v, cudaStream_t st);
 
 }  // namespace lfbp
