@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <vector>
 
 #include "lfbp_project.h"
 
@@ -409,6 +410,142 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
     }
 }
 
+// The same sum for DB depths of one cut-out size that read the same input
+// image (the backprojections): each staged subgrid of the shared image feeds
+// the DB depths' weights, so staging is paid once per DB depths.  Block: one
+// output phase, a 32 x 64 output tile, depths d[blockIdx.y*DB .. +DB) (missing
+// depths at the end get zero weights and no output).
+template <int S, int DB>
+__global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_constant__ PcArgs a) {
+  constexpr int RI = 4, TI = 8 * RI;
+  constexpr int S4 = (S + 3) & ~3;
+  constexpr int IR = TI + S - 1;
+  constexpr int IC = kPcTJ + S;
+  constexpr int ICP = (IC + 1) & ~1;
+  __shared__ __align__(16) float w_s[2][DB * S * S4];
+  __shared__ __align__(16) float I_s[2][IR * ICP];
+  const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
+  int t = blockIdx.x;
+  const int tj = t % a.nTJ;
+  t /= a.nTJ;
+  const int ti = t % a.nTI;
+  t /= a.nTI;
+  const int py = t % Ny, px = t / Ny;
+  const int i0 = ti * TI, j0 = tj * kPcTJ;
+  const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
+  const int a0 = wi * RI, b0 = 2 * lane;
+  const int dbase = (int)blockIdx.y * DB;
+  const int nd = min(DB, a.ndepth - dbase);
+  const int Ks = a.d[dbase].Ks, Kt = a.d[dbase].Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
+  const int nrho = min(Nx, Ks), ntau = min(Ny, Kt);
+
+  auto stage = [&](int rho, int tau, int buf) {
+    const int Ssig = (Ks - rho + Nx - 1) / Nx, Sups = (Kt - tau + Ny - 1) / Ny;
+    const int xoff = px + rho - cs, yoff = py + tau - ct;
+    const int ar = pmod(xoff, Nx), br = pmod(yoff, Ny);
+    for (int e = tid; e < DB * S * S4; e += kPcThreads) {
+      const int dd = e / (S * S4), ee = e - dd * (S * S4);
+      const int sg = ee / S4, up = ee - sg * S4;
+      const bool ok = dd < nd && sg < Ssig && up < Sups;
+      const float* Az = a.A + (ok ? a.d[dbase + dd].off : 0);
+      const int u = Nx * sg + rho, v = Ny * up + tau;
+      const float* src =
+          !ok ? a.A
+              : a.mapped ? Az + (((size_t)ar * Ny + br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
+                         : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
+      cp_async4(&w_s[buf][e], src, ok);
+    }
+    for (int r = wi; r < IR; r += kPcThreads / 32) {
+      const int x = Nx * (i0 + r) + xoff;
+      const bool xin = x >= 0 && x < Wx;
+      const float* row = a.in + (size_t)(xin ? x : 0) * Wy;
+      for (int col = lane; col < ICP; col += 32) {
+        const int y = Ny * (j0 + col) + yoff;
+        const bool ok = xin && col < IC && y >= 0 && y < Wy;
+        cp_async4(&I_s[buf][r * ICP + col], ok ? row + y : a.in, ok);
+      }
+    }
+    cp_async_commit();
+  };
+
+  float acc[DB][RI][2];
+#pragma unroll
+  for (int d = 0; d < DB; ++d)
+#pragma unroll
+    for (int i = 0; i < RI; ++i) acc[d][i][0] = acc[d][i][1] = 0.f;
+  int rho = 0, tau = 0;
+  stage(0, 0, 0);
+  for (int k = 0;; ++k) {
+    const int buf = k & 1;
+    int nrho2 = rho, ntau2 = tau + 1;
+    if (ntau2 >= ntau) {
+      ntau2 = 0;
+      ++nrho2;
+    }
+    const bool more = nrho2 < nrho;
+    if (more)
+      stage(nrho2, ntau2, buf ^ 1);
+    else
+      cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const float* Ib = I_s[buf];
+#pragma unroll
+    for (int r = 0; r < RI + S - 1; ++r) {
+      float xv[S + 2];
+      const float* src = Ib + (a0 + r) * ICP + b0;
+#pragma unroll
+      for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
+        const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
+        xv[2 * c2] = p.x;
+        xv[2 * c2 + 1] = p.y;
+      }
+#pragma unroll
+      for (int d = 0; d < DB; ++d) {
+        const float* wb = w_s[buf] + d * (S * S4);
+#pragma unroll
+        for (int sg = 0; sg < S; ++sg) {
+          const int ai = r - sg;
+          if (ai < 0 || ai >= RI) continue;
+#pragma unroll
+          for (int up = 0; up < S; ++up) {
+            const float wv = wb[sg * S4 + up];
+            acc[d][ai][0] = fmaf(xv[up], wv, acc[d][ai][0]);
+            acc[d][ai][1] = fmaf(xv[up + 1], wv, acc[d][ai][1]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!more) break;
+    rho = nrho2;
+    tau = ntau2;
+  }
+  cp_async_wait<0>();
+
+#pragma unroll
+  for (int d = 0; d < DB; ++d) {
+    if (d >= nd) break;
+    const long long zo = (long long)a.d[dbase + d].z * a.out_zstride;
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
+        if (X >= Wx || Y >= Wy) continue;
+        const long long o = zo + (long long)X * Wy + Y;
+        if (a.epi == kEpiStore) {
+          a.out[o] = acc[d][i][c];
+        } else if (a.epi == kEpiAccumulate) {
+          a.out[o] += acc[d][i][c];
+        } else {
+          const float n = a.norm[o];
+          a.out[o] = n != 0.f ? (a.g[o] / n) * acc[d][i][c] : 0.f;
+        }
+      }
+  }
+}
+
 // Quotient of Eq. 2 in place: r = f / fe where fe != 0, else 0.
 __global__ void k_rl_quotient(const float* __restrict__ f, float* fe_r, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -554,6 +691,18 @@ int launch_pc_size(int S, const PcArgs& a, int nblocks, int ny, cudaStream_t st)
 }
 }  // namespace
 
+constexpr int kPcDB = 4;  // depths per block of k_phase_conv_md
+
+int launch_pc_md(int S, const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
+  const dim3 grid((unsigned)nblocks, (unsigned)ny);
+  switch (S) {  // small cut-outs only: there staging dominates one depth's work
+    case 3: k_phase_conv_md<3, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
+    case 5: k_phase_conv_md<5, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
+    default: k_phase_conv_md<7, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
 int phase_conv_size(int Nx, int Ny, int Ks, int Kt) {
   const int s = std::max((Ks + Nx - 1) / Nx, (Kt + Ny - 1) / Ny);
   for (int S : kPcSizes)
@@ -589,11 +738,39 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   a.sum_depths = sum_depths;
   const long long nblocks = (long long)Nx * Ny * a.nTI * a.nTJ;
   if (nblocks > 0x7fffffffLL) return -1;
+  // depths that read one shared image (backprojections) in groups of one
+  // cut-out size: several depths per block (k_phase_conv_md)
+  std::vector<char> done(Nz, 0);
+  if (!sum_depths && in_zstride == 0) {
+    for (int z0 = 0; z0 < Nz; ++z0) {
+      if (done[z0]) continue;
+      std::vector<int> grp;
+      for (int z = z0; z < Nz; ++z)
+        if (!done[z] && Ks[z] == Ks[z0] && Kt[z] == Kt[z0]) grp.push_back(z);
+      const int S = phase_conv_size(Nx, Ny, Ks[z0], Kt[z0]);
+      if ((int)grp.size() < 3 || S > 7) continue;  // one depth per block
+      for (size_t g0 = 0; g0 < grp.size(); g0 += kPcMaxDepths) {
+        const int n = (int)std::min(grp.size() - g0, (size_t)kPcMaxDepths);
+        for (int i = 0; i < n; ++i) {
+          const int z = grp[g0 + i];
+          a.d[i].off = off[z];
+          a.d[i].Ks = Ks[z];
+          a.d[i].Kt = Kt[z];
+          a.d[i].z = z;
+          done[z] = 1;
+        }
+        a.ndepth = n;
+        a.epi = epi;
+        const int rc = launch_pc_md(S, a, (int)nblocks, (n + kPcDB - 1) / kPcDB, st);
+        if (rc) return rc;
+      }
+    }
+  }
   bool first = true;
   for (int S : kPcSizes) {  // one launch per instance size (and per 64 depths)
     int n = 0;
     for (int z = 0; z <= Nz; ++z) {
-      const bool take = z < Nz && phase_conv_size(Nx, Ny, Ks[z], Kt[z]) == S;
+      const bool take = z < Nz && !done[z] && phase_conv_size(Nx, Ny, Ks[z], Kt[z]) == S;
       if (take) {
         a.d[n].off = off[z];
         a.d[n].Ks = Ks[z];

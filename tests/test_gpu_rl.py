@@ -52,6 +52,7 @@ CASES = [  # Nx, Ny, Ks, Kt, Wx, Wy
     (5, 5, [15, 5, 25], [15, 5, 25], 37, 40),
     (1, 1, [3], [5], 9, 7),
     (11, 11, [33, 99], [33, 99], 66, 77),
+    (3, 5, [9] * 5 + [15], [15] * 5 + [5], 30, 41),  # five equal cut-outs: several depths per block
 ]
 
 
