@@ -237,3 +237,39 @@ def test_tuner_then_batched(lf, tmp_path, monkeypatch):
     # a second process-level tune reads the cache instead of timing
     assert lf.tune_batched(plans, Hs, reps=1) == (tb, cps, st)
     lf.sync_status()
+
+
+def test_ragged_workload_full_tuned(lf):
+    """The ragged batch in the launch shape the bench times: the autotuner's pick."""
+    specs = lfgen.config_specs("ragged")
+    plans = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, s.torch_dtype) for s in specs]
+    Hs = [lfgen.generate(s, device="cuda").to(s.torch_dtype) for s in specs]
+    lf.tune_batched(plans, Hs, reps=1)
+    outs = lf.backproject_batched(plans, Hs)
+    lf.sync_status()
+    for i, (s, H) in enumerate(zip(specs, Hs)):
+        want = oracle.transpose(H.cpu().numpy(), s.Nx, s.Ny, s.Ks, s.Kt)
+        _assert_same_bits(outs[i], want, f"ragged[{i}] tuned")
+        outs[i] = None
+        Hs[i] = None
+        del want
+        torch.cuda.empty_cache()
+
+
+def test_every_launch_shape_of_the_tuner_grid(lf, monkeypatch):
+    """Each tile-size x CTAs-per-SM shape the autotuner may pick maps bit-exactly
+    (mid workload, fp32, and its fp16 copy in the same batch)."""
+    spec = lfgen.config_specs("mid")[0]
+    H32 = lfgen.generate(spec, device="cuda")
+    H16 = H32.half()
+    plans = [lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32),
+             lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float16)]
+    want = [oracle.transpose(h.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt) for h in (H32, H16)]
+    for tb in (16384, 24576, 32768, 49152):
+        for cps in (2, 3, 4):
+            monkeypatch.setenv("LFBP_TILE_BYTES", str(tb))
+            monkeypatch.setenv("LFBP_CTAS_PER_SM", str(cps))
+            outs = lf.backproject_batched(plans, [H32, H16])
+            lf.sync_status()
+            for o, w in zip(outs, want):
+                _assert_same_bits(o, w, f"tile {tb} cps {cps}")

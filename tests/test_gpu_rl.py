@@ -180,3 +180,22 @@ def test_rl_validation(lf):
     rc = lib.lfbp_rl_step(plan.handle, H32.data_ptr(), None, g.data_ptr(), f.data_ptr(), 12, 12,
                           g.data_ptr(), g.data_ptr(), work.data_ptr(), None)
     assert rc == -2
+
+
+def test_projectors_are_deterministic(lf):
+    """Fixed-order fp32 sums, no atomics: repeated calls give identical bits."""
+    spec = lfgen.config_specs("autograd")[0]
+    Nx, Ny, Ks, Kt = spec.Nx, spec.Ny, list(spec.Ks), list(spec.Kt)
+    W = 6 * Nx
+    plan = lf.Plan(Nx, Ny, Ks, Kt, torch.float32)
+    Hd = lfgen.generate(spec, device="cuda")
+    f = torch.from_numpy(lfgen.raw_image(64, Nx, 19)[:W, :W].astype(np.float32).copy()).cuda()
+    g = torch.rand((len(Ks), W, W), device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    norm = lf.rl_normaliser(plan, Hd, None, W, W)
+    outs = [lf.rl_step(plan, Hd, None, norm, f, g).cpu().numpy() for _ in range(2)]
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+    grads = [lf.backproject_volume_grad(plan, f, g).cpu().numpy() for _ in range(2)]
+    assert np.array_equal(grads[0].view(np.uint32), grads[1].view(np.uint32))
+    fw = [lf.forward_project(plan, Hd, g).cpu().numpy() for _ in range(2)]
+    assert np.array_equal(fw[0].view(np.uint32), fw[1].view(np.uint32))
+    lf.sync_status()
