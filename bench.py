@@ -470,12 +470,14 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
     h16 = [h.half() for h in Hs]
     o16 = [torch.empty_like(h) for h in h16]
     nb = sum(2 * h.numel() * 2 for h in h16)
+    tuned16 = None if args.no_tune else lf.tune_batched(p16, h16, o16)
     tb, _, _ = timed(lambda: lf.backproject_batched(p16, h16, o16), steps, 3)
     tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(p16, h16, o16)],
                      steps, 3)
     res["highres_fp16"] = {"batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
                            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
-                           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+                           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4),
+                           "tuned": _tuned_desc(tuned16)}
     del h16, o16
     torch.cuda.empty_cache()
     # the same array padded centrally to K = K_max at every depth (the dense
