@@ -165,8 +165,8 @@ int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* 
 
 /*
  * Autotuner for lfbp_backproject_batched: times a small grid of launch shapes
- * (shared-memory bytes per tile in {16, 24, 32, 48} KiB x persistent CTAs per
- * SM in {2, 3, 4}) on the given buffers with CUDA events (reps timed launches
+ * (shared-memory bytes per tile in {12, 16, 24, 32, 40, 48, 64} KiB x
+ * persistent CTAs per SM in {1, 2, 3, 4}) on the given buffers with CUDA events (reps timed launches
  * each, after one warm-up) and keeps the fastest for later batched calls with
  * the same plans (by handle).  Writes H' into dHp as a side effect and
  * synchronises the stream.  If the environment variable LFBP_TUNE_CACHE names

@@ -861,8 +861,8 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
   const std::string sig = plans_signature(dev, n, plans);
   Tuning best = default_tuning();
   if (!cache_lookup(sig, &best)) {
-    const int tiles[] = {16384, 24576, 32768, 49152};
-    const int ctas[] = {2, 3, 4};
+    const int tiles[] = {12288, 16384, 24576, 32768, 40960, 49152, 65536};
+    const int ctas[] = {1, 2, 3, 4};
     float best_ms = 1e30f;
     cudaEvent_t a, b;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");

@@ -228,7 +228,7 @@ def test_tuner_then_batched(lf, tmp_path, monkeypatch):
     plans = [lf.Plan(a, b, c, d, t) for a, b, c, d, t in shapes]
     Hs = [_random_bits(p.elems, p.dtype, 40 + i) for i, p in enumerate(plans)]
     tb, cps, st = lf.tune_batched(plans, Hs, reps=1)
-    assert tb in (16384, 24576, 32768, 49152) and cps in (2, 3, 4)
+    assert tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536) and cps in (1, 2, 3, 4)
     assert (tmp_path / "tune.txt").read_text().strip()
     for rep in range(2):
         outs = lf.backproject_batched(plans, Hs)
@@ -265,8 +265,8 @@ def test_every_launch_shape_of_the_tuner_grid(lf, monkeypatch):
     plans = [lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32),
              lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float16)]
     want = [oracle.transpose(h.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt) for h in (H32, H16)]
-    for tb in (16384, 24576, 32768, 49152):
-        for cps in (2, 3, 4):
+    for tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536):
+        for cps in (1, 2, 3, 4):
             monkeypatch.setenv("LFBP_TILE_BYTES", str(tb))
             monkeypatch.setenv("LFBP_CTAS_PER_SM", str(cps))
             outs = lf.backproject_batched(plans, [H32, H16])
