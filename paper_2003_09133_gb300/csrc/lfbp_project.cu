@@ -187,8 +187,9 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
   constexpr int TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;   // weight row pitch
   constexpr int IR = TI + S - 1;     // subgrid rows
-  constexpr int IC = kPcTJ + S;      // subgrid columns (lane cols 2l .. 2l+S)
-  constexpr int ICP = (IC + 1) & ~1; // even pitch: 8-byte aligned pairs
+  constexpr int RH = RI / 2;         // output rows per thread (half a warp per row group)
+  constexpr int IC = kPcTJ + S + 3;  // subgrid columns (lane cols 4l .. 4l+S+2, read in fours)
+  constexpr int ICP = (IC + 3) & ~3; // 16-byte aligned rows
   __shared__ __align__(16) float w_s[2][S * S4];
   __shared__ __align__(16) float I_s[2][IR * ICP];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
@@ -200,7 +201,8 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
   const int py = t % Ny, px = t / Ny;
   const int i0 = ti * TI, j0 = tj * kPcTJ;
   const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
-  const int a0 = wi * RI, b0 = 2 * lane;
+  // lanes 0-15 and 16-31 take the two halves of the warp's RI rows; 4 columns each
+  const int a0 = wi * RI + (lane >> 4) * RH, b0 = 4 * (lane & 15);
   const int d_lo = a.sum_depths ? 0 : (int)blockIdx.y;
   const int d_hi = a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
 
@@ -244,9 +246,9 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
     return ++c.di < d_hi;
   };
 
-  float acc[RI][2];
+  float acc[RH][4];
 #pragma unroll
-  for (int i = 0; i < RI; ++i) acc[i][0] = acc[i][1] = 0.f;
+  for (int i = 0; i < RH; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
   PcCursor cur{d_lo, 0, 0};
   PcCursor nxt = cur;
   bool more = advance(nxt);
@@ -262,24 +264,26 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
     const float* Ib = I_s[buf];
     const float* wb = w_s[buf];
 #pragma unroll
-    for (int r = 0; r < RI + S - 1; ++r) {
-      float xv[S + 2];
+    for (int r = 0; r < RH + S - 1; ++r) {
+      float xv[4 * ((S + 6) / 4)];
       const float* src = Ib + (a0 + r) * ICP + b0;
 #pragma unroll
-      for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
-        const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
-        xv[2 * c2] = p.x;
-        xv[2 * c2 + 1] = p.y;
+      for (int c4 = 0; c4 < (S + 6) / 4; ++c4) {
+        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c4);
+        xv[4 * c4] = p.x;
+        xv[4 * c4 + 1] = p.y;
+        xv[4 * c4 + 2] = p.z;
+        xv[4 * c4 + 3] = p.w;
       }
 #pragma unroll
       for (int sg = 0; sg < S; ++sg) {
         const int ai = r - sg;
-        if (ai < 0 || ai >= RI) continue;
+        if (ai < 0 || ai >= RH) continue;
 #pragma unroll
         for (int up = 0; up < S; ++up) {
           const float wv = wb[sg * S4 + up];
-          acc[ai][0] = fmaf(xv[up], wv, acc[ai][0]);
-          acc[ai][1] = fmaf(xv[up + 1], wv, acc[ai][1]);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[ai][c] = fmaf(xv[up + c], wv, acc[ai][c]);
         }
       }
     }
@@ -292,9 +296,9 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
 
   const long long zo = a.sum_depths ? 0 : (long long)a.d[blockIdx.y].z * a.out_zstride;
 #pragma unroll
-  for (int i = 0; i < RI; ++i)
+  for (int i = 0; i < RH; ++i)
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < 4; ++c) {
       const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
       if (X >= Wx || Y >= Wy) continue;
       const long long o = zo + (long long)X * Wy + Y;
@@ -420,8 +424,9 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
   constexpr int RI = 4, TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;
   constexpr int IR = TI + S - 1;
-  constexpr int IC = kPcTJ + S;
-  constexpr int ICP = (IC + 1) & ~1;
+  constexpr int RH = RI / 2;
+  constexpr int IC = kPcTJ + S + 3;
+  constexpr int ICP = (IC + 3) & ~3;
   __shared__ __align__(16) float w_s[2][DB * S * S4];
   __shared__ __align__(16) float I_s[2][IR * ICP];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
@@ -433,7 +438,8 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
   const int py = t % Ny, px = t / Ny;
   const int i0 = ti * TI, j0 = tj * kPcTJ;
   const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
-  const int a0 = wi * RI, b0 = 2 * lane;
+  // lanes 0-15 and 16-31 take the two halves of the warp's RI rows; 4 columns each
+  const int a0 = wi * RI + (lane >> 4) * RH, b0 = 4 * (lane & 15);
   const int dbase = (int)blockIdx.y * DB;
   const int nd = min(DB, a.ndepth - dbase);
   const int Ks = a.d[dbase].Ks, Kt = a.d[dbase].Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
@@ -468,11 +474,11 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
     cp_async_commit();
   };
 
-  float acc[DB][RI][2];
+  float acc[DB][RH][4];
 #pragma unroll
   for (int d = 0; d < DB; ++d)
 #pragma unroll
-    for (int i = 0; i < RI; ++i) acc[d][i][0] = acc[d][i][1] = 0.f;
+    for (int i = 0; i < RH; ++i) acc[d][i][0] = acc[d][i][1] = acc[d][i][2] = acc[d][i][3] = 0.f;
   int rho = 0, tau = 0;
   stage(0, 0, 0);
   for (int k = 0;; ++k) {
@@ -491,14 +497,16 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
     __syncthreads();
     const float* Ib = I_s[buf];
 #pragma unroll
-    for (int r = 0; r < RI + S - 1; ++r) {
-      float xv[S + 2];
+    for (int r = 0; r < RH + S - 1; ++r) {
+      float xv[4 * ((S + 6) / 4)];
       const float* src = Ib + (a0 + r) * ICP + b0;
 #pragma unroll
-      for (int c2 = 0; c2 < (S + 2) / 2; ++c2) {
-        const float2 p = *reinterpret_cast<const float2*>(src + 2 * c2);
-        xv[2 * c2] = p.x;
-        xv[2 * c2 + 1] = p.y;
+      for (int c4 = 0; c4 < (S + 6) / 4; ++c4) {
+        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c4);
+        xv[4 * c4] = p.x;
+        xv[4 * c4 + 1] = p.y;
+        xv[4 * c4 + 2] = p.z;
+        xv[4 * c4 + 3] = p.w;
       }
 #pragma unroll
       for (int d = 0; d < DB; ++d) {
@@ -506,12 +514,12 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
 #pragma unroll
         for (int sg = 0; sg < S; ++sg) {
           const int ai = r - sg;
-          if (ai < 0 || ai >= RI) continue;
+          if (ai < 0 || ai >= RH) continue;
 #pragma unroll
           for (int up = 0; up < S; ++up) {
             const float wv = wb[sg * S4 + up];
-            acc[d][ai][0] = fmaf(xv[up], wv, acc[d][ai][0]);
-            acc[d][ai][1] = fmaf(xv[up + 1], wv, acc[d][ai][1]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[d][ai][c] = fmaf(xv[up + c], wv, acc[d][ai][c]);
           }
         }
       }
@@ -528,9 +536,9 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
     if (d >= nd) break;
     const long long zo = (long long)a.d[dbase + d].z * a.out_zstride;
 #pragma unroll
-    for (int i = 0; i < RI; ++i)
+    for (int i = 0; i < RH; ++i)
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < 4; ++c) {
         const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
         if (X >= Wx || Y >= Wy) continue;
         const long long o = zo + (long long)X * Wy + Y;
