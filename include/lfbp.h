@@ -276,6 +276,13 @@ int lfbp_rl_normaliser(lfbp_plan p, const void* dH, const void* dHp, int Wx, int
  * word for the current device: LFBP_OK, or LFBP_ERR_TIMEOUT when a bounded
  * in-kernel wait gave up (the output is then incomplete), or LFBP_ERR_CUDA
  * when the synchronisation itself failed.
+ *
+ * Tests of the error paths: the environment variable LFBP_FAULT (read at each
+ * call) injects a failure -- "plan" (plan creation returns LFBP_ERR_NOMEM),
+ * "alloc" (building a batch's work list returns LFBP_ERR_NOMEM), "graph" (its
+ * graph instantiation returns LFBP_ERR_CUDA) or "stall" (persistent launches
+ * issue no copies, so their bounded waits run out and this call returns
+ * LFBP_ERR_TIMEOUT about 2 s later).  Unset in normal use.
  */
 int lfbp_sync_status(void* cuda_stream);
 

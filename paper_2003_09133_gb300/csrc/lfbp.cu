@@ -29,6 +29,13 @@ namespace lfbp {
 // written by a kernel whose bounded wait gave up.
 __device__ int g_status;
 
+// Fault injection for tests of the error paths (LFBP_FAULT=stall, host side):
+// 1 makes the persistent kernel's producers register their copies' bytes on
+// the full barrier without issuing the copies, so every consumer wait runs
+// out (a barrier phase nothing completes) and the kernel ends with
+// LFBP_ERR_TIMEOUT in g_status.  0 in normal use.
+__device__ int g_fault;
+
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
 constexpr int kProducerWarps = 2;  // warps sharing each tile's bulk copies
@@ -145,6 +152,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
     }
     fence_mbar_init();
   }
+  const bool stall = g_fault == 1;  // injected: register bytes, issue no copies
   __syncthreads();
 
   if (warp < kProducerWarps) {
@@ -180,8 +188,12 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       const unsigned char* in_arr = ptrs.in[td.arr];
       const unsigned char* in_depth = in_arr + td.off_bytes;
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
-      issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
-                       kProducerWarps);
+      if (stall) {
+        if (lane == 0) mbar_expect_tx(fb, 16);
+      } else {
+        issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
+                         kProducerWarps);
+      }
       // the tile context is built while the copies are in flight
       if (warp == 0) {
         unsigned char* info = info_base + (size_t)s * kInfoBytes;
@@ -197,7 +209,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
     }
     // make sure no copy into this CTA's shared memory is still in flight (the
     // full barriers count the bytes of every producer warp's copies)
-    if (lane == 0) {
+    if (lane == 0 && !stall) {
       const int armed = it;  // stages armed: iterations 0..it-1
       for (int s = 0; s < nstages && s < armed; ++s) {
         const int last = ((armed - 1 - s) / nstages) * nstages + s;  // last iteration using s
@@ -263,6 +275,36 @@ int cuda_fail(cudaError_t e, const char* what) {
 
 std::mutex g_mu;
 unsigned long long g_next_uid = 1;
+
+// LFBP_FAULT: plan | alloc | graph | stall -- injected failures for tests of
+// the error paths (plan creation, the work list's device allocation, the
+// graph instantiation, a persistent kernel whose waits run out).
+enum Fault { kFaultNone = 0, kFaultPlan, kFaultAlloc, kFaultGraph, kFaultStall };
+int fault_mode() {
+  const char* s = std::getenv("LFBP_FAULT");
+  if (!s || !*s) return kFaultNone;
+  if (!std::strcmp(s, "plan")) return kFaultPlan;
+  if (!std::strcmp(s, "alloc")) return kFaultAlloc;
+  if (!std::strcmp(s, "graph")) return kFaultGraph;
+  if (!std::strcmp(s, "stall")) return kFaultStall;
+  return kFaultNone;
+}
+
+// Keep the device's g_fault equal to the stall injection (in stream order).
+int sync_device_fault(int dev, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<int, int> current;
+  const int want = fault_mode() == kFaultStall ? 1 : 0;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = current.find(dev);
+  if ((it == current.end() && want == 0) || (it != current.end() && it->second == want)) return 0;
+  cudaError_t e = cudaMemcpyToSymbolAsync(g_fault, &want, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return -1;
+  e = cudaStreamSynchronize(st);  // `want` lives on this stack frame
+  if (e != cudaSuccess) return -1;
+  current[dev] = want;
+  return 0;
+}
 
 int env_int(const char* name, int dflt) {
   const char* s = std::getenv(name);
@@ -577,6 +619,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   bs.grid = std::max(1, std::min(sms * tu.ctas_per_sm, bs.ntiles));
   cudaError_t e;
   if (bs.ntiles) {
+    if (fault_mode() == kFaultAlloc) return fail(LFBP_ERR_NOMEM, "injected failure (LFBP_FAULT=alloc)");
     if ((e = cudaMalloc(&bs.d_tiles, sizeof(TileDesc) * tiles.size())) != cudaSuccess)
       return cuda_fail(e, "cudaMalloc(tiles)");
     if ((e = cudaMemcpy(bs.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
@@ -598,6 +641,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   kp.kernelParams = args;
   if ((e = cudaGraphAddKernelNode(&bs.knode, bs.graph, nullptr, 0, &kp)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphAddKernelNode");
+  if (fault_mode() == kFaultGraph) return fail(LFBP_ERR_CUDA, "injected failure (LFBP_FAULT=graph)");
   if ((e = cudaGraphInstantiate(&bs.exec, bs.graph, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphInstantiate");
   return LFBP_OK;
@@ -674,6 +718,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     if ((e = cudaGraphExecKernelNodeSetParams(bs->exec, bs->knode, &kp)) != cudaSuccess)
       return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
   }
+  if (sync_device_fault(bs->dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
   if ((e = cudaGraphLaunch(bs->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return LFBP_OK;
 }
@@ -790,6 +835,7 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     nd->grid = std::max(1, std::min(nd->sms * tu.ctas_per_sm, nd->ntiles));
   }
   if ((rc = ensure_smem_attr((const void*)k_gather_persistent, nd->smem))) return rc;
+  if (sync_device_fault(dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
   BatchPtrs np;
   std::memset(&np, 0, sizeof(np));
   for (int i = 0; i < n; ++i) {
@@ -864,6 +910,7 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
     const int tiles[] = {12288, 16384, 24576, 32768, 40960, 49152, 65536};
     const int ctas[] = {1, 2, 3, 4};
     float best_ms = 1e30f;
+    if (sync_device_fault(dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
     cudaEvent_t a, b;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     if ((e = cudaEventCreate(&b)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -944,6 +991,7 @@ int make_plan(lfbp_plan* out, int Nx, int Ny, int Nz, const int* Ks, const int* 
               lfbp_dtype dt, lfbp_mode mode) {
   if (!out) return fail(LFBP_ERR_NULL, "out is NULL");
   *out = nullptr;
+  if (fault_mode() == kFaultPlan) return fail(LFBP_ERR_NOMEM, "injected failure (LFBP_FAULT=plan)");
   if (Nz < 0) return fail(LFBP_ERR_BAD_SHAPE, "Nz must be >= 0");
   if (Nz > 0 && (!Ks || !Kt)) return fail(LFBP_ERR_NULL, "Ks/Kt is NULL");
   if (Nx < 1 || Ny < 1 || Nx % 2 == 0 || Ny % 2 == 0)

@@ -136,3 +136,16 @@ def test_python_binding_refuses_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_injected_plan_failure(lib, monkeypatch):
+    """LFBP_FAULT=plan: plan creation fails as an allocation failure would,
+    leaves no handle, and the next call without the injection succeeds."""
+    monkeypatch.setenv("LFBP_FAULT", "plan")
+    rc, h = _plan(lib, 5, 5, [15], [15])
+    assert rc == -8 and not h.value
+    assert b"injected" in lib.lfbp_last_error()
+    monkeypatch.delenv("LFBP_FAULT")
+    rc, h = _plan(lib, 5, 5, [15], [15])
+    assert rc == 0 and h.value
+    lib.lfbp_plan_destroy(h)

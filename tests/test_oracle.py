@@ -349,3 +349,27 @@ def test_rl_step_homogeneity_and_zeros():
     H0[Nx * Ny * Ks[0] * Kt[0]:] = 0.0
     Hp0 = oracle.transpose(H0, Nx, Ny, Ks, Kt)
     assert (oracle.rl_step(H0, Hp0, Nx, Ny, Ks, Kt, g, f)[1] == 0).all()
+
+
+@pytest.mark.parametrize("Nx,Ny,K,Kt,m,mt", [(5, 3, 15, 9, 3, 1), (3, 5, 21, 25, 9, 10),
+                                              (7, 7, 9, 9, 4, 4)])
+def test_centred_cropping_commutes_with_the_map(Nx, Ny, K, Kt, m, mt):
+    """Reading A6: a centred crop of the cut-outs (m entries off each end of s,
+    mt off each end of t) taken before the map equals the same crop of H'
+    taken after it, so ragged per-depth storage loses nothing.  A centre
+    offset taken from the uncropped size, or a flip about the wrong centre,
+    breaks it (for m = (K-1)/2 the crop is the central entry alone)."""
+    H = _rand(Nx * Ny * K * Kt, 9).reshape(Nx, Ny, K, Kt)
+    crop = lambda A: A[:, :, m:K - m, mt:Kt - mt]
+    Hp = oracle.transpose(H.reshape(-1), Nx, Ny, [K], [Kt]).reshape(Nx, Ny, K, Kt)
+    Hc = np.ascontiguousarray(crop(H))
+    Hpc = oracle.transpose(Hc.reshape(-1), Nx, Ny, [K - 2 * m], [Kt - 2 * mt])
+    np.testing.assert_array_equal(Hpc.reshape(Hc.shape), crop(Hp))
+    # the ragged array of both sizes maps depth by depth
+    both = np.concatenate([H.reshape(-1), Hc.reshape(-1)])
+    Hb = oracle.transpose(both, Nx, Ny, [K, K - 2 * m], [Kt, Kt - 2 * mt])
+    np.testing.assert_array_equal(Hb[:H.size], Hp.reshape(-1))
+    np.testing.assert_array_equal(Hb[H.size:], Hpc)
+    # the central entry alone: H'[p, q, 0, 0] = H[p, q, 0, 0] for a 1 x 1 cut-out
+    c = np.ascontiguousarray(H[:, :, (K - 1) // 2:(K + 1) // 2, (Kt - 1) // 2:(Kt + 1) // 2])
+    np.testing.assert_array_equal(oracle.transpose(c.reshape(-1), Nx, Ny, [1], [1]), c.reshape(-1))
