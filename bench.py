@@ -523,9 +523,78 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                      "tuned": _tuned_desc(rtuned)}
     del rH, rO
     torch.cuda.empty_cache()
+    res["paper_window"] = _paper_window_extra(lf, specs, Hs, outs, timed, steps, world)
+    res["table1"] = _table1_extra(lf, world, args.no_tune)
     res["rl_step"] = _rl_extra(lf, timed, steps)
     res["autograd_step"] = _autograd_extra(lf, timed, steps)
     return res
+
+
+def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
+    """The headline array in the literal Eqs. (4)-(9) mode (entries the paper's
+    loop ranges leave unwritten are zero-filled), batched and plain."""
+    import torch
+    pw = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float32, mode=lf.MAP_PAPER_WINDOW) for s in specs]
+    nb = sum(2 * h.numel() * h.element_size() for h in Hs)
+    tb, _, _ = timed(lambda: lf.backproject_batched(pw, Hs, outs), steps, 3)
+    tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(pw, Hs, outs)],
+                     steps, 3)
+    return {"mode": "MAP_PAPER_WINDOW", "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
+            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
+            "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+
+
+# Table 1 of the paper: n_s = n_t, n_x, n_y and the paper's own time in seconds
+# (MATLAB 2019a on an i7-6700K, precision not stated; context only), n_z = 11.
+TABLE1 = [(89, 11, 11, 0.10), (177, 11, 11, 0.36), (287, 11, 11, 1.05), (507, 11, 11, 3.13),
+          (91, 15, 15, 0.13), (121, 15, 15, 0.23), (211, 21, 21, 1.08), (249, 31, 31, 2.85),
+          (311, 31, 31, 4.74), (307, 51, 51, 11.3), (181, 95, 55, 5.9)]
+
+
+def _table1_extra(lf, world, no_tune=False, reps=5):
+    """Every PSF-array size of Table 1 (11 depths of one K; K not a multiple of
+    N; the last row the non-square 95 x 55 cell), fp32, seeded uniform values:
+    one batched launch per array, in the launch shape the library's autotuner
+    picks for it (`tuned`; the default shape's time beside it).  Inputs of
+    0.04-10.8 GB per direction; arrays below 2 x L2 are timed with an L2 flush
+    between launches."""
+    import torch
+    nmax = max(nx * ny * k * k * 11 for k, nx, ny, _ in TABLE1)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    Hbuf = torch.empty(nmax, dtype=torch.float32, device="cuda").uniform_(generator=gen)
+    Obuf = torch.empty_like(Hbuf)
+    flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
+    rows = []
+    for k, nx, ny, paper_s in TABLE1:
+        plan = lf.Plan(nx, ny, [k] * 11, [k] * 11, torch.float32)
+        H, O = Hbuf[:plan.elems], Obuf[:plan.elems]
+        nb = 2 * plan.elems * 4
+
+        def time_it():
+            for _ in range(3):
+                lf.backproject_batched([plan], [H], [O])
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(reps)]
+            for a, b in ev:
+                if nb < 2 * 129e6:
+                    flush.zero_()  # outside the timed launch
+                a.record()
+                lf.backproject_batched([plan], [H], [O])
+                b.record()
+            torch.cuda.synchronize()
+            lf.sync_status()
+            return sum(a.elapsed_time(b) for a, b in ev) / reps
+        t_default = time_it()
+        tuned = None if no_tune else lf.tune_batched([plan], [H], [O])
+        t = time_it() if tuned else t_default
+        rows.append({"K": k, "Nx": nx, "Ny": ny, "Nz": 11, "elements": plan.elems,
+                     "ms": round(t, 4), "GBps": round(world * nb / (t * 1e-3) / 1e9, 1),
+                     "default_shape_GBps": round(world * nb / (t_default * 1e-3) / 1e9, 1),
+                     "tuned": _tuned_desc(tuned), "paper_s": paper_s})
+    del Hbuf, Obuf, flush
+    torch.cuda.empty_cache()
+    return {"dtype": "f32", "data": "seeded uniform values (a permutation's time does not "
+                                     "depend on them)", "rows": rows}
 
 
 def _autograd_extra(lf, timed, steps):

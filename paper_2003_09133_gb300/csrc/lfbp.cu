@@ -29,12 +29,6 @@ namespace lfbp {
 // written by a kernel whose bounded wait gave up.
 __device__ int g_status;
 
-// Fault injection for tests of the error paths (LFBP_FAULT=stall, host side):
-// 1 makes the persistent kernel's producers register their copies' bytes on
-// the full barrier without issuing the copies, so every consumer wait runs
-// out (a barrier phase nothing completes) and the kernel ends with
-// LFBP_ERR_TIMEOUT in g_status.  0 in normal use.
-__device__ int g_fault;
 
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per in-kernel wait
 constexpr int kPlainThreads = 256;
@@ -129,6 +123,13 @@ __global__ void __launch_bounds__(kPlainThreads)
 // copies (warp 0 also writes the stage's tile context); the other warps
 // consume.
 // smem: [nstages x stage_bytes][nstages x descriptor][full[nstages]][empty[nstages]]
+//
+// kStall (fault injection for tests of the error paths, LFBP_FAULT=stall):
+// the producers register their copies' bytes on the full barrier without
+// issuing the copies, so no barrier phase completes, every consumer wait runs
+// out and the kernel ends with LFBP_ERR_TIMEOUT in the status word.  The
+// normal instantiation is kStall = false.
+template <bool kStall>
 __global__ void __launch_bounds__(kPersistentThreads, 3)
     k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
                         const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
@@ -152,7 +153,6 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
     }
     fence_mbar_init();
   }
-  const bool stall = g_fault == 1;  // injected: register bytes, issue no copies
   __syncthreads();
 
   if (warp < kProducerWarps) {
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       const unsigned char* in_arr = ptrs.in[td.arr];
       const unsigned char* in_depth = in_arr + td.off_bytes;
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
-      if (stall) {
+      if (kStall) {
         if (lane == 0) mbar_expect_tx(fb, 16);
       } else {
         issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
     }
     // make sure no copy into this CTA's shared memory is still in flight (the
     // full barriers count the bytes of every producer warp's copies)
-    if (lane == 0 && !stall) {
+    if (lane == 0 && !kStall) {
       const int armed = it;  // stages armed: iterations 0..it-1
       for (int s = 0; s < nstages && s < armed; ++s) {
         const int last = ((armed - 1 - s) / nstages) * nstages + s;  // last iteration using s
@@ -288,22 +288,6 @@ int fault_mode() {
   if (!std::strcmp(s, "graph")) return kFaultGraph;
   if (!std::strcmp(s, "stall")) return kFaultStall;
   return kFaultNone;
-}
-
-// Keep the device's g_fault equal to the stall injection (in stream order).
-int sync_device_fault(int dev, cudaStream_t st) {
-  static std::mutex mu;
-  static std::map<int, int> current;
-  const int want = fault_mode() == kFaultStall ? 1 : 0;
-  std::lock_guard<std::mutex> lk(mu);
-  auto it = current.find(dev);
-  if ((it == current.end() && want == 0) || (it != current.end() && it->second == want)) return 0;
-  cudaError_t e = cudaMemcpyToSymbolAsync(g_fault, &want, sizeof(int), 0, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return -1;
-  e = cudaStreamSynchronize(st);  // `want` lives on this stack frame
-  if (e != cudaSuccess) return -1;
-  current[dev] = want;
-  return 0;
 }
 
 int env_int(const char* name, int dflt) {
@@ -626,7 +610,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
                         cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(tiles)");
   }
-  if ((rc = ensure_smem_attr((const void*)k_gather_persistent, bs.smem))) return rc;
+  if ((rc = ensure_smem_attr((const void*)k_gather_persistent<false>, bs.smem))) return rc;
   // a one-node graph: relaunching it costs one cudaGraphLaunch; pointer
   // changes are patched into the node's parameters
   if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
@@ -634,7 +618,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
-  kp.func = (void*)k_gather_persistent;
+  kp.func = (void*)k_gather_persistent<false>;
   kp.gridDim = dim3(bs.grid);
   kp.blockDim = dim3(kPersistentThreads);
   kp.sharedMemBytes = bs.smem;
@@ -710,7 +694,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     void* args[] = {&bs->ptrs, &bs->d_tiles, &bs->ntiles, &bs->stage_bytes, &bs->nstages};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.func = (void*)k_gather_persistent;
+    kp.func = (void*)k_gather_persistent<false>;
     kp.gridDim = dim3(bs->grid);
     kp.blockDim = dim3(kPersistentThreads);
     kp.sharedMemBytes = bs->smem;
@@ -718,7 +702,14 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     if ((e = cudaGraphExecKernelNodeSetParams(bs->exec, bs->knode, &kp)) != cudaSuccess)
       return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
   }
-  if (sync_device_fault(bs->dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
+  if (fault_mode() == kFaultStall) {  // the injected kernel, launched directly
+    int rc = ensure_smem_attr((const void*)k_gather_persistent<true>, bs->smem);
+    if (rc) return rc;
+    k_gather_persistent<true><<<bs->grid, kPersistentThreads, bs->smem, st>>>(
+        bs->ptrs, bs->d_tiles, bs->ntiles, bs->stage_bytes, bs->nstages);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
+    return LFBP_OK;
+  }
   if ((e = cudaGraphLaunch(bs->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return LFBP_OK;
 }
@@ -834,8 +825,7 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     nd->smem = persistent_smem_bytes(stage_bytes, nst);
     nd->grid = std::max(1, std::min(nd->sms * tu.ctas_per_sm, nd->ntiles));
   }
-  if ((rc = ensure_smem_attr((const void*)k_gather_persistent, nd->smem))) return rc;
-  if (sync_device_fault(dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
+  if ((rc = ensure_smem_attr((const void*)k_gather_persistent<false>, nd->smem))) return rc;
   BatchPtrs np;
   std::memset(&np, 0, sizeof(np));
   for (int i = 0; i < n; ++i) {
@@ -843,8 +833,14 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     np.out[i] = (unsigned char*)out[i];
     np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
   }
-  k_gather_persistent<<<nd->grid, kPersistentThreads, nd->smem, st>>>(np, nd->d_tiles, nd->ntiles,
-                                                                      nd->stage_bytes, nd->nstages);
+  if (fault_mode() == kFaultStall) {
+    if ((rc = ensure_smem_attr((const void*)k_gather_persistent<true>, nd->smem))) return rc;
+    k_gather_persistent<true><<<nd->grid, kPersistentThreads, nd->smem, st>>>(
+        np, nd->d_tiles, nd->ntiles, nd->stage_bytes, nd->nstages);
+  } else {
+    k_gather_persistent<false><<<nd->grid, kPersistentThreads, nd->smem, st>>>(
+        np, nd->d_tiles, nd->ntiles, nd->stage_bytes, nd->nstages);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
   return LFBP_OK;
 }
@@ -910,7 +906,6 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
     const int tiles[] = {12288, 16384, 24576, 32768, 40960, 49152, 65536};
     const int ctas[] = {1, 2, 3, 4};
     float best_ms = 1e30f;
-    if (sync_device_fault(dev, st)) return fail(LFBP_ERR_CUDA, "setting the fault flag failed");
     cudaEvent_t a, b;
     if ((e = cudaEventCreate(&a)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
     if ((e = cudaEventCreate(&b)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -931,7 +926,7 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
         const int smem = bs.smem;
         for (int r = 0; r <= reps; ++r) {
           if (r == 1) cudaEventRecord(a, st);
-          k_gather_persistent<<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.ntiles,
+          k_gather_persistent<false><<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.ntiles,
                                                                          bs.stage_bytes, bs.nstages);
         }
         cudaEventRecord(b, st);

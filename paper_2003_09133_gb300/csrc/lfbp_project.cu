@@ -174,10 +174,95 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Sub-problem cursor: depth di, input phase (rho, tau).
-struct PcCursor {
+// Sub-problem: depth di, input phase (rho, tau), with the quantities its
+// staging needs kept up to date incrementally (no division per sub-problem):
+// xoff = px + rho - c_s, yoff = py + tau - c_t, their cell positions
+// ar = xoff mod Nx, br = yoff mod Ny, and the taps of the phase,
+// Ssig = ceil((Ks - rho) / Nx) = Ks / Nx + [rho < Ks mod Nx] (rho < Nx), Sups likewise.
+struct PcSub {
   int di, rho, tau;
+  int Ks, Kt;
+  int xoff, yoff, ar, br;
+  int Ssig, Sups;
+  int qs, ms, qt, mt;  // Ks / Nx, Ks mod Nx, Kt / Ny, Kt mod Ny
 };
+
+__device__ __forceinline__ void pc_sub_depth(PcSub& c, int di, int Ks, int Kt, int px, int py,
+                                             int Nx, int Ny) {
+  c.di = di;
+  c.rho = c.tau = 0;
+  c.Ks = Ks;
+  c.Kt = Kt;
+  c.xoff = px - (Ks - 1) / 2;
+  c.yoff = py - (Kt - 1) / 2;
+  c.ar = pmod(c.xoff, Nx);
+  c.br = pmod(c.yoff, Ny);
+  c.qs = Ks / Nx;
+  c.ms = Ks - c.qs * Nx;
+  c.qt = Kt / Ny;
+  c.mt = Kt - c.qt * Ny;
+  c.Ssig = c.qs + (c.ms > 0);
+  c.Sups = c.qt + (c.mt > 0);
+}
+
+// Next (rho, tau) of the same depth; false after the last one.
+__device__ __forceinline__ bool pc_sub_next_phase(PcSub& c, int px, int py, int Nx, int Ny) {
+  if (c.tau + 1 < Ny && c.tau + 1 < c.Kt) {
+    ++c.tau;
+    ++c.yoff;
+    c.br = c.br + 1 == Ny ? 0 : c.br + 1;
+    c.Sups = c.qt + (c.tau < c.mt);
+    return true;
+  }
+  if (c.rho + 1 < Nx && c.rho + 1 < c.Ks) {
+    ++c.rho;
+    ++c.xoff;
+    c.ar = c.ar + 1 == Nx ? 0 : c.ar + 1;
+    c.Ssig = c.qs + (c.rho < c.ms);
+    c.tau = 0;
+    c.yoff = py - (c.Kt - 1) / 2;
+    c.br = pmod(c.yoff, Ny);
+    c.Sups = c.qt + (c.mt > 0);
+    return true;
+  }
+  return false;
+}
+
+// Copies of the input subgrid I(r, col) = in(Nx*(i0+r) + xoff, Ny*(j0+col) + yoff),
+// r < IR, col < ICP (zero outside the sensor / volume and for col >= IC) into
+// dst[r * ICP + col]; warp wi takes rows wi, wi+8, ..., lane the columns
+// lane + 32 k.  Row and column tests and offsets are formed once per row and
+// once per column.
+template <int IR, int IC, int ICP>
+__device__ __forceinline__ void pc_stage_input(float* dst, const float* inz, const float* dummy,
+                                               int Nx, int Ny, int Wx, int Wy, int i0, int j0,
+                                               int xoff, int yoff, int wi, int lane) {
+  constexpr int KC = (ICP + 31) / 32;
+  int yk[KC];
+  bool okc[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    yk[k] = Ny * (j0 + lane + 32 * k) + yoff;
+    okc[k] = lane + 32 * k < IC && yk[k] >= 0 && yk[k] < Wy;
+  }
+  int x = Nx * (i0 + wi) + xoff;
+#pragma unroll
+  for (int rr = 0; rr < (IR + 7) / 8; ++rr) {
+    const int r = wi + 8 * rr;
+    if (r < IR) {
+      const bool xin = x >= 0 && x < Wx;
+      const float* row = inz + (long long)(xin ? x : 0) * Wy;
+#pragma unroll
+      for (int k = 0; k < KC; ++k) {
+        if (k + 1 < KC || lane + 32 * k < ICP) {
+          const bool ok = xin && okc[k];
+          cp_async4(dst + r * ICP + lane + 32 * k, ok ? row + yk[k] : dummy, ok);
+        }
+      }
+    }
+    x += 8 * Nx;
+  }
+}
 
 // RI: output rows per thread; the block (8 warps) covers 8*RI rows x 64 columns.
 // The sub-problems (depth, rho, tau) run through a two-buffer pipeline: the
@@ -206,51 +291,39 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
   const int d_lo = a.sum_depths ? 0 : (int)blockIdx.y;
   const int d_hi = a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
 
+  static_assert(S * S4 <= kPcThreads, "one weight per thread");
   // issue the copies of sub-problem c into buffer buf (one commit group)
-  auto stage = [&](const PcCursor& c, int buf) {
-    const PcDepth dd = a.d[c.di];
-    const int Ks = dd.Ks, Kt = dd.Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
-    const float* Az = a.A + dd.off;
-    const float* inz = a.in + (long long)dd.z * a.in_zstride;
-    const int Ssig = (Ks - c.rho + Nx - 1) / Nx, Sups = (Kt - c.tau + Ny - 1) / Ny;
-    const int xoff = px + c.rho - cs, yoff = py + c.tau - ct;
-    const int ar = pmod(xoff, Nx), br = pmod(yoff, Ny);
-    for (int e = tid; e < S * S4; e += kPcThreads) {
-      const int sg = e / S4, up = e - sg * S4;
-      const bool ok = sg < Ssig && up < Sups;
+  auto stage = [&](const PcSub& c, int buf) {
+    const PcDepth& dd = a.d[c.di];
+    const int Ks = c.Ks, Kt = c.Kt;
+    if (tid < S * S4) {
+      const int sg = tid / S4, up = tid - sg * S4;
+      const bool ok = sg < c.Ssig && up < c.Sups;
       const int u = Nx * sg + c.rho, v = Ny * up + c.tau;
+      const float* Az = a.A + dd.off;
       const float* src =
           !ok ? a.A
-              : a.mapped ? Az + (((size_t)ar * Ny + br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
+              : a.mapped ? Az + (((size_t)c.ar * Ny + c.br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
                          : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
-      cp_async4(&w_s[buf][e], src, ok);
+      cp_async4(&w_s[buf][tid], src, ok);
     }
-    for (int r = wi; r < IR; r += kPcThreads / 32) {
-      const int x = Nx * (i0 + r) + xoff;
-      const bool xin = x >= 0 && x < Wx;
-      const float* row = inz + (size_t)(xin ? x : 0) * Wy;
-      for (int col = lane; col < ICP; col += 32) {
-        const int y = Ny * (j0 + col) + yoff;
-        const bool ok = xin && col < IC && y >= 0 && y < Wy;
-        cp_async4(&I_s[buf][r * ICP + col], ok ? row + y : a.in, ok);
-      }
-    }
+    pc_stage_input<IR, IC, ICP>(I_s[buf], a.in + (long long)dd.z * a.in_zstride, a.in, Nx, Ny, Wx,
+                                Wy, i0, j0, c.xoff, c.yoff, wi, lane);
     cp_async_commit();
   };
-  auto advance = [&](PcCursor& c) -> bool {  // next sub-problem; false at the end
-    const PcDepth& dd = a.d[c.di];
-    if (++c.tau < Ny && c.tau < dd.Kt) return true;
-    c.tau = 0;
-    if (++c.rho < Nx && c.rho < dd.Ks) return true;
-    c.rho = 0;
-    return ++c.di < d_hi;
+  auto advance = [&](PcSub& c) -> bool {  // next sub-problem; false at the end
+    if (pc_sub_next_phase(c, px, py, Nx, Ny)) return true;
+    if (c.di + 1 >= d_hi) return false;
+    pc_sub_depth(c, c.di + 1, a.d[c.di + 1].Ks, a.d[c.di + 1].Kt, px, py, Nx, Ny);
+    return true;
   };
 
   float acc[RH][4];
 #pragma unroll
   for (int i = 0; i < RH; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-  PcCursor cur{d_lo, 0, 0};
-  PcCursor nxt = cur;
+  PcSub cur;
+  pc_sub_depth(cur, d_lo, a.d[d_lo].Ks, a.d[d_lo].Kt, px, py, Nx, Ny);
+  PcSub nxt = cur;
   bool more = advance(nxt);
   stage(cur, 0);
   for (int k = 0;; ++k) {
@@ -442,35 +515,24 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
   const int a0 = wi * RI + (lane >> 4) * RH, b0 = 4 * (lane & 15);
   const int dbase = (int)blockIdx.y * DB;
   const int nd = min(DB, a.ndepth - dbase);
-  const int Ks = a.d[dbase].Ks, Kt = a.d[dbase].Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
-  const int nrho = min(Nx, Ks), ntau = min(Ny, Kt);
+  const int Ks = a.d[dbase].Ks, Kt = a.d[dbase].Kt;
+  static_assert(DB * S * S4 <= kPcThreads, "one weight per thread");
+  // this thread's weight slot: depth wd, tap row wsg, column wup (fixed for the block)
+  const int wd = tid / (S * S4), wsg = (tid - wd * (S * S4)) / S4, wup = tid % S4;
+  const float* wAz = a.A + (wd < nd ? a.d[dbase + wd].off : 0);
 
-  auto stage = [&](int rho, int tau, int buf) {
-    const int Ssig = (Ks - rho + Nx - 1) / Nx, Sups = (Kt - tau + Ny - 1) / Ny;
-    const int xoff = px + rho - cs, yoff = py + tau - ct;
-    const int ar = pmod(xoff, Nx), br = pmod(yoff, Ny);
-    for (int e = tid; e < DB * S * S4; e += kPcThreads) {
-      const int dd = e / (S * S4), ee = e - dd * (S * S4);
-      const int sg = ee / S4, up = ee - sg * S4;
-      const bool ok = dd < nd && sg < Ssig && up < Sups;
-      const float* Az = a.A + (ok ? a.d[dbase + dd].off : 0);
-      const int u = Nx * sg + rho, v = Ny * up + tau;
+  auto stage = [&](const PcSub& c, int buf) {
+    if (tid < DB * S * S4) {
+      const bool ok = wd < nd && wsg < c.Ssig && wup < c.Sups;
+      const int u = Nx * wsg + c.rho, v = Ny * wup + c.tau;
       const float* src =
           !ok ? a.A
-              : a.mapped ? Az + (((size_t)ar * Ny + br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
-                         : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
-      cp_async4(&w_s[buf][e], src, ok);
+              : a.mapped ? wAz + (((size_t)c.ar * Ny + c.br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
+                         : wAz + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
+      cp_async4(&w_s[buf][tid], src, ok);
     }
-    for (int r = wi; r < IR; r += kPcThreads / 32) {
-      const int x = Nx * (i0 + r) + xoff;
-      const bool xin = x >= 0 && x < Wx;
-      const float* row = a.in + (size_t)(xin ? x : 0) * Wy;
-      for (int col = lane; col < ICP; col += 32) {
-        const int y = Ny * (j0 + col) + yoff;
-        const bool ok = xin && col < IC && y >= 0 && y < Wy;
-        cp_async4(&I_s[buf][r * ICP + col], ok ? row + y : a.in, ok);
-      }
-    }
+    pc_stage_input<IR, IC, ICP>(I_s[buf], a.in, a.in, Nx, Ny, Wx, Wy, i0, j0, c.xoff, c.yoff, wi,
+                                lane);
     cp_async_commit();
   };
 
@@ -479,18 +541,15 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
   for (int d = 0; d < DB; ++d)
 #pragma unroll
     for (int i = 0; i < RH; ++i) acc[d][i][0] = acc[d][i][1] = acc[d][i][2] = acc[d][i][3] = 0.f;
-  int rho = 0, tau = 0;
-  stage(0, 0, 0);
+  PcSub cur;
+  pc_sub_depth(cur, dbase, Ks, Kt, px, py, Nx, Ny);
+  stage(cur, 0);
   for (int k = 0;; ++k) {
     const int buf = k & 1;
-    int nrho2 = rho, ntau2 = tau + 1;
-    if (ntau2 >= ntau) {
-      ntau2 = 0;
-      ++nrho2;
-    }
-    const bool more = nrho2 < nrho;
+    PcSub nxt = cur;
+    const bool more = pc_sub_next_phase(nxt, px, py, Nx, Ny);
     if (more)
-      stage(nrho2, ntau2, buf ^ 1);
+      stage(nxt, buf ^ 1);
     else
       cp_async_commit();
     cp_async_wait<1>();
@@ -526,8 +585,7 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
     }
     __syncthreads();
     if (!more) break;
-    rho = nrho2;
-    tau = ntau2;
+    cur = nxt;
   }
   cp_async_wait<0>();
 

@@ -273,3 +273,24 @@ def test_every_launch_shape_of_the_tuner_grid(lf, monkeypatch):
             lf.sync_status()
             for o, w in zip(outs, want):
                 _assert_same_bits(o, w, f"tile {tb} cps {cps}")
+
+
+# Table 1 of the paper (n_s = n_t, n_x, n_y): K not a multiple of N, rows of
+# up to 507 elements, cells of up to 95 x 55 positions
+TABLE1 = [(89, 11, 11), (177, 11, 11), (287, 11, 11), (507, 11, 11), (91, 15, 15), (121, 15, 15),
+          (211, 21, 21), (249, 31, 31), (311, 31, 31), (307, 51, 51), (181, 95, 55)]
+
+
+@pytest.mark.parametrize("K,Nx,Ny", TABLE1, ids=lambda v: str(v))
+def test_table1_shapes_full_size(lf, K, Nx, Ny):
+    """Two depths of each Table 1 size (the full per-depth size; the paper's
+    arrays repeat it 11 times), fp32 random bits, plain and batched."""
+    Ks = [K, K]
+    plan = lf.Plan(Nx, Ny, Ks, Ks, torch.float32)
+    bits = np.random.default_rng(K * 1000 + Nx).integers(0, 2 ** 32, plan.elems, dtype=np.uint32)
+    Hn = bits.view(np.float32)
+    H = torch.from_numpy(Hn).cuda()
+    want = oracle.transpose(Hn, Nx, Ny, Ks, Ks)
+    _assert_same_bits(lf.backproject_batched([plan], [H])[0], want, "batched")
+    _assert_same_bits(lf.backproject_array(plan, H), want, "plain")
+    lf.sync_status()
