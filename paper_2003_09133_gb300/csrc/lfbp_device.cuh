@@ -486,7 +486,7 @@ struct alignas(16) TileCtx {
   int nunits;      // warp steps of the tile: ceil(Ny * ngm / 4)
   uint32_t D;      // bytes between diagonal neighbours: (P - 1) * es
   uint32_t W;      // bytes of Ny slots: Ny * P * es
-  int fast;        // 1: chunk path (mode 0, ncols >= 16/es, Ny >= 16/es)
+  int fast;        // 1: chunk path (mode 0 or 1, ncols >= 16/es, Ny >= 16/es)
   FastDiv fncols, fNy, fNx, fngc, fngm;
 };
 
@@ -537,7 +537,7 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       c.s0 = td.Ks - 1 - td.u0;
       c.nrows = td.nrows;
       c.tab_s = smem_addr(tab);
-      c.fast = c.mode == 0 && td.ncols >= E && td.Ny >= E;
+      c.fast = c.mode <= 1 && td.ncols >= E && td.Ny >= E;
       break;
     case 1:
       c.fncols = make_fastdiv(td.ncols);
@@ -734,6 +734,9 @@ __device__ __forceinline__ int tab_load(const TileCtx& c, int j) {
 // chunk because Ny and ncols are at least its element count.  Chunks cut by
 // a run's ends store element by element.  `rot` rotates the step-to-warp
 // assignment from tile to tile so that the warps share the remainder steps.
+// MASK (the paper-window mode, Fig. 10's loop ranges): element k is kept
+// iff its output position has p + u in [h_x, Ks - 1 + h_x] and q + v in
+// [h_y, Kt - 1 + h_y]; the others are written as zero.
 // Stage addresses of one chunk of the chunk path: chunk element 0 is run
 // element e of run q.  A, kwA: address of element 0 and the first element that
 // wraps from segment Ny-1 to 0 (same row); B, kwB: the same for the elements
@@ -741,6 +744,7 @@ __device__ __forceinline__ int tab_load(const TileCtx& c, int j) {
 struct ChunkAddr {
   uint32_t A, B;
   int kwA, kx, kwB;
+  int j, vl;  // row and column of chunk element 0 (used by the paper-window mask)
 };
 
 template <int ES, bool ONEROW>
@@ -755,6 +759,8 @@ __device__ __forceinline__ ChunkAddr chunk_addr(const TileCtx& c, int q, int e) 
     const int b = (int)fmod2((uint32_t)(q + c.cbb + e), c.fNy);
     s.A = c.A0 + (uint32_t)b * c.PES - (uint32_t)e * ES;
     s.kwA = Ny - b;
+    s.j = 0;
+    s.vl = e;
   } else {
     const int j = e > 0 ? (int)fdiv2((uint32_t)e, c.fncols) : 0;
     const int vl = e - j * c.ncols;
@@ -768,8 +774,28 @@ __device__ __forceinline__ ChunkAddr chunk_addr(const TileCtx& c, int q, int e) 
     if (bq0 >= Ny) bq0 -= Ny;
     s.B = c.stage_s + (uint32_t)(rbn + bq0 * c.P) * ES - (uint32_t)s.kx * c.D;
     s.kwB = s.kx + Ny - bq0;
+    s.j = j;
+    s.vl = vl;
   }
   return s;
+}
+
+// Paper-window mask of chunk element k (run q): rows j (k < kx) or j + 1,
+// columns vl + k or k - kx; see gather_chunks.
+template <bool ONEROW>
+__device__ __forceinline__ bool chunk_keep(const TileCtx& c, const ChunkAddr& s, int q, int k) {
+  const bool nxt = !ONEROW && k >= s.kx;
+  const int j = nxt ? s.j + 1 : s.j;
+  const int vl = nxt ? k - s.kx : s.vl + k;
+  const int pu = c.p + c.u0 + j - ((c.Nx - 1) >> 1);
+  const int qv = q + c.v0 + vl - ((c.Ny - 1) >> 1);
+  return (unsigned)pu <= (unsigned)(c.Ks - 1) && (unsigned)qv <= (unsigned)(c.Kt - 1);
+}
+
+template <class T, bool MASK, bool ONEROW>
+__device__ __forceinline__ T masked(const TileCtx& c, const ChunkAddr& s, int q, int k, T x) {
+  if (MASK && !chunk_keep<ONEROW>(c, s, q, k)) return (T)0;
+  return x;
 }
 
 // stage address of chunk element k
@@ -786,7 +812,7 @@ __device__ __forceinline__ uint32_t chunk_elem(const TileCtx& c, const ChunkAddr
   return a;
 }
 
-template <int ES, bool ONEROW>
+template <int ES, bool ONEROW, bool MASK>
 __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarps, int lane,
                                               int rot) {
   using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
@@ -816,7 +842,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
       T v[EPL];
       static_for<0, EPL>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        v[k] = smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k));
+        v[k] = masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
       });
       store_out16(c, dst, pack16(v));
     } else {
@@ -824,7 +850,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
       for (int k = 0; k < EPL; ++k) {
         if (e + k < 0 || e + k >= L) continue;
         store_out(c, reinterpret_cast<T*>(dst) + k,
-                  smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
+                  masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k))));
       }
     }
   }
@@ -849,7 +875,8 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
 #pragma unroll
     for (int k = 0; k < EPL; ++k) {
       if (e + k < 0 || e + k >= L) continue;
-      store_out(c, reinterpret_cast<T*>(dst) + k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
+      store_out(c, reinterpret_cast<T*>(dst) + k,
+                masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k))));
     }
   }
 }
@@ -955,16 +982,30 @@ __device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nw
                                                 int rot = 0) {
   const TileCtx c = cs;  // into registers, once per tile
   if (c.fast) {
-    if (c.es == 4) {
-      if (c.nrows == 1)
-        gather_chunks<4, true>(c, w, nwarps, lane, rot);
-      else
-        gather_chunks<4, false>(c, w, nwarps, lane, rot);
+    if (c.mode == 0) {
+      if (c.es == 4) {
+        if (c.nrows == 1)
+          gather_chunks<4, true, false>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<4, false, false>(c, w, nwarps, lane, rot);
+      } else {
+        if (c.nrows == 1)
+          gather_chunks<2, true, false>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<2, false, false>(c, w, nwarps, lane, rot);
+      }
     } else {
-      if (c.nrows == 1)
-        gather_chunks<2, true>(c, w, nwarps, lane, rot);
-      else
-        gather_chunks<2, false>(c, w, nwarps, lane, rot);
+      if (c.es == 4) {
+        if (c.nrows == 1)
+          gather_chunks<4, true, true>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<4, false, true>(c, w, nwarps, lane, rot);
+      } else {
+        if (c.nrows == 1)
+          gather_chunks<2, true, true>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<2, false, true>(c, w, nwarps, lane, rot);
+      }
     }
     return;
   }
