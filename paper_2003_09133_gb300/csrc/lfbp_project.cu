@@ -233,7 +233,7 @@ __device__ __forceinline__ bool pc_sub_next_phase(PcSub& c, int px, int py, int 
 // dst[r * ICP + col]; warp wi takes rows wi, wi+8, ..., lane the columns
 // lane + 32 k.  Row and column tests and offsets are formed once per row and
 // once per column.
-template <int IR, int IC, int ICP>
+template <int IR, int IC, int ICP, int UR = (IR + 7) / 8>
 __device__ __forceinline__ void pc_stage_input(float* dst, const float* inz, const float* dummy,
                                                int Nx, int Ny, int Wx, int Wy, int i0, int j0,
                                                int xoff, int yoff, int wi, int lane) {
@@ -246,7 +246,7 @@ __device__ __forceinline__ void pc_stage_input(float* dst, const float* inz, con
     okc[k] = lane + 32 * k < IC && yk[k] >= 0 && yk[k] < Wy;
   }
   int x = Nx * (i0 + wi) + xoff;
-#pragma unroll
+#pragma unroll UR
   for (int rr = 0; rr < (IR + 7) / 8; ++rr) {
     const int r = wi + 8 * rr;
     if (r < IR) {
@@ -392,97 +392,124 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
 //   F(i, j) = f(p + Nx i, q + Ny j),  G(a, b) = dg_z(Nx a + p + rho - c_s, Ny b + q + tau - c_t),
 // the S x S outputs of one (rho, tau) are  O[sigma][upsilon] = sum_{i,j} F(i,j) G(i+sigma, j+upsilon).
 // Block: one cell (p, q) of one depth; the cell's pixels in tiles of
-// kGrI x kGrJ.  Per tile F is staged once; per (rho, tau) the G tile is
-// staged and thread (i, sigma) sums its row of products for all upsilon in
-// registers (F and G read in blocks of S columns), then the rows are reduced:
-// a shuffle tree over a warp's 32 rows, then the two warps of each sigma in
-// order (deterministic).  Tiles after the first add to the output.
+// kGrI x kGrJ.  Per tile F is staged once; the G tiles of the (rho, tau)
+// sub-problems run through a two-buffer cp.async pipeline.  Thread (i, sigma)
+// walks row i of F and row i + sigma of G in steps of four columns (16-byte
+// shared loads; a sliding window of G columns in registers) and sums its
+// row's products for all upsilon; then the rows are reduced: a shuffle tree
+// over a warp's 32 rows, then the two warps of each sigma in order
+// (deterministic).  Tiles after the first add to the output.
 constexpr int kGrI = 64, kGrJ = 64;
 
 template <int S>
+struct GradGeom {
+  static constexpr int FP = kGrJ + 4;                      // F row pitch (= 4 mod 8: no conflicts)
+  static constexpr int GR = kGrI + S - 1;                  // G tile rows
+  static constexpr int GJ = (kGrJ + S - 1 + 3) & ~3;       // G tile columns read
+  static constexpr int GP = (GJ % 8 == 4) ? GJ : GJ + 4;   // G row pitch (= 4 mod 8)
+  static constexpr int NW = 4 * ((S + 3 + 3) / 4);         // G window (columns) per step
+  static constexpr size_t smem = sizeof(float) * (kGrI * FP + 2 * GR * GP);
+};
+
+template <int S>
 __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcArgs a) {
-  constexpr int JB = (kGrJ + S - 1) / S;       // column blocks of S
-  constexpr int FJ = JB * S;                   // F tile columns (zero-padded)
-  constexpr int GR = kGrI + S - 1;             // G tile rows
-  constexpr int GJ = FJ + S - 1;               // G tile columns
-  // odd row pitches: the 32 lanes of a warp read one column of 32 rows
-  constexpr int FP = FJ | 1, GP = GJ | 1;
-  __shared__ float F_s[kGrI * FP];
-  __shared__ float G_s[GR * GP];
+  using Gm = GradGeom<S>;
+  constexpr int FP = Gm::FP, GR = Gm::GR, GJ = Gm::GJ, GP = Gm::GP, NW = Gm::NW;
+  static_assert(kGrJ - 4 + NW <= GJ, "window stays inside the staged columns");
+  extern __shared__ __align__(16) float gsm[];
+  float* F_s = gsm;
+  float* G_s = gsm + kGrI * FP;  // [2][GR * GP]
   __shared__ float part[8][S];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   const int p = blockIdx.x / Ny, q = blockIdx.x % Ny;
   const PcDepth dd = a.d[blockIdx.y];
-  const int Ks = dd.Ks, Kt = dd.Kt, cs = (Ks - 1) / 2, ct = (Kt - 1) / 2;
+  const int Ks = dd.Ks, Kt = dd.Kt;
   const float* f = a.in;
   const float* dg = a.g + (long long)dd.z * a.out_zstride;
   float* dA = a.out + dd.off + ((long long)p * Ny + q) * Ks * Kt;
   const int nI = (Wx - p + Nx - 1) / Nx, nJ = (Wy - q + Ny - 1) / Ny;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i = tid & 63, sgs = tid >> 6;
   bool first_tile = true;
   for (int i0 = 0; i0 < nI; i0 += kGrI)
     for (int j0 = 0; j0 < nJ; j0 += kGrJ) {
-      __syncthreads();
-      for (int e = tid; e < kGrI * FJ; e += 256) {
-        const int i = e / FJ, j = e - i * FJ;
-        const bool ok = i0 + i < nI && j < kGrJ && j0 + j < nJ;
-        F_s[i * FP + j] = ok ? __ldg(f + (size_t)(p + Nx * (i0 + i)) * Wy + (q + Ny * (j0 + j))) : 0.f;
-      }
-      for (int rho = 0; rho < Nx && rho < Ks; ++rho) {
-        const int Ssig = (Ks - rho + Nx - 1) / Nx;
-        for (int tau = 0; tau < Ny && tau < Kt; ++tau) {
-          const int Sups = (Kt - tau + Ny - 1) / Ny;
-          const int xo = p + rho - cs, yo = q + tau - ct;
-          __syncthreads();  // F staged / the previous G and part consumed
-          for (int e = tid; e < GR * GJ; e += 256) {
-            const int r = e / GJ, c = e - r * GJ;
-            const int x = Nx * (i0 + r) + xo, y = Ny * (j0 + c) + yo;
-            G_s[r * GP + c] =
-                (x >= 0 && x < Wx && y >= 0 && y < Wy) ? __ldg(dg + (size_t)x * Wy + y) : 0.f;
+      __syncthreads();  // the previous tile's buffers are consumed
+      pc_stage_input<kGrI, kGrJ, FP, 1>(F_s, f, f, Nx, Ny, Wx, Wy, i0, j0, p, q, warp, lane);
+      PcSub cur;
+      pc_sub_depth(cur, 0, Ks, Kt, p, q, Nx, Ny);
+      pc_stage_input<GR, GJ, GP, 1>(G_s, dg, dg, Nx, Ny, Wx, Wy, i0, j0, cur.xoff, cur.yoff, warp,
+                                    lane);
+      cp_async_commit();
+      for (int k = 0;; ++k) {
+        const int buf = k & 1;
+        PcSub nxt = cur;
+        const bool more = pc_sub_next_phase(nxt, p, q, Nx, Ny);
+        if (more)
+          pc_stage_input<GR, GJ, GP, 1>(G_s + (buf ^ 1) * (GR * GP), dg, dg, Nx, Ny, Wx, Wy, i0,
+                                        j0, nxt.xoff, nxt.yoff, warp, lane);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();  // F and this sub-problem's G have landed
+        const float* Gb = G_s + buf * (GR * GP);
+        for (int s0 = 0; s0 < S; s0 += 4) {
+          const int sg = s0 + sgs;
+          float acc[S];
+#pragma unroll
+          for (int up = 0; up < S; ++up) acc[up] = 0.f;
+          if (sg < S) {
+            const float* Fr = F_s + i * FP;
+            const float* Gr = Gb + (i + sg) * GP;
+            float w[NW];
+#pragma unroll
+            for (int c4 = 0; c4 < NW / 4; ++c4) {
+              const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * c4);
+              w[4 * c4] = g4.x;
+              w[4 * c4 + 1] = g4.y;
+              w[4 * c4 + 2] = g4.z;
+              w[4 * c4 + 3] = g4.w;
+            }
+#pragma unroll
+            for (int j4 = 0; j4 < kGrJ / 4; ++j4) {
+              const float4 f4 = *reinterpret_cast<const float4*>(Fr + 4 * j4);
+              const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int up = 0; up < S; ++up) acc[up] = fmaf(fv[c], w[c + up], acc[up]);
+              if (j4 + 1 < kGrJ / 4) {  // slide the window by four columns
+#pragma unroll
+                for (int t = 0; t < NW - 4; ++t) w[t] = w[t + 4];
+                const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * j4 + NW);
+                w[NW - 4] = g4.x;
+                w[NW - 3] = g4.y;
+                w[NW - 2] = g4.z;
+                w[NW - 1] = g4.w;
+              }
+            }
+          }
+          // rows of the warp: shuffle tree; then the two warps of each sigma
+#pragma unroll
+          for (int up = 0; up < S; ++up) {
+            float v = acc[up];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) part[warp][up] = v;
           }
           __syncthreads();
-          // thread (i, sigma): i = tid % 64 (a warp holds 32 consecutive rows), sigma = round*4 + tid/64
-          for (int s0 = 0; s0 < S; s0 += 4) {
-            const int sg = s0 + (tid >> 6), i = tid & 63;
-            float acc[S];
-#pragma unroll
-            for (int up = 0; up < S; ++up) acc[up] = 0.f;
-            if (sg < S) {
-              const float* Fr = F_s + i * FP;
-              const float* Gr = G_s + (i + sg) * GP;
-              for (int jb = 0; jb < JB; ++jb) {
-                float fv[S], gv[2 * S - 1];
-#pragma unroll
-                for (int k = 0; k < S; ++k) fv[k] = Fr[jb * S + k];
-#pragma unroll
-                for (int k = 0; k < 2 * S - 1; ++k) gv[k] = Gr[jb * S + k];
-#pragma unroll
-                for (int k = 0; k < S; ++k)
-#pragma unroll
-                  for (int up = 0; up < S; ++up) acc[up] = fmaf(fv[k], gv[k + up], acc[up]);
-              }
+          if (tid < 4 * S) {  // (sigma slot, upsilon): warps 2w and 2w+1 hold sigma s0 + w
+            const int w2 = tid / S, up = tid - w2 * S, sgo = s0 + w2;
+            if (sgo < cur.Ssig && up < cur.Sups) {
+              const float v = part[2 * w2][up] + part[2 * w2 + 1][up];
+              float* o = dA + (size_t)(Nx * sgo + cur.rho) * Kt + (Ny * up + cur.tau);
+              *o = first_tile ? v : *o + v;
             }
-            // rows of the warp: shuffle tree; then the two warps of each sigma
-#pragma unroll
-            for (int up = 0; up < S; ++up) {
-              float v = acc[up];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-              if (lane == 0) part[warp][up] = v;
-            }
-            __syncthreads();
-            if (tid < 4 * S) {  // (sigma slot, upsilon): warps 2w and 2w+1 hold sigma s0 + w
-              const int w = tid / S, up = tid - w * S, sgo = s0 + w;
-              if (sgo < Ssig && up < Sups) {
-                const float v = part[2 * w][up] + part[2 * w + 1][up];
-                float* o = dA + (size_t)(Nx * sgo + rho) * Kt + (Ny * up + tau);
-                *o = first_tile ? v : *o + v;
-              }
-            }
-            __syncthreads();
           }
+          __syncthreads();  // part and (after the last round) buffer buf are free
         }
+        if (!more) break;
+        cur = nxt;
       }
+      cp_async_wait<0>();
       first_tile = false;
     }
 }
@@ -858,6 +885,21 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   return 0;
 }
 
+namespace {
+template <int S>
+int launch_grad(const PcArgs& a, dim3 grid, cudaStream_t st) {
+  static bool attr_set = false;  // per instance; setting it twice is harmless
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_phase_grad<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GradGeom<S>::smem) != cudaSuccess)
+      return -6;
+    attr_set = true;
+  }
+  k_phase_grad<S><<<grid, 256, GradGeom<S>::smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+}  // namespace
+
 int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, const long long* off,
                       const int* Ks, const int* Kt, int Wx, int Wy, float* dA, cudaStream_t st) {
   for (int z = 0; z < Nz; ++z)
@@ -886,15 +928,17 @@ int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, c
       if (n == kPcMaxDepths || (z == Nz && n > 0)) {
         a.ndepth = n;
         const dim3 grid((unsigned)(Nx * Ny), (unsigned)n);
+        int rc = 0;
         switch (S) {
-          case 3: k_phase_grad<3><<<grid, 256, 0, st>>>(a); break;
-          case 5: k_phase_grad<5><<<grid, 256, 0, st>>>(a); break;
-          case 7: k_phase_grad<7><<<grid, 256, 0, st>>>(a); break;
-          case 9: k_phase_grad<9><<<grid, 256, 0, st>>>(a); break;
-          case 11: k_phase_grad<11><<<grid, 256, 0, st>>>(a); break;
-          case 13: k_phase_grad<13><<<grid, 256, 0, st>>>(a); break;
-          default: k_phase_grad<15><<<grid, 256, 0, st>>>(a); break;
+          case 3: rc = launch_grad<3>(a, grid, st); break;
+          case 5: rc = launch_grad<5>(a, grid, st); break;
+          case 7: rc = launch_grad<7>(a, grid, st); break;
+          case 9: rc = launch_grad<9>(a, grid, st); break;
+          case 11: rc = launch_grad<11>(a, grid, st); break;
+          case 13: rc = launch_grad<13>(a, grid, st); break;
+          default: rc = launch_grad<15>(a, grid, st); break;
         }
+        if (rc) return rc;
         if (cudaGetLastError() != cudaSuccess) return -6;
         n = 0;
       }
