@@ -1122,9 +1122,12 @@ int project(lfbp_plan p, const float* A, int mapped, const float* A_direct, int 
             const float* norm, int Wx, int Wy, int sum_depths, int epi, cudaStream_t st) {
   std::vector<long long> off(p->Nz);
   for (int z = 0; z < p->Nz; ++z) off[z] = (long long)p->off[z];
+  int* status = nullptr;
+  if (cudaGetSymbolAddress((void**)&status, g_status) != cudaSuccess)
+    return fail(LFBP_ERR_CUDA, "cudaGetSymbolAddress(status)");
   const int rc = launch_phase_projection(A, mapped, p->Nx, p->Ny, p->Nz, off.data(), p->Ks.data(),
                                          p->Kt.data(), in, in_zs, out, out_zs, g, norm, Wx, Wy,
-                                         sum_depths, epi, st);
+                                         sum_depths, epi, status, st);
   if (rc == 0) return LFBP_OK;
   if (rc != -1) return fail(LFBP_ERR_CUDA, "k_phase_conv launch failed");
   for (int z = 0; z < p->Nz; ++z) {

@@ -23,13 +23,18 @@
 //
 // Every output element is produced by exactly one thread in a fixed order:
 // results are deterministic (no atomics).
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
+#include "lfbp_device.cuh"
 #include "lfbp_project.h"
 
 namespace lfbp {
@@ -142,6 +147,8 @@ struct PcDepth {
 };
 
 struct PcArgs {
+  CUtensorMap tmap;  // phase planes of `in` (TMA path): dims {Pjp, Pi, planes}
+  int* status;       // device status word (a wait that ran out: LFBP_ERR_TIMEOUT)
   const float* A;
   const float* in;
   long long in_zstride;
@@ -185,6 +192,7 @@ struct PcSub {
   int xoff, yoff, ar, br;
   int Ssig, Sups;
   int qs, ms, qt, mt;  // Ks / Nx, Ks mod Nx, Kt / Ny, Kt mod Ny
+  int qx, qy;          // floor(xoff / Nx), floor(yoff / Ny): the subgrid's offset in its phase plane
 };
 
 __device__ __forceinline__ void pc_sub_depth(PcSub& c, int di, int Ks, int Kt, int px, int py,
@@ -197,6 +205,8 @@ __device__ __forceinline__ void pc_sub_depth(PcSub& c, int di, int Ks, int Kt, i
   c.yoff = py - (Kt - 1) / 2;
   c.ar = pmod(c.xoff, Nx);
   c.br = pmod(c.yoff, Ny);
+  c.qx = (c.xoff - c.ar) / Nx;
+  c.qy = (c.yoff - c.br) / Ny;
   c.qs = Ks / Nx;
   c.ms = Ks - c.qs * Nx;
   c.qt = Kt / Ny;
@@ -210,18 +220,25 @@ __device__ __forceinline__ bool pc_sub_next_phase(PcSub& c, int px, int py, int 
   if (c.tau + 1 < Ny && c.tau + 1 < c.Kt) {
     ++c.tau;
     ++c.yoff;
-    c.br = c.br + 1 == Ny ? 0 : c.br + 1;
+    if (++c.br == Ny) {
+      c.br = 0;
+      ++c.qy;
+    }
     c.Sups = c.qt + (c.tau < c.mt);
     return true;
   }
   if (c.rho + 1 < Nx && c.rho + 1 < c.Ks) {
     ++c.rho;
     ++c.xoff;
-    c.ar = c.ar + 1 == Nx ? 0 : c.ar + 1;
+    if (++c.ar == Nx) {
+      c.ar = 0;
+      ++c.qx;
+    }
     c.Ssig = c.qs + (c.rho < c.ms);
     c.tau = 0;
     c.yoff = py - (c.Kt - 1) / 2;
     c.br = pmod(c.yoff, Ny);
+    c.qy = (c.yoff - c.br) / Ny;
     c.Sups = c.qt + (c.mt > 0);
     return true;
   }
@@ -264,19 +281,120 @@ __device__ __forceinline__ void pc_stage_input(float* dst, const float* inz, con
   }
 }
 
+// ------------------------------------------------------------ TMA staging --
+// On the TMA path a projection's input is first laid out by phase (planes,
+// k_phase_planes below): plane (z, rx, ry) holds in_z(Nx*i + rx, Ny*j + ry)
+// at [i][j], zero outside the sensor / volume.  A sub-problem's subgrid
+// I(r, col) = in(Nx*(i0+r) + xoff, Ny*(j0+col) + yoff) is then the box of
+// plane (z, xoff mod Nx, yoff mod Ny) at rows i0 + floor(xoff/Nx) + r and
+// columns j0 + floor(yoff/Ny) + col, moved by one TMA tensor copy; rows and
+// columns outside the plane arrive as zeros.  The box starts at the
+// 16-byte-aligned column below, REM = floor(yoff/Ny) mod 4 columns early, and
+// the compute reads from column REM on.
+constexpr uint64_t kPcWaitNs = 2000000000ull;  // 2 s per in-kernel wait
+
+template <int S>
+struct PcBox {
+  // a lane's 16-byte reads start at b0 <= 60 and cover REM + S + 3 <= S + 6 columns
+  static constexpr int BX = (kPcTJ + S + 5 + 3) & ~3;
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+// Thread 0: the TMA copy of sub-problem c's subgrid (plane z0 + (ar, br)) into
+// `dst`, completing on `bar` (one arrival plus the box's bytes).
+__device__ __forceinline__ void pc_tma_stage(const PcArgs& a, const PcSub& c, int zplane0,
+                                             float* dst, uint64_t* bar, int i0, int j0,
+                                             uint32_t bytes) {
+  fence_proxy_async_smem();  // the buffer's previous (generic) reads come first
+  const uint32_t b = smem_addr(bar);
+  mbar_expect_tx(b, bytes);
+  tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+              (zplane0 + c.ar) * a.Ny + c.br, b);
+  mbar_arrive(b);
+}
+
+// Products of one staged sub-problem: rows r of the subgrid tile (pitch PITCH,
+// data from column REM on) against the S x S sub-kernel, into acc.
+template <int S, int RH, int REM, int PITCH, int NACC>
+__device__ __forceinline__ void pc_products(const float* Ib, const float* const* wbs, int a0, int b0,
+                                            float (&acc)[NACC][RH][4]) {
+  constexpr int S4 = (S + 3) & ~3;
+  constexpr int NC4 = (REM + S + 3 + 3) / 4;
+#pragma unroll
+  for (int r = 0; r < RH + S - 1; ++r) {
+    float xv[4 * NC4];
+    const float* src = Ib + (a0 + r) * PITCH + b0;
+#pragma unroll
+    for (int c4 = 0; c4 < NC4; ++c4) {
+      const float4 p = *reinterpret_cast<const float4*>(src + 4 * c4);
+      xv[4 * c4] = p.x;
+      xv[4 * c4 + 1] = p.y;
+      xv[4 * c4 + 2] = p.z;
+      xv[4 * c4 + 3] = p.w;
+    }
+#pragma unroll
+    for (int d = 0; d < NACC; ++d) {
+      const float* wb = wbs[d];
+#pragma unroll
+      for (int sg = 0; sg < S; ++sg) {
+        const int ai = r - sg;
+        if (ai < 0 || ai >= RH) continue;
+#pragma unroll
+        for (int up = 0; up < S; ++up) {
+          const float wv = wb[sg * S4 + up];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[d][ai][c] = fmaf(xv[REM + up + c], wv, acc[d][ai][c]);
+        }
+      }
+    }
+  }
+}
+
+template <int S, int RH, int PITCH, int NACC>
+__device__ __forceinline__ void pc_products_rem(int rem, const float* Ib, const float* const* wbs,
+                                                int a0, int b0, float (&acc)[NACC][RH][4]) {
+  switch (rem) {
+    case 0: pc_products<S, RH, 0, PITCH, NACC>(Ib, wbs, a0, b0, acc); break;
+    case 1: pc_products<S, RH, 1, PITCH, NACC>(Ib, wbs, a0, b0, acc); break;
+    case 2: pc_products<S, RH, 2, PITCH, NACC>(Ib, wbs, a0, b0, acc); break;
+    default: pc_products<S, RH, 3, PITCH, NACC>(Ib, wbs, a0, b0, acc); break;
+  }
+}
+
+// A wait that ran out: record it, let this thread's copies land, and tell the
+// caller to return (every thread of the block takes the same branch).
+__device__ __forceinline__ bool pc_abort(const PcArgs& a, bool timed_out) {
+  if (!__syncthreads_or(timed_out)) return false;
+  if (threadIdx.x == 0 && a.status) atomicCAS(a.status, 0, kStatusTimeout);
+  cp_async_wait<0>();
+  return true;
+}
+
 // RI: output rows per thread; the block (8 warps) covers 8*RI rows x 64 columns.
 // The sub-problems (depth, rho, tau) run through a two-buffer pipeline: the
 // copies of the next one are in flight while the current one is computed.
-template <int S, int RI>
+// kTma: the input subgrid arrives by one TMA tensor copy from the phase planes
+// (a.tmap); otherwise by the 4-byte cp.async staging above.
+template <int S, int RI, bool kTma>
 __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant__ PcArgs a) {
   constexpr int TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;   // weight row pitch
   constexpr int IR = TI + S - 1;     // subgrid rows
   constexpr int RH = RI / 2;         // output rows per thread (half a warp per row group)
   constexpr int IC = kPcTJ + S + 3;  // subgrid columns (lane cols 4l .. 4l+S+2, read in fours)
-  constexpr int ICP = (IC + 3) & ~3; // 16-byte aligned rows
+  constexpr int ICP = kTma ? PcBox<S>::BX : (IC + 3) & ~3;  // 16-byte aligned rows
+  constexpr int IB = (IR * ICP + 31) & ~31;  // buffer stride: 128-byte aligned TMA destinations
   __shared__ __align__(16) float w_s[2][S * S4];
-  __shared__ __align__(16) float I_s[2][IR * ICP];
+  __shared__ __align__(128) float I_s[2][IB];
+  __shared__ __align__(8) uint64_t full[2];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   int t = blockIdx.x;
   const int tj = t % a.nTJ;
@@ -290,6 +408,14 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
   const int a0 = wi * RI + (lane >> 4) * RH, b0 = 4 * (lane & 15);
   const int d_lo = a.sum_depths ? 0 : (int)blockIdx.y;
   const int d_hi = a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
+  if (kTma) {
+    if (tid == 0) {
+      mbar_init(smem_addr(&full[0]), 1);
+      mbar_init(smem_addr(&full[1]), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
 
   static_assert(S * S4 <= kPcThreads, "one weight per thread");
   // issue the copies of sub-problem c into buffer buf (one commit group)
@@ -307,8 +433,14 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
                          : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
       cp_async4(&w_s[buf][tid], src, ok);
     }
-    pc_stage_input<IR, IC, ICP>(I_s[buf], a.in + (long long)dd.z * a.in_zstride, a.in, Nx, Ny, Wx,
-                                Wy, i0, j0, c.xoff, c.yoff, wi, lane);
+    if (kTma) {
+      if (tid == 0)
+        pc_tma_stage(a, c, (a.in_zstride ? dd.z : 0) * Nx, I_s[buf], &full[buf], i0, j0,
+                     (uint32_t)(IR * ICP * sizeof(float)));
+    } else {
+      pc_stage_input<IR, IC, ICP>(I_s[buf], a.in + (long long)dd.z * a.in_zstride, a.in, Nx, Ny,
+                                  Wx, Wy, i0, j0, c.xoff, c.yoff, wi, lane);
+    }
     cp_async_commit();
   };
   auto advance = [&](PcSub& c) -> bool {  // next sub-problem; false at the end
@@ -318,9 +450,9 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
     return true;
   };
 
-  float acc[RH][4];
+  float acc[1][RH][4];
 #pragma unroll
-  for (int i = 0; i < RH; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+  for (int i = 0; i < RH; ++i) acc[0][i][0] = acc[0][i][1] = acc[0][i][2] = acc[0][i][3] = 0.f;
   PcSub cur;
   pc_sub_depth(cur, d_lo, a.d[d_lo].Ks, a.d[d_lo].Kt, px, py, Nx, Ny);
   PcSub nxt = cur;
@@ -332,34 +464,24 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
       stage(nxt, buf ^ 1);
     else
       cp_async_commit();  // keep the group count uniform
-    cp_async_wait<1>();   // the current buffer has landed (this thread's copies)
-    __syncthreads();      // ... and everybody's
-    const float* Ib = I_s[buf];
-    const float* wb = w_s[buf];
-#pragma unroll
-    for (int r = 0; r < RH + S - 1; ++r) {
-      float xv[4 * ((S + 6) / 4)];
-      const float* src = Ib + (a0 + r) * ICP + b0;
-#pragma unroll
-      for (int c4 = 0; c4 < (S + 6) / 4; ++c4) {
-        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c4);
-        xv[4 * c4] = p.x;
-        xv[4 * c4 + 1] = p.y;
-        xv[4 * c4 + 2] = p.z;
-        xv[4 * c4 + 3] = p.w;
+    cp_async_wait<1>();   // the current buffer's weights have landed (this thread's copies)
+    if (kTma) {
+      const bool ok = mbar_wait_bounded(smem_addr(&full[buf]), (uint32_t)((k >> 1) & 1), nullptr,
+                                        kPcWaitNs);
+      if (pc_abort(a, !ok)) {
+        if (tid == 0 && more)  // the copy into the other buffer
+          mbar_wait_bounded(smem_addr(&full[buf ^ 1]), (uint32_t)(((k + 1) >> 1) & 1), nullptr,
+                            kPcWaitNs);
+        return;
       }
-#pragma unroll
-      for (int sg = 0; sg < S; ++sg) {
-        const int ai = r - sg;
-        if (ai < 0 || ai >= RH) continue;
-#pragma unroll
-        for (int up = 0; up < S; ++up) {
-          const float wv = wb[sg * S4 + up];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[ai][c] = fmaf(xv[up + c], wv, acc[ai][c]);
-        }
-      }
+    } else {
+      __syncthreads();  // ... and everybody's
     }
+    const float* wbs[1] = {w_s[buf]};
+    if (kTma)
+      pc_products_rem<S, RH, ICP, 1>(cur.qy & 3, I_s[buf], wbs, a0, b0, acc);
+    else
+      pc_products<S, RH, 0, ICP, 1>(I_s[buf], wbs, a0, b0, acc);
     __syncthreads();  // buffer buf is free for the copies issued next round
     if (!more) break;
     cur = nxt;
@@ -376,12 +498,12 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
       if (X >= Wx || Y >= Wy) continue;
       const long long o = zo + (long long)X * Wy + Y;
       if (a.epi == kEpiStore) {
-        a.out[o] = acc[i][c];
+        a.out[o] = acc[0][i][c];
       } else if (a.epi == kEpiAccumulate) {
-        a.out[o] += acc[i][c];
+        a.out[o] += acc[0][i][c];
       } else {
         const float n = a.norm[o];
-        a.out[o] = n != 0.f ? (a.g[o] / n) * acc[i][c] : 0.f;
+        a.out[o] = n != 0.f ? (a.g[o] / n) * acc[0][i][c] : 0.f;
       }
     }
 }
@@ -519,16 +641,18 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
 // the DB depths' weights, so staging is paid once per DB depths.  Block: one
 // output phase, a 32 x 64 output tile, depths d[blockIdx.y*DB .. +DB) (missing
 // depths at the end get zero weights and no output).
-template <int S, int DB>
+template <int S, int DB, bool kTma>
 __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_constant__ PcArgs a) {
   constexpr int RI = 4, TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;
   constexpr int IR = TI + S - 1;
   constexpr int RH = RI / 2;
   constexpr int IC = kPcTJ + S + 3;
-  constexpr int ICP = (IC + 3) & ~3;
+  constexpr int ICP = kTma ? PcBox<S>::BX : (IC + 3) & ~3;
+  constexpr int IB = (IR * ICP + 31) & ~31;  // buffer stride: 128-byte aligned TMA destinations
   __shared__ __align__(16) float w_s[2][DB * S * S4];
-  __shared__ __align__(16) float I_s[2][IR * ICP];
+  __shared__ __align__(128) float I_s[2][IB];
+  __shared__ __align__(8) uint64_t full[2];
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   int t = blockIdx.x;
   const int tj = t % a.nTJ;
@@ -547,6 +671,14 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
   // this thread's weight slot: depth wd, tap row wsg, column wup (fixed for the block)
   const int wd = tid / (S * S4), wsg = (tid - wd * (S * S4)) / S4, wup = tid % S4;
   const float* wAz = a.A + (wd < nd ? a.d[dbase + wd].off : 0);
+  if (kTma) {
+    if (tid == 0) {
+      mbar_init(smem_addr(&full[0]), 1);
+      mbar_init(smem_addr(&full[1]), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
 
   auto stage = [&](const PcSub& c, int buf) {
     if (tid < DB * S * S4) {
@@ -558,8 +690,13 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
                          : wAz + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
       cp_async4(&w_s[buf][tid], src, ok);
     }
-    pc_stage_input<IR, IC, ICP>(I_s[buf], a.in, a.in, Nx, Ny, Wx, Wy, i0, j0, c.xoff, c.yoff, wi,
-                                lane);
+    if (kTma) {
+      if (tid == 0)
+        pc_tma_stage(a, c, 0, I_s[buf], &full[buf], i0, j0, (uint32_t)(IR * ICP * sizeof(float)));
+    } else {
+      pc_stage_input<IR, IC, ICP>(I_s[buf], a.in, a.in, Nx, Ny, Wx, Wy, i0, j0, c.xoff, c.yoff,
+                                  wi, lane);
+    }
     cp_async_commit();
   };
 
@@ -580,36 +717,25 @@ __global__ void __launch_bounds__(kPcThreads, 2) k_phase_conv_md(const __grid_co
     else
       cp_async_commit();
     cp_async_wait<1>();
-    __syncthreads();
-    const float* Ib = I_s[buf];
-#pragma unroll
-    for (int r = 0; r < RH + S - 1; ++r) {
-      float xv[4 * ((S + 6) / 4)];
-      const float* src = Ib + (a0 + r) * ICP + b0;
-#pragma unroll
-      for (int c4 = 0; c4 < (S + 6) / 4; ++c4) {
-        const float4 p = *reinterpret_cast<const float4*>(src + 4 * c4);
-        xv[4 * c4] = p.x;
-        xv[4 * c4 + 1] = p.y;
-        xv[4 * c4 + 2] = p.z;
-        xv[4 * c4 + 3] = p.w;
+    if (kTma) {
+      const bool ok = mbar_wait_bounded(smem_addr(&full[buf]), (uint32_t)((k >> 1) & 1), nullptr,
+                                        kPcWaitNs);
+      if (pc_abort(a, !ok)) {
+        if (tid == 0 && more)
+          mbar_wait_bounded(smem_addr(&full[buf ^ 1]), (uint32_t)(((k + 1) >> 1) & 1), nullptr,
+                            kPcWaitNs);
+        return;
       }
-#pragma unroll
-      for (int d = 0; d < DB; ++d) {
-        const float* wb = w_s[buf] + d * (S * S4);
-#pragma unroll
-        for (int sg = 0; sg < S; ++sg) {
-          const int ai = r - sg;
-          if (ai < 0 || ai >= RH) continue;
-#pragma unroll
-          for (int up = 0; up < S; ++up) {
-            const float wv = wb[sg * S4 + up];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[d][ai][c] = fmaf(xv[up + c], wv, acc[d][ai][c]);
-          }
-        }
-      }
+    } else {
+      __syncthreads();
     }
+    const float* wbs[DB];
+#pragma unroll
+    for (int d = 0; d < DB; ++d) wbs[d] = w_s[buf] + d * (S * S4);
+    if (kTma)
+      pc_products_rem<S, RH, ICP, DB>(cur.qy & 3, I_s[buf], wbs, a0, b0, acc);
+    else
+      pc_products<S, RH, 0, ICP, DB>(I_s[buf], wbs, a0, b0, acc);
     __syncthreads();
     if (!more) break;
     cur = nxt;
@@ -761,40 +887,176 @@ int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, con
 namespace {
 constexpr int kPcSizes[] = {3, 5, 7, 9, 11, 13, 15};  // kernel instances (sub-kernel extent S)
 
-template <int S>
-int launch_pc(const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
-  // depth sums run one block per output tile: half-height tiles for more blocks
-  if (a.sum_depths)
-    k_phase_conv<S, 2><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
-  else
-    k_phase_conv<S, 4><<<dim3((unsigned)nblocks, (unsigned)ny), kPcThreads, 0, st>>>(a);
+constexpr int kPcTmaMaxS = 9;  // TMA path instances: S <= 9 (larger cut-outs are rare)
+
+// Phase planes of the TMA path (see TMA staging above): block = one plane row
+// (z, rx, ry, i); threads along j.  Writes are coalesced; the reads, Ny apart,
+// come from L2.
+__global__ void k_phase_planes(const float* __restrict__ in, long long in_zstride, int Nx, int Ny,
+                               int Wx, int Wy, int Pi, int Pjp, float* __restrict__ planes) {
+  int t = blockIdx.x;
+  const int i = t % Pi;
+  t /= Pi;
+  const int ry = t % Ny;
+  t /= Ny;
+  const int rx = t % Nx;
+  const int z = t / Nx;
+  const int x = Nx * i + rx;
+  const float* row = in + (long long)z * in_zstride + (long long)(x < Wx ? x : 0) * Wy;
+  float* out = planes + (long long)blockIdx.x * Pjp;
+  for (int j = threadIdx.x; j < Pjp; j += blockDim.x) {
+    const int y = Ny * j + ry;
+    out[j] = (x < Wx && y < Wy) ? __ldg(row + y) : 0.f;
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The library's own stream-ordered memory pool on the current device (memory
+// is kept across calls: release threshold at the maximum), so that the
+// scratch planes of a call cost no device-wide synchronisation and leave the
+// application's pools alone.
+cudaMemPool_t scratch_pool() {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+  uint64_t keep = ~0ull;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  pools[dev] = pool;
+  return pool;
+}
+
+// Phase planes of one projection input on the stream (stream-ordered
+// allocation; release with planes_release).
+struct Planes {
+  float* ptr = nullptr;
+  int Pi = 0, Pjp = 0, nplanes = 0;
+};
+
+bool tma_enabled() {
+  const char* s = std::getenv("LFBP_PROJ_TMA");
+  return !(s && s[0] == '0') && encode_tiled() != nullptr;
+}
+
+int planes_build(Planes& pl, const float* in, long long in_zstride, int nz, int Nx, int Ny, int Wx,
+                 int Wy, cudaStream_t st) {
+  pl.Pi = (Wx + Nx - 1) / Nx;
+  pl.Pjp = (((Wy + Ny - 1) / Ny) + 3) & ~3;
+  const long long rows = (long long)nz * Nx * Ny * pl.Pi;
+  if (rows > 0x7fffffffLL || (long long)nz * Nx * Ny > 0x7fffffffLL) return -1;
+  pl.nplanes = nz * Nx * Ny;
+  cudaMemPool_t pool = scratch_pool();
+  if (!pool || cudaMallocFromPoolAsync((void**)&pl.ptr, (size_t)rows * pl.Pjp * sizeof(float), pool,
+                                       st) != cudaSuccess) {
+    pl.ptr = nullptr;
+    return -1;
+  }
+  k_phase_planes<<<(unsigned)rows, 128, 0, st>>>(in, in_zstride, Nx, Ny, Wx, Wy, pl.Pi, pl.Pjp,
+                                                 pl.ptr);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
-int launch_pc_size(int S, const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
+void planes_release(Planes& pl, cudaStream_t st) {
+  if (pl.ptr) cudaFreeAsync(pl.ptr, st);
+  pl.ptr = nullptr;
+}
+
+// Tensor map over the planes with a box of BX columns x IR rows x 1 plane.
+int planes_map(const Planes& pl, int BX, int IR, CUtensorMap* map) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn) return -1;
+  const cuuint64_t dims[3] = {(cuuint64_t)pl.Pjp, (cuuint64_t)pl.Pi, (cuuint64_t)pl.nplanes};
+  const cuuint64_t strides[2] = {(cuuint64_t)pl.Pjp * sizeof(float),
+                                 (cuuint64_t)pl.Pjp * pl.Pi * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)IR, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, pl.ptr, dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS
+             ? 0
+             : -1;
+}
+
+template <int S, int RI>
+int launch_pc_ri(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+  const dim3 grid((unsigned)nblocks, (unsigned)ny);
+  if (S <= kPcTmaMaxS && pl) {
+    if (planes_map(*pl, PcBox<S>::BX, 8 * RI + S - 1, &a.tmap)) return -6;
+    k_phase_conv<S, RI, (S <= kPcTmaMaxS)><<<grid, kPcThreads, 0, st>>>(a);
+  } else {
+    k_phase_conv<S, RI, false><<<grid, kPcThreads, 0, st>>>(a);
+  }
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
+template <int S>
+int launch_pc(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+  // depth sums run one block per output tile: half-height tiles for more blocks
+  return a.sum_depths ? launch_pc_ri<S, 2>(a, pl, nblocks, ny, st)
+                      : launch_pc_ri<S, 4>(a, pl, nblocks, ny, st);
+}
+
+int launch_pc_size(int S, PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
   switch (S) {
-    case 3: return launch_pc<3>(a, nblocks, ny, st);
-    case 5: return launch_pc<5>(a, nblocks, ny, st);
-    case 7: return launch_pc<7>(a, nblocks, ny, st);
-    case 9: return launch_pc<9>(a, nblocks, ny, st);
-    case 11: return launch_pc<11>(a, nblocks, ny, st);
-    case 13: return launch_pc<13>(a, nblocks, ny, st);
-    default: return launch_pc<15>(a, nblocks, ny, st);
+    case 3: return launch_pc<3>(a, pl, nblocks, ny, st);
+    case 5: return launch_pc<5>(a, pl, nblocks, ny, st);
+    case 7: return launch_pc<7>(a, pl, nblocks, ny, st);
+    case 9: return launch_pc<9>(a, pl, nblocks, ny, st);
+    case 11: return launch_pc<11>(a, pl, nblocks, ny, st);
+    case 13: return launch_pc<13>(a, pl, nblocks, ny, st);
+    default: return launch_pc<15>(a, pl, nblocks, ny, st);
   }
 }
-}  // namespace
 
 constexpr int kPcDB = 4;  // depths per block of k_phase_conv_md
 
-int launch_pc_md(int S, const PcArgs& a, int nblocks, int ny, cudaStream_t st) {
-  const dim3 grid((unsigned)nblocks, (unsigned)ny);
-  switch (S) {  // small cut-outs only: there staging dominates one depth's work
-    case 3: k_phase_conv_md<3, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
-    case 5: k_phase_conv_md<5, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
-    default: k_phase_conv_md<7, kPcDB><<<grid, kPcThreads, 0, st>>>(a); break;
+template <int S>
+int launch_md(PcArgs& a, const Planes* pl, dim3 grid, cudaStream_t st) {
+  if (pl) {
+    if (planes_map(*pl, PcBox<S>::BX, 32 + S - 1, &a.tmap)) return -6;
+    k_phase_conv_md<S, kPcDB, true><<<grid, kPcThreads, 0, st>>>(a);
+  } else {
+    k_phase_conv_md<S, kPcDB, false><<<grid, kPcThreads, 0, st>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
+
+int launch_pc_md(int S, PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+  const dim3 grid((unsigned)nblocks, (unsigned)ny);
+  switch (S) {  // small cut-outs only: there staging dominates one depth's work
+    case 3: return launch_md<3>(a, pl, grid, st);
+    case 5: return launch_md<5>(a, pl, grid, st);
+    default: return launch_md<7>(a, pl, grid, st);
+  }
+}
+}  // namespace
 
 int phase_conv_size(int Nx, int Ny, int Ks, int Kt) {
   const int s = std::max((Ks + Nx - 1) / Nx, (Kt + Ny - 1) / Ny);
@@ -807,12 +1069,34 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
                             const long long* off, const int* Ks, const int* Kt, const float* in,
                             long long in_zstride, float* out, long long out_zstride,
                             const float* g, const float* norm, int Wx, int Wy, int sum_depths,
-                            int epi, cudaStream_t st) {
-  for (int z = 0; z < Nz; ++z)
-    if (!phase_conv_size(Nx, Ny, Ks[z], Kt[z])) return -1;
+                            int epi, int* status, cudaStream_t st) {
+  bool any_tma = false;
+  for (int z = 0; z < Nz; ++z) {
+    const int S = phase_conv_size(Nx, Ny, Ks[z], Kt[z]);
+    if (!S) return -1;
+    any_tma |= S <= kPcTmaMaxS;
+  }
   const int nI = (Wx + Nx - 1) / Nx, nJ = (Wy + Ny - 1) / Ny;
+  // the input by phase for the TMA path (released, stream-ordered, on return)
+  struct PlanesGuard {
+    Planes pl;
+    bool on = false;
+    cudaStream_t st;
+    ~PlanesGuard() {
+      if (on) planes_release(pl, st);
+    }
+  } pg;
+  pg.st = st;
+  if (any_tma && Nz > 0 && tma_enabled()) {
+    if (planes_build(pg.pl, in, in_zstride, in_zstride ? Nz : 1, Nx, Ny, Wx, Wy, st) == 0)
+      pg.on = true;
+    else if (pg.pl.ptr)
+      return -6;  // allocated but the relayout launch failed
+  }
+  const Planes* pl = pg.on ? &pg.pl : nullptr;
   PcArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.status = status;
   a.A = A;
   a.in = in;
   a.in_zstride = in_zstride;
@@ -854,7 +1138,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         }
         a.ndepth = n;
         a.epi = epi;
-        const int rc = launch_pc_md(S, a, (int)nblocks, (n + kPcDB - 1) / kPcDB, st);
+        const int rc = launch_pc_md(S, a, pl, (int)nblocks, (n + kPcDB - 1) / kPcDB, st);
         if (rc) return rc;
       }
     }
@@ -875,7 +1159,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         a.ndepth = n;
         // summed depths: the first launch stores (or applies epi), later ones add
         a.epi = sum_depths ? (first ? epi : kEpiAccumulate) : epi;
-        const int rc = launch_pc_size(S, a, (int)nblocks, sum_depths ? 1 : n, st);
+        const int rc = launch_pc_size(S, a, pl, (int)nblocks, sum_depths ? 1 : n, st);
         if (rc) return rc;
         first = false;
         n = 0;

@@ -30,11 +30,15 @@ int launch_backproject_grad(const float* f, const float* dg, int Nx, int Ny, int
 // per-depth outputs at out + z*out_zstride, or, with sum_depths, one output
 // summed over depths in order.  Returns -1 (nothing launched) when a depth's
 // cut-out exceeds 15 cells per axis; the caller then uses launch_projector.
+// `status`: the device status word, where a kernel whose bounded wait ran out
+// records LFBP_ERR_TIMEOUT.  Cut-outs of up to 9 cells per axis take the TMA
+// path (the input laid out by phase in a stream-ordered scratch buffer, one
+// tensor copy per sub-problem) unless LFBP_PROJ_TMA=0.
 int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
                             const long long* off, const int* Ks, const int* Kt, const float* in,
                             long long in_zstride, float* out, long long out_zstride,
                             const float* g, const float* norm, int Wx, int Wy, int sum_depths,
-                            int epi, cudaStream_t st);
+                            int epi, int* status, cudaStream_t st);
 // dA_z[p][q][u][v] = sum over pixels S of cell (p, q) of f[S] * dg_z[S + (u-c_s, v-c_t)]
 // for every depth (dA_z at dA + off[z], dg_z at dg + z*Wx*Wy); -1 (nothing
 // launched) when a cut-out exceeds 15 cells per axis (use launch_backproject_grad).
