@@ -967,8 +967,10 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
   return LFBP_OK;
 }
 
+// `a`: the plan-sized array (H or H'), or with a_bytes > 0 an input of that
+// many bytes; `out`: the output, out_bytes long.
 int check_projector(lfbp_plan p, const void* a, const void* b, const void* out, int Wx, int Wy,
-                    size_t out_bytes) {
+                    size_t out_bytes, size_t a_bytes = 0) {
   if (!p) return fail(LFBP_ERR_NULL, "plan is NULL");
   if (p->dt != LFBP_F32) return fail(LFBP_ERR_DTYPE, "projectors need an LFBP_F32 plan");
   if (Wx < 1 || Wy < 1) return fail(LFBP_ERR_BAD_SHAPE, "sensor must be at least 1 x 1");
@@ -977,7 +979,7 @@ int check_projector(lfbp_plan p, const void* a, const void* b, const void* out, 
   if ((p->Nz > 0 && !a) || !b || !out) return fail(LFBP_ERR_NULL, "buffer pointer is NULL");
   if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)out) & 3)
     return fail(LFBP_ERR_ALIGN, "buffers must be 4-byte aligned");
-  const size_t sa = p->off.back() * 4;
+  const size_t sa = a_bytes ? a_bytes : p->off.back() * 4;
   if (a && overlaps(a, sa, out, out_bytes)) return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   return LFBP_OK;
 }
@@ -1174,15 +1176,20 @@ int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, i
 
 int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
                                  void* dHp_grad, void* cuda_stream) {
-  int rc = check_projector(p, dgrad, df, dHp_grad, Wx, Wy, p ? p->off.back() * 4 : 0);
+  // dgrad is the Nz x Wx x Wy gradient volume, not a plan-sized array
+  int rc = check_projector(p, dgrad, df, dHp_grad, Wx, Wy, p ? p->off.back() * 4 : 0,
+                           (size_t)(p ? p->Nz : 0) * Wx * Wy * 4);
   if (rc) return rc;
   if (overlaps(df, (size_t)Wx * Wy * 4, dHp_grad, p->off.back() * 4))
     return fail(LFBP_ERR_ALIAS, "output overlaps an input");
   float* out = (float*)dHp_grad;
   std::vector<long long> off(p->Nz);
   for (int z = 0; z < p->Nz; ++z) off[z] = (long long)p->off[z];
+  int* status = nullptr;
+  if (cudaGetSymbolAddress((void**)&status, g_status) != cudaSuccess)
+    return fail(LFBP_ERR_CUDA, "cudaGetSymbolAddress(status)");
   const int prc = launch_phase_grad(df, dgrad, p->Nx, p->Ny, p->Nz, off.data(), p->Ks.data(),
-                                    p->Kt.data(), Wx, Wy, out, (cudaStream_t)cuda_stream);
+                                    p->Kt.data(), Wx, Wy, out, status, (cudaStream_t)cuda_stream);
   if (prc == 0) return LFBP_OK;
   if (prc != -1) return fail(LFBP_ERR_CUDA, "k_phase_grad launch failed");
   for (int z = 0; z < p->Nz; ++z) {

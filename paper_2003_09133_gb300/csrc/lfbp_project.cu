@@ -147,7 +147,8 @@ struct PcDepth {
 };
 
 struct PcArgs {
-  CUtensorMap tmap;  // phase planes of `in` (TMA path): dims {Pjp, Pi, planes}
+  CUtensorMap tmap;   // phase planes of `in` (TMA path): dims {Pjp, Pi, planes}
+  CUtensorMap tmap2;  // phase planes of `g` (the gradient's dL/dg, TMA path)
   int* status;       // device status word (a wait that ran out: LFBP_ERR_TIMEOUT)
   const float* A;
   const float* in;
@@ -523,25 +524,68 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
 // (deterministic).  Tiles after the first add to the output.
 constexpr int kGrI = 64, kGrJ = 64;
 
-template <int S>
+template <int S, bool kTma>
 struct GradGeom {
   static constexpr int FP = kGrJ + 4;                      // F row pitch (= 4 mod 8: no conflicts)
   static constexpr int GR = kGrI + S - 1;                  // G tile rows
-  static constexpr int GJ = (kGrJ + S - 1 + 3) & ~3;       // G tile columns read
-  static constexpr int GP = (GJ % 8 == 4) ? GJ : GJ + 4;   // G row pitch (= 4 mod 8)
-  static constexpr int NW = 4 * ((S + 3 + 3) / 4);         // G window (columns) per step
-  static constexpr size_t smem = sizeof(float) * (kGrI * FP + 2 * GR * GP);
+  // cp.async path: columns 0 .. GJ-1 from column 0; TMA path: the box starts up
+  // to 3 columns early (REM) and a window of NWT columns covers REM + S + 3
+  static constexpr int NW = 4 * ((S + 3 + 3) / 4);         // G window (columns) per step, REM = 0
+  static constexpr int NWT = 4 * ((S + 6 + 3) / 4);        // ... for any REM < 4
+  static constexpr int GJ0 = kTma ? kGrJ - 4 + NWT : (kGrJ + S - 1 + 3) & ~3;
+  static constexpr int GP = (GJ0 % 8 == 4) ? GJ0 : GJ0 + 4;  // G row pitch (= 4 mod 8)
+  static constexpr int GB = (GR * GP + 31) & ~31;          // G buffer stride (128-byte aligned)
+  // + 128: the start is rounded up to a 128-byte boundary (TMA destinations)
+  static constexpr size_t smem = sizeof(float) * (kGrI * FP + 2 * GB) + 128;
 };
 
-template <int S>
+// Thread (row i, sigma)'s sums over one G tile: acc[up] = sum_j F(i, j) G(i + sigma, j + up),
+// F row Fr, G row Gr (data from column REM on), 16-byte loads with a sliding
+// window of NW G columns in registers.
+template <int S, int REM, int NW>
+__device__ __forceinline__ void grad_row(const float* Fr, const float* Gr, float (&acc)[S]) {
+  float w[NW];
+#pragma unroll
+  for (int c4 = 0; c4 < NW / 4; ++c4) {
+    const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * c4);
+    w[4 * c4] = g4.x;
+    w[4 * c4 + 1] = g4.y;
+    w[4 * c4 + 2] = g4.z;
+    w[4 * c4 + 3] = g4.w;
+  }
+#pragma unroll
+  for (int j4 = 0; j4 < kGrJ / 4; ++j4) {
+    const float4 f4 = *reinterpret_cast<const float4*>(Fr + 4 * j4);
+    const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int up = 0; up < S; ++up) acc[up] = fmaf(fv[c], w[REM + c + up], acc[up]);
+    if (j4 + 1 < kGrJ / 4) {  // slide the window by four columns
+#pragma unroll
+      for (int t = 0; t < NW - 4; ++t) w[t] = w[t + 4];
+      const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * j4 + NW);
+      w[NW - 4] = g4.x;
+      w[NW - 3] = g4.y;
+      w[NW - 2] = g4.z;
+      w[NW - 1] = g4.w;
+    }
+  }
+}
+
+// kTma: F and the G tiles arrive by TMA tensor copies from the phase planes of
+// f (a.tmap) and of dg (a.tmap2); otherwise by 4-byte cp.async copies.
+template <int S, bool kTma>
 __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcArgs a) {
-  using Gm = GradGeom<S>;
-  constexpr int FP = Gm::FP, GR = Gm::GR, GJ = Gm::GJ, GP = Gm::GP, NW = Gm::NW;
-  static_assert(kGrJ - 4 + NW <= GJ, "window stays inside the staged columns");
-  extern __shared__ __align__(16) float gsm[];
+  using Gm = GradGeom<S, kTma>;
+  constexpr int FP = Gm::FP, GR = Gm::GR, GJ0 = Gm::GJ0, GP = Gm::GP, GB = Gm::GB;
+  static_assert(kTma || kGrJ - 4 + Gm::NW <= GJ0, "window stays inside the staged columns");
+  extern __shared__ __align__(128) float gsm_raw[];
+  float* gsm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(gsm_raw) + 127) & ~uintptr_t(127));
   float* F_s = gsm;
-  float* G_s = gsm + kGrI * FP;  // [2][GR * GP]
+  float* G_s = gsm + kGrI * FP;  // [2][GB]
   __shared__ float part[8][S];
+  __shared__ __align__(8) uint64_t bars[3];  // G buffers 0, 1; F
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   const int p = blockIdx.x / Ny, q = blockIdx.x % Ny;
   const PcDepth dd = a.d[blockIdx.y];
@@ -552,27 +596,80 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
   const int nI = (Wx - p + Nx - 1) / Nx, nJ = (Wy - q + Ny - 1) / Ny;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i = tid & 63, sgs = tid >> 6;
+  if (kTma) {
+    if (tid == 0) {
+      for (int b = 0; b < 3; ++b) mbar_init(smem_addr(&bars[b]), 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  // the G tile of sub-problem c into buffer buf
+  auto stage_g = [&](const PcSub& c, int buf, int i0, int j0) {
+    float* dst = G_s + buf * GB;
+    if (kTma) {
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        const uint32_t b = smem_addr(&bars[buf]);
+        mbar_expect_tx(b, (uint32_t)(GR * GP * sizeof(float)));
+        tma_load_3d(smem_addr(dst), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                    (dd.z * Nx + c.ar) * Ny + c.br, b);
+        mbar_arrive(b);
+      }
+    } else {
+      pc_stage_input<GR, GJ0, GP, 1>(dst, dg, dg, Nx, Ny, Wx, Wy, i0, j0, c.xoff, c.yoff, warp,
+                                     lane);
+    }
+  };
   bool first_tile = true;
+  int ng = 0;  // G tiles staged so far (buffer uses: parity of each buffer's barrier)
+  int nf = 0;  // F tiles staged so far
   for (int i0 = 0; i0 < nI; i0 += kGrI)
     for (int j0 = 0; j0 < nJ; j0 += kGrJ) {
       __syncthreads();  // the previous tile's buffers are consumed
-      pc_stage_input<kGrI, kGrJ, FP, 1>(F_s, f, f, Nx, Ny, Wx, Wy, i0, j0, p, q, warp, lane);
+      if (kTma) {
+        if (tid == 0) {
+          fence_proxy_async_smem();
+          const uint32_t b = smem_addr(&bars[2]);
+          mbar_expect_tx(b, (uint32_t)(kGrI * FP * sizeof(float)));
+          tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, b);
+          mbar_arrive(b);
+        }
+      } else {
+        pc_stage_input<kGrI, kGrJ, FP, 1>(F_s, f, f, Nx, Ny, Wx, Wy, i0, j0, p, q, warp, lane);
+      }
       PcSub cur;
       pc_sub_depth(cur, 0, Ks, Kt, p, q, Nx, Ny);
-      pc_stage_input<GR, GJ, GP, 1>(G_s, dg, dg, Nx, Ny, Wx, Wy, i0, j0, cur.xoff, cur.yoff, warp,
-                                    lane);
+      const int g0 = ng;  // this tile's first G tile goes to buffer g0 & 1
+      stage_g(cur, g0 & 1, i0, j0);
+      ++ng;
       cp_async_commit();
       for (int k = 0;; ++k) {
-        const int buf = k & 1;
+        const int buf = (g0 + k) & 1;
         PcSub nxt = cur;
         const bool more = pc_sub_next_phase(nxt, p, q, Nx, Ny);
-        if (more)
-          pc_stage_input<GR, GJ, GP, 1>(G_s + (buf ^ 1) * (GR * GP), dg, dg, Nx, Ny, Wx, Wy, i0,
-                                        j0, nxt.xoff, nxt.yoff, warp, lane);
+        if (more) {
+          stage_g(nxt, buf ^ 1, i0, j0);
+          ++ng;
+        }
         cp_async_commit();
         cp_async_wait<1>();
-        __syncthreads();  // F and this sub-problem's G have landed
-        const float* Gb = G_s + buf * (GR * GP);
+        if (kTma) {
+          const bool okg = mbar_wait_bounded(smem_addr(&bars[buf]),
+                                             (uint32_t)(((g0 + k) >> 1) & 1), nullptr, kPcWaitNs);
+          const bool okf = k > 0 || mbar_wait_bounded(smem_addr(&bars[2]), (uint32_t)(nf & 1),
+                                                      nullptr, kPcWaitNs);
+          const bool ok = okg && okf;
+          if (pc_abort(a, !ok)) {
+            if (tid == 0 && more)
+              mbar_wait_bounded(smem_addr(&bars[buf ^ 1]), (uint32_t)(((g0 + k + 1) >> 1) & 1),
+                                nullptr, kPcWaitNs);
+            return;
+          }
+        } else {
+          __syncthreads();  // F and this sub-problem's G have landed
+        }
+        const float* Gb = G_s + buf * GB;
+        const int rem = kTma ? (cur.qy & 3) : 0;
         for (int s0 = 0; s0 < S; s0 += 4) {
           const int sg = s0 + sgs;
           float acc[S];
@@ -581,31 +678,14 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
           if (sg < S) {
             const float* Fr = F_s + i * FP;
             const float* Gr = Gb + (i + sg) * GP;
-            float w[NW];
-#pragma unroll
-            for (int c4 = 0; c4 < NW / 4; ++c4) {
-              const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * c4);
-              w[4 * c4] = g4.x;
-              w[4 * c4 + 1] = g4.y;
-              w[4 * c4 + 2] = g4.z;
-              w[4 * c4 + 3] = g4.w;
-            }
-#pragma unroll
-            for (int j4 = 0; j4 < kGrJ / 4; ++j4) {
-              const float4 f4 = *reinterpret_cast<const float4*>(Fr + 4 * j4);
-              const float fv[4] = {f4.x, f4.y, f4.z, f4.w};
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-#pragma unroll
-                for (int up = 0; up < S; ++up) acc[up] = fmaf(fv[c], w[c + up], acc[up]);
-              if (j4 + 1 < kGrJ / 4) {  // slide the window by four columns
-#pragma unroll
-                for (int t = 0; t < NW - 4; ++t) w[t] = w[t + 4];
-                const float4 g4 = *reinterpret_cast<const float4*>(Gr + 4 * j4 + NW);
-                w[NW - 4] = g4.x;
-                w[NW - 3] = g4.y;
-                w[NW - 2] = g4.z;
-                w[NW - 1] = g4.w;
+            if (!kTma) {
+              grad_row<S, 0, Gm::NW>(Fr, Gr, acc);
+            } else {
+              switch (rem) {
+                case 0: grad_row<S, 0, Gm::NWT>(Fr, Gr, acc); break;
+                case 1: grad_row<S, 1, Gm::NWT>(Fr, Gr, acc); break;
+                case 2: grad_row<S, 2, Gm::NWT>(Fr, Gr, acc); break;
+                default: grad_row<S, 3, Gm::NWT>(Fr, Gr, acc); break;
               }
             }
           }
@@ -632,6 +712,7 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
         cur = nxt;
       }
       cp_async_wait<0>();
+      ++nf;
       first_tile = false;
     }
 }
@@ -1080,20 +1161,17 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   // the input by phase for the TMA path (released, stream-ordered, on return)
   struct PlanesGuard {
     Planes pl;
-    bool on = false;
     cudaStream_t st;
-    ~PlanesGuard() {
-      if (on) planes_release(pl, st);
-    }
+    ~PlanesGuard() { planes_release(pl, st); }
   } pg;
   pg.st = st;
+  bool tma = false;
   if (any_tma && Nz > 0 && tma_enabled()) {
-    if (planes_build(pg.pl, in, in_zstride, in_zstride ? Nz : 1, Nx, Ny, Wx, Wy, st) == 0)
-      pg.on = true;
-    else if (pg.pl.ptr)
-      return -6;  // allocated but the relayout launch failed
+    const int r = planes_build(pg.pl, in, in_zstride, in_zstride ? Nz : 1, Nx, Ny, Wx, Wy, st);
+    if (r == -6) return -6;  // the relayout launch failed
+    tma = r == 0;            // -1: no scratch memory, the cp.async path instead
   }
-  const Planes* pl = pg.on ? &pg.pl : nullptr;
+  const Planes* pl = tma ? &pg.pl : nullptr;
   PcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.status = status;
@@ -1170,27 +1248,65 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
 }
 
 namespace {
-template <int S>
-int launch_grad(const PcArgs& a, dim3 grid, cudaStream_t st) {
+template <int S, bool kTma>
+int launch_grad_t(const PcArgs& a, dim3 grid, cudaStream_t st) {
   static bool attr_set = false;  // per instance; setting it twice is harmless
   if (!attr_set) {
-    if (cudaFuncSetAttribute(k_phase_grad<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)GradGeom<S>::smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_phase_grad<S, kTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)GradGeom<S, kTma>::smem) != cudaSuccess)
       return -6;
     attr_set = true;
   }
-  k_phase_grad<S><<<grid, 256, GradGeom<S>::smem, st>>>(a);
+  k_phase_grad<S, kTma><<<grid, 256, GradGeom<S, kTma>::smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
+// With phase planes of f (pf) and dg (pg): tensor maps for the F box
+// (kGrI rows x FP columns) and the G boxes (GR rows x GP columns).
+template <int S>
+int launch_grad(PcArgs& a, const Planes* pf, const Planes* pg, dim3 grid, cudaStream_t st) {
+  if (S <= kPcTmaMaxS && pf && pg) {
+    using Gm = GradGeom<S, true>;
+    if (planes_map(*pf, Gm::FP, kGrI, &a.tmap) || planes_map(*pg, Gm::GP, Gm::GR, &a.tmap2))
+      return -6;
+    return launch_grad_t<S, (S <= kPcTmaMaxS)>(a, grid, st);
+  }
+  return launch_grad_t<S, false>(a, grid, st);
 }
 }  // namespace
 
 int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, const long long* off,
-                      const int* Ks, const int* Kt, int Wx, int Wy, float* dA, cudaStream_t st) {
-  for (int z = 0; z < Nz; ++z)
-    if (!phase_conv_size(Nx, Ny, Ks[z], Kt[z])) return -1;
+                      const int* Ks, const int* Kt, int Wx, int Wy, float* dA, int* status,
+                      cudaStream_t st) {
+  bool any_tma = false;
+  for (int z = 0; z < Nz; ++z) {
+    const int S = phase_conv_size(Nx, Ny, Ks[z], Kt[z]);
+    if (!S) return -1;
+    any_tma |= S <= kPcTmaMaxS;
+  }
   if ((long long)Nx * Ny > 0x7fffffffLL) return -1;
+  // f and dg by phase for the TMA path (released, stream-ordered, on return)
+  struct Guard {
+    Planes pf, pg;
+    cudaStream_t st;
+    ~Guard() {
+      planes_release(pf, st);
+      planes_release(pg, st);
+    }
+  } gd;
+  gd.st = st;
+  bool tma = false;
+  if (any_tma && Nz > 0 && tma_enabled()) {
+    const int r1 = planes_build(gd.pf, f, 0, 1, Nx, Ny, Wx, Wy, st);
+    const int r2 = r1 ? r1 : planes_build(gd.pg, dg, (long long)Wx * Wy, Nz, Nx, Ny, Wx, Wy, st);
+    if (r1 == -6 || r2 == -6) return -6;
+    tma = r1 == 0 && r2 == 0;
+  }
+  const Planes* pf = tma ? &gd.pf : nullptr;
+  const Planes* pg = tma ? &gd.pg : nullptr;
   PcArgs a;
   std::memset(&a, 0, sizeof(a));
+  a.status = status;
   a.in = f;
   a.g = dg;
   a.out_zstride = (long long)Wx * Wy;
@@ -1214,13 +1330,13 @@ int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, c
         const dim3 grid((unsigned)(Nx * Ny), (unsigned)n);
         int rc = 0;
         switch (S) {
-          case 3: rc = launch_grad<3>(a, grid, st); break;
-          case 5: rc = launch_grad<5>(a, grid, st); break;
-          case 7: rc = launch_grad<7>(a, grid, st); break;
-          case 9: rc = launch_grad<9>(a, grid, st); break;
-          case 11: rc = launch_grad<11>(a, grid, st); break;
-          case 13: rc = launch_grad<13>(a, grid, st); break;
-          default: rc = launch_grad<15>(a, grid, st); break;
+          case 3: rc = launch_grad<3>(a, pf, pg, grid, st); break;
+          case 5: rc = launch_grad<5>(a, pf, pg, grid, st); break;
+          case 7: rc = launch_grad<7>(a, pf, pg, grid, st); break;
+          case 9: rc = launch_grad<9>(a, pf, pg, grid, st); break;
+          case 11: rc = launch_grad<11>(a, pf, pg, grid, st); break;
+          case 13: rc = launch_grad<13>(a, pf, pg, grid, st); break;
+          default: rc = launch_grad<15>(a, pf, pg, grid, st); break;
         }
         if (rc) return rc;
         if (cudaGetLastError() != cudaSuccess) return -6;

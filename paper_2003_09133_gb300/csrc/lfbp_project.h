@@ -43,7 +43,8 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
 // for every depth (dA_z at dA + off[z], dg_z at dg + z*Wx*Wy); -1 (nothing
 // launched) when a cut-out exceeds 15 cells per axis (use launch_backproject_grad).
 int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, const long long* off,
-                      const int* Ks, const int* Kt, int Wx, int Wy, float* dA, cudaStream_t st);
+                      const int* Ks, const int* Kt, int Wx, int Wy, float* dA, int* status,
+                      cudaStream_t st);
 // fe_r[i] = f[i] / fe_r[i] where fe_r[i] != 0, else 0 (the quotient of Eq. 2)
 int launch_rl_quotient(const float* f, float* fe_r, long long n, cudaStream_t st);
 // r[i] = f[i] / sum_{z < Nz} parts[z*n + i] (fixed order; 0 where the sum is 0)

@@ -149,3 +149,17 @@ def test_injected_plan_failure(lib, monkeypatch):
     rc, h = _plan(lib, 5, 5, [15], [15])
     assert rc == 0 and h.value
     lib.lfbp_plan_destroy(h)
+
+
+def test_gradient_validation_sizes_the_gradient_volume(lib):
+    """lfbp_backproject_volume_grad's dL/dg is an Nz x Wx x Wy volume: an output
+    starting inside it (or inside f) is an overlap, rejected before any launch.
+    (That an output right after it is accepted is checked on the GPU.)"""
+    rc, h = _plan(lib, 3, 3, [9, 15], [9, 15])   # 3*3*(81+225) = 2754 elements
+    assert rc == 0
+    W = 12
+    vol = 2 * W * W * 4                          # 1152 bytes: smaller than the plan
+    f, dg = 0x10000000, 0x20000000
+    assert lib.lfbp_backproject_volume_grad(h, f, dg, W, W, dg + vol - 16, None) == -4
+    assert lib.lfbp_backproject_volume_grad(h, f, dg, W, W, f + W * W * 4 - 16, None) == -4
+    lib.lfbp_plan_destroy(h)

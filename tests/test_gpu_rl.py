@@ -202,11 +202,12 @@ def test_projectors_are_deterministic(lf):
 
 
 def test_tma_and_cpasync_staging_agree_bitwise(lf, monkeypatch):
-    """The projectors stage their input subgrids either by TMA tensor copies
-    from the input laid out by phase (default) or by 4-byte cp.async copies
-    (LFBP_PROJ_TMA=0).  Both feed the same products in the same order, so the
-    normaliser, both forms of the update and the backprojection agree bit for
-    bit; rows and columns outside the sensor arrive as zeros either way."""
+    """The projectors and the H'-gradient stage their input tiles either by
+    TMA tensor copies from the inputs laid out by phase (default) or by 4-byte
+    cp.async copies (LFBP_PROJ_TMA=0).  Both feed the same products in the same
+    order, so the normaliser, both forms of the update, the backprojection and
+    the gradient agree bit for bit; rows and columns outside the sensor arrive
+    as zeros either way."""
     spec = lfgen.config_specs("autograd")[0]
     cases = CASES + [(spec.Nx, spec.Ny, list(spec.Ks), list(spec.Kt), 7 * spec.Nx + 5, 6 * spec.Ny)]
     for Nx, Ny, Ks, Kt, Wx, Wy in cases:
@@ -221,8 +222,25 @@ def test_tma_and_cpasync_staging_agree_bitwise(lf, monkeypatch):
             g2 = gd.clone()
             lf.rl_step(plan, Hd, None, norm, fd, g2, out=g2)
             vol = lf.backproject_volume_from_h(plan, Hd, fd)
+            grad = lf.backproject_volume_grad(plan, fd, gd)
             lf.sync_status()
-            res[mode] = [x.cpu().numpy() for x in (norm, out, g2, vol)]
-        for what, a, b in zip(("normaliser", "update", "update in place", "backprojection"),
-                              res["1"], res["0"]):
+            res[mode] = [x.cpu().numpy() for x in (norm, out, g2, vol, grad)]
+        for what, a, b in zip(("normaliser", "update", "update in place", "backprojection",
+                               "gradient"), res["1"], res["0"]):
             assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (Nx, Ny, Ks, Wx, Wy, what)
+
+
+def test_gradient_output_right_after_the_gradient_volume(lf):
+    """dL/dg sized as an Nz x Wx x Wy volume (smaller than the plan here): an
+    output placed right after it in one allocation is accepted and correct."""
+    Nx, Ny, Ks, W = 3, 3, [9, 15], 12
+    plan = lf.Plan(Nx, Ny, Ks, Ks, torch.float32)
+    nvol = len(Ks) * W * W
+    buf = torch.zeros(nvol + plan.elems, device="cuda")
+    dg, out = buf[:nvol].view(len(Ks), W, W), buf[nvol:]
+    dg.copy_(torch.rand((len(Ks), W, W), device="cuda", generator=torch.Generator("cuda").manual_seed(3)))
+    f = torch.rand((W, W), device="cuda", generator=torch.Generator("cuda").manual_seed(4))
+    lf.backproject_volume_grad(plan, f, dg, out=out)
+    want = lf.backproject_volume_grad(plan, f, dg.clone())
+    lf.sync_status()
+    assert torch.equal(out, want)
