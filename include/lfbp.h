@@ -190,6 +190,19 @@ int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void
 int lfbp_adjoint(lfbp_plan p, const void* dHp_grad, void* dH_grad, void* cuda_stream);
 
 /*
+ * Scratch memory of the projector entry points below (backprojection,
+ * forward projection, gradient, Richardson-Lucy update and normaliser): for
+ * cut-outs of up to 9 cells per axis the kernels read their input tiles by
+ * TMA tensor copies from a copy of the input laid out by phase (about the
+ * size of the input image or volume).  That copy is allocated stream-ordered
+ * on the call's stream from a memory pool the library creates per device (its
+ * memory is kept for reuse, not returned to the system) and released on the
+ * stream when the call's kernels are done.  When the pool cannot provide it,
+ * the kernels read the input directly (same results, bit for bit).  The
+ * environment variable LFBP_PROJ_TMA=0 selects the direct reads.
+ */
+
+/*
  * Backprojection of a sensor image through H' (the H' f inside the
  * Richardson-Lucy update, Eq. 2) on a finite Wx x Wy sensor whose voxel grid
  * coincides laterally with the pixel grid; the cell position of a point P is
@@ -216,8 +229,9 @@ int lfbp_forward_project(lfbp_plan p, const void* dH, const float* dg, int Wx, i
  * Gradient of a loss L(g) with g = H' f (lfbp_backproject_volume) with respect
  * to the entries of H', given dL/dg ([Nz][Wx][Wy] fp32):
  *   dL/dH'_z[p][q][u][v] = sum over pixels S of cell (p, q) of f[S] * dL/dg_z[S + (u-c_s, v-c_t)]
- * df: [Wx][Wy]; dHp_grad: output in the plan's layout (fp32).  Each output is
- * one thread's fixed-order fp32 sum (deterministic, no atomics).
+ * df: [Wx][Wy]; dHp_grad: output in the plan's layout (fp32); it must not
+ * overlap df or dgrad (LFBP_ERR_ALIAS).  Each output is a fixed-order fp32
+ * sum (deterministic, no atomics).
  */
 int lfbp_backproject_volume_grad(lfbp_plan p, const float* df, const float* dgrad, int Wx, int Wy,
                                  void* dHp_grad, void* cuda_stream);
