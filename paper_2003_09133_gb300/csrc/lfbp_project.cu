@@ -322,6 +322,18 @@ __device__ __forceinline__ void pc_tma_stage(const PcArgs& a, const PcSub& c, in
   mbar_arrive(b);
 }
 
+// The same copy for a barrier whose arrivals come from elsewhere (only the
+// expected bytes are registered here).
+__device__ __forceinline__ void pc_tma_stage_noarrive(const PcArgs& a, const PcSub& c, int zplane0,
+                                                      float* dst, uint64_t* bar, int i0, int j0,
+                                                      uint32_t bytes) {
+  fence_proxy_async_smem();
+  const uint32_t b = smem_addr(bar);
+  mbar_expect_tx(b, bytes);
+  tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+              (zplane0 + c.ar) * a.Ny + c.br, b);
+}
+
 // Products of one staged sub-problem: rows r of the subgrid tile (pitch PITCH,
 // data from column REM on) against the S x S sub-kernel, into acc.
 template <int S, int RH, int REM, int PITCH, int NACC>
@@ -377,6 +389,167 @@ __device__ __forceinline__ bool pc_abort(const PcArgs& a, bool timed_out) {
   if (threadIdx.x == 0 && a.status) atomicCAS(a.status, 0, kStatusTimeout);
   cp_async_wait<0>();
   return true;
+}
+
+// cp.async copies of this thread so far arrive on `bar` when they land (the
+// arrival counts toward the barrier's expected count).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+               : "memory");
+}
+
+constexpr int kPcStages = 3;                    // input/weight stages of the pipelined kernel
+constexpr int kPcPipeThreads = kPcThreads + 32;  // 8 consumer warps + 1 producer warp
+
+// The TMA path of k_phase_conv as a producer/consumer pipeline without
+// block-wide barriers.  Warp 8 produces: per sub-problem it issues the weights
+// as 4-byte cp.async copies, lane by lane, and each lane's copies arrive on the
+// stage's full barrier when they land.  Lane 0 also issues the TMA copy of the
+// input subgrid and writes the stage's column remainder, releasing it with a
+// plain arrival.  Warps 0-7 consume the stages in order and release each one
+// with a per-warp arrival on its empty barrier.  Same products in the same
+// order as k_phase_conv.
+// DB = 1: one depth per block (grid.y), or all depths summed (sum_depths);
+// DB > 1: DB depths of one cut-out size reading one shared image, each staged
+// subgrid feeding all DB depths' weights (the backprojections).
+template <int S, int RI, int DB>
+__global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid_constant__ PcArgs a) {
+  constexpr int TI = 8 * RI;
+  constexpr int S4 = (S + 3) & ~3;
+  constexpr int IR = TI + S - 1;
+  constexpr int RH = RI / 2;
+  constexpr int ICP = PcBox<S>::BX;
+  constexpr int IB = (IR * ICP + 31) & ~31;
+  constexpr int NW = DB * S * S4;  // weights per stage
+  __shared__ __align__(128) float I_s[kPcStages][IB];
+  __shared__ __align__(16) float w_s[kPcStages][NW];
+  __shared__ int rem_s[kPcStages];
+  __shared__ __align__(8) uint64_t full[kPcStages], empty[kPcStages];
+  __shared__ int abort_flag;
+  const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
+  int t = blockIdx.x;
+  const int tj = t % a.nTJ;
+  t /= a.nTJ;
+  const int ti = t % a.nTI;
+  t /= a.nTI;
+  const int py = t % Ny, px = t / Ny;
+  const int i0 = ti * TI, j0 = tj * kPcTJ;
+  const int tid = threadIdx.x, wi = tid >> 5, lane = tid & 31;
+  // DB = 1: depths d_lo .. d_hi-1 in sequence; DB > 1: the group dbase .. dbase+nd-1 at once
+  const int dbase = DB > 1 ? (int)blockIdx.y * DB : 0;
+  const int nd = DB > 1 ? min(DB, a.ndepth - dbase) : 1;
+  const int d_lo = DB > 1 ? dbase : a.sum_depths ? 0 : (int)blockIdx.y;
+  const int d_hi = DB > 1 ? dbase + 1 : a.sum_depths ? a.ndepth : (int)blockIdx.y + 1;
+  int nsub = 0;
+  for (int d = d_lo; d < d_hi; ++d) nsub += min(Nx, a.d[d].Ks) * min(Ny, a.d[d].Kt);
+  if (tid == 0) {
+    for (int s = 0; s < kPcStages; ++s) {
+      mbar_init(smem_addr(&full[s]), 33);  // 32 copy-completion arrivals + lane 0's release
+      mbar_init(smem_addr(&empty[s]), 8);
+    }
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (wi == 8) {
+    // ---- producer warp
+    PcSub c;
+    pc_sub_depth(c, d_lo, a.d[d_lo].Ks, a.d[d_lo].Kt, px, py, Nx, Ny);
+    int issued = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const int s = k % kPcStages;
+      if (k >= kPcStages &&
+          !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((k / kPcStages - 1) & 1), &abort_flag,
+                             kPcWaitNs)) {
+        if (lane == 0) {
+          abort_flag = 1;
+          if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+        }
+        break;
+      }
+      const int Ks = c.Ks, Kt = c.Kt;
+      for (int e = lane; e < NW; e += 32) {
+        const int wd = e / (S * S4), ee = e - wd * (S * S4);
+        const int sg = ee / S4, up = ee - sg * S4;
+        const bool ok = wd < nd && sg < c.Ssig && up < c.Sups;
+        const int u = Nx * sg + c.rho, v = Ny * up + c.tau;
+        const float* Az = a.A + (ok ? a.d[DB > 1 ? dbase + wd : c.di].off : 0);
+        const float* src =
+            !ok ? a.A
+                : a.mapped ? Az + (((size_t)c.ar * Ny + c.br) * Ks + (Ks - 1 - u)) * Kt + (Kt - 1 - v)
+                           : Az + (((size_t)px * Ny + py) * Ks + u) * Kt + v;
+        cp_async4(&w_s[s][e], src, ok);
+      }
+      if (lane == 0) {
+        rem_s[s] = c.qy & 3;
+        const int zp = (DB == 1 && a.in_zstride) ? a.d[c.di].z * Nx : 0;
+        pc_tma_stage_noarrive(a, c, zp, I_s[s], &full[s], i0, j0,
+                              (uint32_t)(IR * ICP * sizeof(float)));
+      }
+      cp_async_arrive_noinc(&full[s]);  // this lane's arrival, once its copies have landed
+      if (lane == 0) mbar_arrive(smem_addr(&full[s]));  // releases rem_s[s]
+      ++issued;
+      if (k + 1 < nsub && !pc_sub_next_phase(c, px, py, Nx, Ny))
+        pc_sub_depth(c, c.di + 1, a.d[c.di + 1].Ks, a.d[c.di + 1].Kt, px, py, Nx, Ny);
+    }
+    // nothing of this CTA may still be landing when it exits: wait for the
+    // stages still in flight (already complete unless the consumers gave up)
+    if (lane == 0)
+      for (int j = issued - 1; j >= 0 && j >= issued - kPcStages; --j)
+        mbar_wait_bounded(smem_addr(&full[j % kPcStages]), (uint32_t)((j / kPcStages) & 1), nullptr,
+                          kPcWaitNs);
+    cp_async_wait<0>();
+    return;
+  }
+
+  // ---- consumer warps
+  const int a0 = wi * RI + (lane >> 4) * RH, b0 = 4 * (lane & 15);
+  float acc[DB][RH][4];
+#pragma unroll
+  for (int d = 0; d < DB; ++d)
+#pragma unroll
+    for (int i = 0; i < RH; ++i) acc[d][i][0] = acc[d][i][1] = acc[d][i][2] = acc[d][i][3] = 0.f;
+  for (int k = 0; k < nsub; ++k) {
+    const int s = k % kPcStages;
+    if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)((k / kPcStages) & 1), &abort_flag,
+                           kPcWaitNs)) {
+      if (lane == 0) {
+        abort_flag = 1;
+        if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+      }
+      return;
+    }
+    const float* wbs[DB];
+#pragma unroll
+    for (int d = 0; d < DB; ++d) wbs[d] = w_s[s] + d * (S * S4);
+    pc_products_rem<S, RH, ICP, DB>(rem_s[s], I_s[s], wbs, a0, b0, acc);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
+  }
+
+#pragma unroll
+  for (int d = 0; d < DB; ++d) {
+    if (d >= nd) break;
+    const long long zo = DB > 1 ? (long long)a.d[dbase + d].z * a.out_zstride
+                         : a.sum_depths ? 0 : (long long)a.d[blockIdx.y].z * a.out_zstride;
+#pragma unroll
+    for (int i = 0; i < RH; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int X = px + Nx * (i0 + a0 + i), Y = py + Ny * (j0 + b0 + c);
+        if (X >= Wx || Y >= Wy) continue;
+        const long long o = zo + (long long)X * Wy + Y;
+        if (a.epi == kEpiStore) {
+          a.out[o] = acc[d][i][c];
+        } else if (a.epi == kEpiAccumulate) {
+          a.out[o] += acc[d][i][c];
+        } else {
+          const float n = a.norm[o];
+          a.out[o] = n != 0.f ? (a.g[o] / n) * acc[d][i][c] : 0.f;
+        }
+      }
+  }
 }
 
 // RI: output rows per thread; the block (8 warps) covers 8*RI rows x 64 columns.
@@ -1041,6 +1214,11 @@ struct Planes {
   int Pi = 0, Pjp = 0, nplanes = 0;
 };
 
+bool pipe_enabled() {
+  const char* s = std::getenv("LFBP_PROJ_PIPE");
+  return !(s && s[0] == '0');
+}
+
 bool tma_enabled() {
   const char* s = std::getenv("LFBP_PROJ_TMA");
   return !(s && s[0] == '0') && encode_tiled() != nullptr;
@@ -1090,7 +1268,10 @@ int launch_pc_ri(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t 
   const dim3 grid((unsigned)nblocks, (unsigned)ny);
   if (S <= kPcTmaMaxS && pl) {
     if (planes_map(*pl, PcBox<S>::BX, 8 * RI + S - 1, &a.tmap)) return -6;
-    k_phase_conv<S, RI, (S <= kPcTmaMaxS)><<<grid, kPcThreads, 0, st>>>(a);
+    if (pipe_enabled())
+      k_phase_conv_pipe<(S <= kPcTmaMaxS ? S : 3), RI, 1><<<grid, kPcPipeThreads, 0, st>>>(a);
+    else
+      k_phase_conv<S, RI, (S <= kPcTmaMaxS)><<<grid, kPcThreads, 0, st>>>(a);
   } else {
     k_phase_conv<S, RI, false><<<grid, kPcThreads, 0, st>>>(a);
   }
@@ -1121,6 +1302,8 @@ constexpr int kPcDB = 4;  // depths per block of k_phase_conv_md
 template <int S>
 int launch_md(PcArgs& a, const Planes* pl, dim3 grid, cudaStream_t st) {
   if (pl) {
+    // (the pipelined form, k_phase_conv_pipe<S, 4, kPcDB>, measured slower here:
+    // 96 registers x 288 threads leave two blocks per SM, like this one)
     if (planes_map(*pl, PcBox<S>::BX, 32 + S - 1, &a.tmap)) return -6;
     k_phase_conv_md<S, kPcDB, true><<<grid, kPcThreads, 0, st>>>(a);
   } else {

@@ -203,8 +203,10 @@ def test_projectors_are_deterministic(lf):
 
 def test_tma_and_cpasync_staging_agree_bitwise(lf, monkeypatch):
     """The projectors and the H'-gradient stage their input tiles either by
-    TMA tensor copies from the inputs laid out by phase (default) or by 4-byte
-    cp.async copies (LFBP_PROJ_TMA=0).  Both feed the same products in the same
+    TMA tensor copies from the inputs laid out by phase (default; the
+    single-depth projector as a producer/consumer pipeline, or with block
+    barriers under LFBP_PROJ_PIPE=0) or by 4-byte cp.async copies
+    (LFBP_PROJ_TMA=0).  Both feed the same products in the same
     order, so the normaliser, both forms of the update, the backprojection and
     the gradient agree bit for bit; rows and columns outside the sensor arrive
     as zeros either way."""
@@ -215,8 +217,9 @@ def test_tma_and_cpasync_staging_agree_bitwise(lf, monkeypatch):
         H, g, f = _case_data(plan, (Nx, Ny, Ks, Kt, Wx, Wy), 24)
         Hd, gd, fd = (torch.from_numpy(a).cuda() for a in (H, g, f))
         res = {}
-        for mode in ("1", "0"):
-            monkeypatch.setenv("LFBP_PROJ_TMA", mode)
+        for mode in ("1", "0", "1-nopipe"):
+            monkeypatch.setenv("LFBP_PROJ_TMA", mode[0])
+            monkeypatch.setenv("LFBP_PROJ_PIPE", "0" if mode.endswith("nopipe") else "1")
             norm = lf.rl_normaliser(plan, Hd, None, Wx, Wy)
             out = lf.rl_step(plan, Hd, None, norm, fd, gd)
             g2 = gd.clone()
@@ -225,9 +228,11 @@ def test_tma_and_cpasync_staging_agree_bitwise(lf, monkeypatch):
             grad = lf.backproject_volume_grad(plan, fd, gd)
             lf.sync_status()
             res[mode] = [x.cpu().numpy() for x in (norm, out, g2, vol, grad)]
-        for what, a, b in zip(("normaliser", "update", "update in place", "backprojection",
-                               "gradient"), res["1"], res["0"]):
-            assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), (Nx, Ny, Ks, Wx, Wy, what)
+        for other in ("0", "1-nopipe"):
+            for what, a, b in zip(("normaliser", "update", "update in place", "backprojection",
+                                   "gradient"), res["1"], res[other]):
+                assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), \
+                    (Nx, Ny, Ks, Wx, Wy, what, other)
 
 
 def test_gradient_output_right_after_the_gradient_volume(lf):
