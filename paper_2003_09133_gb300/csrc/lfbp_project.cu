@@ -360,11 +360,19 @@ __device__ __forceinline__ void pc_products(const float* Ib, const float* const*
       for (int sg = 0; sg < S; ++sg) {
         const int ai = r - sg;
         if (ai < 0 || ai >= RH) continue;
+        float wr[S4];  // the kernel row sg, in 16-byte shared loads
+#pragma unroll
+        for (int u4 = 0; u4 < S4 / 4; ++u4) {
+          const float4 w4 = *reinterpret_cast<const float4*>(wb + sg * S4 + 4 * u4);
+          wr[4 * u4] = w4.x;
+          wr[4 * u4 + 1] = w4.y;
+          wr[4 * u4 + 2] = w4.z;
+          wr[4 * u4 + 3] = w4.w;
+        }
 #pragma unroll
         for (int up = 0; up < S; ++up) {
-          const float wv = wb[sg * S4 + up];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) acc[d][ai][c] = fmaf(xv[REM + up + c], wv, acc[d][ai][c]);
+          for (int c = 0; c < 4; ++c) acc[d][ai][c] = fmaf(xv[REM + up + c], wr[up], acc[d][ai][c]);
         }
       }
     }
