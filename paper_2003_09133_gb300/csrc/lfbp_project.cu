@@ -898,6 +898,177 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
     }
 }
 
+// The TMA form of k_phase_grad as a producer/consumer pipeline.  Warp 8
+// produces: per cell tile the F box, per (rho, tau) sub-problem a G box into
+// one of kGrStages stages (TMA copies; lane 0 also writes the sub-problem's
+// record and arrives).  Warps 0-7 consume in order: the pair of warps 2w, 2w+1
+// owns sigma = s0 + w of each round (rows i = 32 (warp & 1) + lane), reduces
+// its rows by shuffles and combines the two warps' sums behind an mbarrier of
+// the pair alone (both warps arrive and wait, bounded, once per round; the
+// partial sums alternate between two buffers), so no block-wide barrier is
+// needed; each warp frees a stage with one arrival on its empty barrier.  Same
+// sums in the same order as k_phase_grad.
+constexpr int kGrStages = 2;
+
+struct GrRec {
+  int rho, tau, Ssig, Sups, rem;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid_constant__ PcArgs a) {
+  using Gm = GradGeom<S, true>;
+  constexpr int FP = Gm::FP, GR = Gm::GR, GP = Gm::GP, GB = Gm::GB, NWT = Gm::NWT;
+  extern __shared__ __align__(128) float gsm_raw[];
+  float* gsm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(gsm_raw) + 127) & ~uintptr_t(127));
+  float* F_s = gsm;
+  float* G_s = gsm + kGrI * FP;  // [kGrStages][GB]
+  __shared__ float part[2][8][S];
+  __shared__ GrRec rec[kGrStages];
+  __shared__ __align__(8) uint64_t full[kGrStages], empty[kGrStages], ffull, fempty, pbar[4];
+  __shared__ int abort_flag;
+  const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
+  const int p = blockIdx.x / Ny, q = blockIdx.x % Ny;
+  const PcDepth dd = a.d[blockIdx.y];
+  const int Ks = dd.Ks, Kt = dd.Kt;
+  float* dA = a.out + dd.off + ((long long)p * Ny + q) * Ks * Kt;
+  const int nI = (Wx - p + Nx - 1) / Nx, nJ = (Wy - q + Ny - 1) / Ny;
+  const int ntile = ((nI + kGrI - 1) / kGrI) * ((nJ + kGrJ - 1) / kGrJ);
+  const int nsub = min(Nx, Ks) * min(Ny, Kt);  // sub-problems per tile
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < kGrStages; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), 8);
+    }
+    mbar_init(smem_addr(&ffull), 1);
+    mbar_init(smem_addr(&fempty), 8);
+    for (int w = 0; w < 4; ++w) mbar_init(smem_addr(&pbar[w]), 2);  // the two warps of a pair
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int njt = (nJ + kGrJ - 1) / kGrJ;
+
+  if (warp == 8) {
+    // ---- producer warp (lane 0 issues; the others only take part in the drain)
+    int issued = 0, tiles = 0;
+    bool ok = true;
+    if (lane == 0) {
+      for (int tl = 0; tl < ntile && ok; ++tl) {
+        const int i0 = (tl / njt) * kGrI, j0 = (tl % njt) * kGrJ;
+        if (tl > 0 && !(ok = mbar_wait_bounded(smem_addr(&fempty), (uint32_t)((tl - 1) & 1),
+                                               &abort_flag, kPcWaitNs)))
+          break;
+        fence_proxy_async_smem();
+        mbar_expect_tx(smem_addr(&ffull), (uint32_t)(kGrI * FP * sizeof(float)));
+        tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, smem_addr(&ffull));
+        mbar_arrive(smem_addr(&ffull));
+        ++tiles;
+        PcSub c;
+        pc_sub_depth(c, 0, Ks, Kt, p, q, Nx, Ny);
+        for (int k = 0; k < nsub; ++k) {
+          const int s = issued % kGrStages;
+          if (issued >= kGrStages &&
+              !(ok = mbar_wait_bounded(smem_addr(&empty[s]),
+                                       (uint32_t)((issued / kGrStages - 1) & 1), &abort_flag,
+                                       kPcWaitNs)))
+            break;
+          rec[s] = GrRec{c.rho, c.tau, c.Ssig, c.Sups, c.qy & 3};
+          fence_proxy_async_smem();
+          const uint32_t b = smem_addr(&full[s]);
+          mbar_expect_tx(b, (uint32_t)(GR * GP * sizeof(float)));
+          tma_load_3d(smem_addr(G_s + s * GB), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                      (dd.z * Nx + c.ar) * Ny + c.br, b);
+          mbar_arrive(b);  // releases rec[s]
+          ++issued;
+          pc_sub_next_phase(c, p, q, Nx, Ny);
+        }
+      }
+      if (!ok) {
+        abort_flag = 1;
+        if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+      }
+      // nothing of this CTA may still be landing when it exits
+      for (int j = issued - 1; j >= 0 && j >= issued - kGrStages; --j)
+        mbar_wait_bounded(smem_addr(&full[j % kGrStages]), (uint32_t)((j / kGrStages) & 1), nullptr,
+                          kPcWaitNs);
+      if (tiles > 0)
+        mbar_wait_bounded(smem_addr(&ffull), (uint32_t)((tiles - 1) & 1), nullptr, kPcWaitNs);
+    }
+    return;
+  }
+
+  // ---- consumer warps
+  const int i = ((warp & 1) << 5) + lane, pair = warp >> 1;
+  int used = 0, round = 0;
+  for (int tl = 0; tl < ntile; ++tl) {
+    if (!mbar_wait_bounded(smem_addr(&ffull), (uint32_t)(tl & 1), &abort_flag, kPcWaitNs)) {
+      if (lane == 0) {
+        abort_flag = 1;
+        if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+      }
+      return;
+    }
+    for (int k = 0; k < nsub; ++k, ++used) {
+      const int s = used % kGrStages;
+      if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)((used / kGrStages) & 1), &abort_flag,
+                             kPcWaitNs)) {
+        if (lane == 0) {
+          abort_flag = 1;
+          if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+        }
+        return;
+      }
+      const GrRec r = rec[s];
+      const float* Gb = G_s + s * GB;
+      for (int s0 = 0; s0 < S; s0 += 4, ++round) {
+        const int sg = s0 + pair;
+        float acc[S];
+#pragma unroll
+        for (int up = 0; up < S; ++up) acc[up] = 0.f;
+        if (sg < S) {
+          const float* Fr = F_s + i * FP;
+          const float* Gr = Gb + (i + sg) * GP;
+          switch (r.rem) {
+            case 0: grad_row<S, 0, NWT>(Fr, Gr, acc); break;
+            case 1: grad_row<S, 1, NWT>(Fr, Gr, acc); break;
+            case 2: grad_row<S, 2, NWT>(Fr, Gr, acc); break;
+            default: grad_row<S, 3, NWT>(Fr, Gr, acc); break;
+          }
+        }
+        // the warp's 32 rows by a shuffle tree, then the pair's two warps in order
+        float* pt = part[round & 1][warp];
+#pragma unroll
+        for (int up = 0; up < S; ++up) {
+          float v = acc[up];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) pt[up] = v;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&pbar[pair]));  // releases pt
+        if (!mbar_wait_bounded(smem_addr(&pbar[pair]), (uint32_t)(round & 1), &abort_flag,
+                               kPcWaitNs)) {
+          if (lane == 0) {
+            abort_flag = 1;
+            if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
+          }
+          return;
+        }
+        if ((warp & 1) == 0 && lane < S && sg < r.Ssig && lane < r.Sups) {
+          const float v = part[round & 1][warp][lane] + part[round & 1][warp + 1][lane];
+          float* o = dA + (size_t)(Nx * sg + r.rho) * Kt + (Ny * lane + r.tau);
+          *o = tl == 0 ? v : *o + v;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_addr(&empty[s]));  // this warp is done with stage s
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(&fempty));  // ... and with the tile's F
+  }
+}
+
 // The same sum for DB depths of one cut-out size that read the same input
 // image (the backprojections): each staged subgrid of the shared image feeds
 // the DB depths' weights, so staging is paid once per DB depths.  Block: one
@@ -1452,6 +1623,21 @@ int launch_grad_t(const PcArgs& a, dim3 grid, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
+template <int S>
+int launch_grad_pipe(const PcArgs& a, dim3 grid, cudaStream_t st) {
+  using Gm = GradGeom<S, true>;
+  const size_t smem = sizeof(float) * (kGrI * Gm::FP + kGrStages * Gm::GB) + 128;
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_phase_grad_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return -6;
+    attr_set = true;
+  }
+  k_phase_grad_pipe<S><<<grid, kPcPipeThreads, smem, st>>>(a);
+  return cudaGetLastError() == cudaSuccess ? 0 : -6;
+}
+
 // With phase planes of f (pf) and dg (pg): tensor maps for the F box
 // (kGrI rows x FP columns) and the G boxes (GR rows x GP columns).
 template <int S>
@@ -1460,6 +1646,7 @@ int launch_grad(PcArgs& a, const Planes* pf, const Planes* pg, dim3 grid, cudaSt
     using Gm = GradGeom<S, true>;
     if (planes_map(*pf, Gm::FP, kGrI, &a.tmap) || planes_map(*pg, Gm::GP, Gm::GR, &a.tmap2))
       return -6;
+    if (pipe_enabled()) return launch_grad_pipe<(S <= kPcTmaMaxS ? S : 3)>(a, grid, st);
     return launch_grad_t<S, (S <= kPcTmaMaxS)>(a, grid, st);
   }
   return launch_grad_t<S, false>(a, grid, st);
