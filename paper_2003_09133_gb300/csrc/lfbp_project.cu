@@ -420,7 +420,7 @@ constexpr int kPcPipeThreads = kPcThreads + 32;  // 8 consumer warps + 1 produce
 // DB = 1: one depth per block (grid.y), or all depths summed (sum_depths);
 // DB > 1: DB depths of one cut-out size reading one shared image, each staged
 // subgrid feeding all DB depths' weights (the backprojections).
-template <int S, int RI, int DB>
+template <int S, int RI, int DB, int NST = kPcStages>
 __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid_constant__ PcArgs a) {
   constexpr int TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;
@@ -429,10 +429,10 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
   constexpr int ICP = PcBox<S>::BX;
   constexpr int IB = (IR * ICP + 31) & ~31;
   constexpr int NW = DB * S * S4;  // weights per stage
-  __shared__ __align__(128) float I_s[kPcStages][IB];
-  __shared__ __align__(16) float w_s[kPcStages][NW];
-  __shared__ int rem_s[kPcStages];
-  __shared__ __align__(8) uint64_t full[kPcStages], empty[kPcStages];
+  __shared__ __align__(128) float I_s[NST][IB];
+  __shared__ __align__(16) float w_s[NST][NW];
+  __shared__ int rem_s[NST];
+  __shared__ __align__(8) uint64_t full[NST], empty[NST];
   __shared__ int abort_flag;
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   int t = blockIdx.x;
@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
   int nsub = 0;
   for (int d = d_lo; d < d_hi; ++d) nsub += min(Nx, a.d[d].Ks) * min(Ny, a.d[d].Kt);
   if (tid == 0) {
-    for (int s = 0; s < kPcStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(smem_addr(&full[s]), 33);  // 32 copy-completion arrivals + lane 0's release
       mbar_init(smem_addr(&empty[s]), 8);
     }
@@ -466,9 +466,9 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
     pc_sub_depth(c, d_lo, a.d[d_lo].Ks, a.d[d_lo].Kt, px, py, Nx, Ny);
     int issued = 0;
     for (int k = 0; k < nsub; ++k) {
-      const int s = k % kPcStages;
-      if (k >= kPcStages &&
-          !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((k / kPcStages - 1) & 1), &abort_flag,
+      const int s = k % NST;
+      if (k >= NST &&
+          !mbar_wait_bounded(smem_addr(&empty[s]), (uint32_t)((k / NST - 1) & 1), &abort_flag,
                              kPcWaitNs)) {
         if (lane == 0) {
           abort_flag = 1;
@@ -504,8 +504,8 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
     // nothing of this CTA may still be landing when it exits: wait for the
     // stages still in flight (already complete unless the consumers gave up)
     if (lane == 0)
-      for (int j = issued - 1; j >= 0 && j >= issued - kPcStages; --j)
-        mbar_wait_bounded(smem_addr(&full[j % kPcStages]), (uint32_t)((j / kPcStages) & 1), nullptr,
+      for (int j = issued - 1; j >= 0 && j >= issued - NST; --j)
+        mbar_wait_bounded(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1), nullptr,
                           kPcWaitNs);
     cp_async_wait<0>();
     return;
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
 #pragma unroll
     for (int i = 0; i < RH; ++i) acc[d][i][0] = acc[d][i][1] = acc[d][i][2] = acc[d][i][3] = 0.f;
   for (int k = 0; k < nsub; ++k) {
-    const int s = k % kPcStages;
-    if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)((k / kPcStages) & 1), &abort_flag,
+    const int s = k % NST;
+    if (!mbar_wait_bounded(smem_addr(&full[s]), (uint32_t)((k / NST) & 1), &abort_flag,
                            kPcWaitNs)) {
       if (lane == 0) {
         abort_flag = 1;
@@ -1321,6 +1321,7 @@ namespace {
 constexpr int kPcSizes[] = {3, 5, 7, 9, 11, 13, 15};  // kernel instances (sub-kernel extent S)
 
 constexpr int kPcTmaMaxS = 9;  // TMA path instances: S <= 9 (larger cut-outs are rare)
+constexpr bool kPcTallS3 = true;  // S = 3 forward/one-depth launches: 8 rows per thread
 
 // Phase planes of the TMA path (see TMA staging above): block = one plane row
 // (z, rx, ry, i); threads along j.  Writes are coalesced; the reads, Ny apart,
@@ -1443,12 +1444,18 @@ int planes_map(const Planes& pl, int BX, int IR, CUtensorMap* map) {
 }
 
 template <int S, int RI>
-int launch_pc_ri(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+int launch_pc_ri(PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
+  // output tiles of 8*RI rows x kPcTJ columns per phase
+  a.nTI = ((a.Wx + a.Nx - 1) / a.Nx + 8 * RI - 1) / (8 * RI);
+  a.nTJ = ((a.Wy + a.Ny - 1) / a.Ny + kPcTJ - 1) / kPcTJ;
+  const long long nblocks = (long long)a.Nx * a.Ny * a.nTI * a.nTJ;
+  if (nblocks > 0x7fffffffLL) return -1;
   const dim3 grid((unsigned)nblocks, (unsigned)ny);
   if (S <= kPcTmaMaxS && pl) {
     if (planes_map(*pl, PcBox<S>::BX, 8 * RI + S - 1, &a.tmap)) return -6;
-    if (pipe_enabled())
-      k_phase_conv_pipe<(S <= kPcTmaMaxS ? S : 3), RI, 1><<<grid, kPcPipeThreads, 0, st>>>(a);
+    if (pipe_enabled())  // eight output rows per thread: two stages fit the static limit
+      k_phase_conv_pipe<(S <= kPcTmaMaxS ? S : 3), RI, 1, (RI >= 8 ? 2 : kPcStages)>
+          <<<grid, kPcPipeThreads, 0, st>>>(a);
     else
       k_phase_conv<S, RI, (S <= kPcTmaMaxS)><<<grid, kPcThreads, 0, st>>>(a);
   } else {
@@ -1458,21 +1465,24 @@ int launch_pc_ri(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t 
 }
 
 template <int S>
-int launch_pc(PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
-  // depth sums run one block per output tile: half-height tiles for more blocks
-  return a.sum_depths ? launch_pc_ri<S, 2>(a, pl, nblocks, ny, st)
-                      : launch_pc_ri<S, 4>(a, pl, nblocks, ny, st);
+int launch_pc(PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
+  // depth sums run one block per output tile: half-height tiles for more
+  // blocks; the smallest cut-outs take tall tiles (more products per staged
+  // sub-problem for each thread)
+  if (a.sum_depths) return launch_pc_ri<S, 2>(a, pl, ny, st);
+  if constexpr (S <= 3 && kPcTallS3) return launch_pc_ri<S, 8>(a, pl, ny, st);
+  return launch_pc_ri<S, 4>(a, pl, ny, st);
 }
 
-int launch_pc_size(int S, PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+int launch_pc_size(int S, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
   switch (S) {
-    case 3: return launch_pc<3>(a, pl, nblocks, ny, st);
-    case 5: return launch_pc<5>(a, pl, nblocks, ny, st);
-    case 7: return launch_pc<7>(a, pl, nblocks, ny, st);
-    case 9: return launch_pc<9>(a, pl, nblocks, ny, st);
-    case 11: return launch_pc<11>(a, pl, nblocks, ny, st);
-    case 13: return launch_pc<13>(a, pl, nblocks, ny, st);
-    default: return launch_pc<15>(a, pl, nblocks, ny, st);
+    case 3: return launch_pc<3>(a, pl, ny, st);
+    case 5: return launch_pc<5>(a, pl, ny, st);
+    case 7: return launch_pc<7>(a, pl, ny, st);
+    case 9: return launch_pc<9>(a, pl, ny, st);
+    case 11: return launch_pc<11>(a, pl, ny, st);
+    case 13: return launch_pc<13>(a, pl, ny, st);
+    default: return launch_pc<15>(a, pl, ny, st);
   }
 }
 
@@ -1491,7 +1501,12 @@ int launch_md(PcArgs& a, const Planes* pl, dim3 grid, cudaStream_t st) {
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
-int launch_pc_md(int S, PcArgs& a, const Planes* pl, int nblocks, int ny, cudaStream_t st) {
+int launch_pc_md(int S, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
+  // output tiles of 32 rows x kPcTJ columns per phase
+  a.nTI = ((a.Wx + a.Nx - 1) / a.Nx + 31) / 32;
+  a.nTJ = ((a.Wy + a.Ny - 1) / a.Ny + kPcTJ - 1) / kPcTJ;
+  const long long nblocks = (long long)a.Nx * a.Ny * a.nTI * a.nTJ;
+  if (nblocks > 0x7fffffffLL) return -1;
   const dim3 grid((unsigned)nblocks, (unsigned)ny);
   switch (S) {  // small cut-outs only: there staging dominates one depth's work
     case 3: return launch_md<3>(a, pl, grid, st);
@@ -1548,13 +1563,10 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   a.Ny = Ny;
   a.Wx = Wx;
   a.Wy = Wy;
-  const int TI = sum_depths ? 16 : 32;  // 8 warps x 2 or 4 rows (launch_pc)
-  a.nTI = (nI + TI - 1) / TI;
-  a.nTJ = (nJ + kPcTJ - 1) / kPcTJ;
   a.mapped = mapped;
   a.sum_depths = sum_depths;
-  const long long nblocks = (long long)Nx * Ny * a.nTI * a.nTJ;
-  if (nblocks > 0x7fffffffLL) return -1;
+  // (each launcher sets the output tiling of its kernel: nTI, nTJ)
+  if ((long long)Nx * Ny * ((nI + 15) / 16) * ((nJ + kPcTJ - 1) / kPcTJ) > 0x7fffffffLL) return -1;
   // depths that read one shared image (backprojections) in groups of one
   // cut-out size: several depths per block (k_phase_conv_md)
   std::vector<char> done(Nz, 0);
@@ -1578,7 +1590,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         }
         a.ndepth = n;
         a.epi = epi;
-        const int rc = launch_pc_md(S, a, pl, (int)nblocks, (n + kPcDB - 1) / kPcDB, st);
+        const int rc = launch_pc_md(S, a, pl, (n + kPcDB - 1) / kPcDB, st);
         if (rc) return rc;
       }
     }
@@ -1599,7 +1611,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         a.ndepth = n;
         // summed depths: the first launch stores (or applies epi), later ones add
         a.epi = sum_depths ? (first ? epi : kEpiAccumulate) : epi;
-        const int rc = launch_pc_size(S, a, pl, (int)nblocks, sum_depths ? 1 : n, st);
+        const int rc = launch_pc_size(S, a, pl, sum_depths ? 1 : n, st);
         if (rc) return rc;
         first = false;
         n = 0;
