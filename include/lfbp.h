@@ -294,9 +294,10 @@ int lfbp_rl_normaliser(lfbp_plan p, const void* dH, const void* dHp, int Wx, int
  * Tests of the error paths: the environment variable LFBP_FAULT (read at each
  * call) injects a failure -- "plan" (plan creation returns LFBP_ERR_NOMEM),
  * "alloc" (building a batch's work list returns LFBP_ERR_NOMEM), "graph" (its
- * graph instantiation returns LFBP_ERR_CUDA) or "stall" (persistent launches
- * issue no copies, so their bounded waits run out and this call returns
- * LFBP_ERR_TIMEOUT about 2 s later).  Unset in normal use.
+ * graph instantiation returns LFBP_ERR_CUDA) or "stall" (persistent launches,
+ * and the TMA copies of the projector kernels, are not issued, so their
+ * bounded waits run out and this call returns LFBP_ERR_TIMEOUT some seconds
+ * later).  Unset in normal use.
  */
 int lfbp_sync_status(void* cuda_stream);
 

@@ -150,6 +150,8 @@ struct PcArgs {
   CUtensorMap tmap;   // phase planes of `in` (TMA path): dims {Pjp, Pi, planes}
   CUtensorMap tmap2;  // phase planes of `g` (the gradient's dL/dg, TMA path)
   int* status;       // device status word (a wait that ran out: LFBP_ERR_TIMEOUT)
+  int fault;         // 1 (LFBP_FAULT=stall, tests of the timeout path): TMA copies
+                     // register their bytes on the barrier but are not issued
   const float* A;
   const float* in;
   long long in_zstride;
@@ -317,8 +319,9 @@ __device__ __forceinline__ void pc_tma_stage(const PcArgs& a, const PcSub& c, in
   fence_proxy_async_smem();  // the buffer's previous (generic) reads come first
   const uint32_t b = smem_addr(bar);
   mbar_expect_tx(b, bytes);
-  tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
-              (zplane0 + c.ar) * a.Ny + c.br, b);
+  if (!a.fault)
+    tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                (zplane0 + c.ar) * a.Ny + c.br, b);
   mbar_arrive(b);
 }
 
@@ -330,8 +333,9 @@ __device__ __forceinline__ void pc_tma_stage_noarrive(const PcArgs& a, const PcS
   fence_proxy_async_smem();
   const uint32_t b = smem_addr(bar);
   mbar_expect_tx(b, bytes);
-  tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
-              (zplane0 + c.ar) * a.Ny + c.br, b);
+  if (!a.fault)
+    tma_load_3d(smem_addr(dst), &a.tmap, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                (zplane0 + c.ar) * a.Ny + c.br, b);
 }
 
 // Products of one staged sub-problem: rows r of the subgrid tile (pitch PITCH,
@@ -502,8 +506,9 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_conv_pipe(const __grid
         pc_sub_depth(c, c.di + 1, a.d[c.di + 1].Ks, a.d[c.di + 1].Kt, px, py, Nx, Ny);
     }
     // nothing of this CTA may still be landing when it exits: wait for the
-    // stages still in flight (already complete unless the consumers gave up)
-    if (lane == 0)
+    // stages still in flight (already complete unless the consumers gave up;
+    // none were issued under the stall injection)
+    if (lane == 0 && !a.fault)
       for (int j = issued - 1; j >= 0 && j >= issued - NST; --j)
         mbar_wait_bounded(smem_addr(&full[j % NST]), (uint32_t)((j / NST) & 1), nullptr,
                           kPcWaitNs);
@@ -792,8 +797,9 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
         fence_proxy_async_smem();
         const uint32_t b = smem_addr(&bars[buf]);
         mbar_expect_tx(b, (uint32_t)(GR * GP * sizeof(float)));
-        tma_load_3d(smem_addr(dst), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
-                    (dd.z * Nx + c.ar) * Ny + c.br, b);
+        if (!a.fault)
+          tma_load_3d(smem_addr(dst), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                      (dd.z * Nx + c.ar) * Ny + c.br, b);
         mbar_arrive(b);
       }
     } else {
@@ -812,7 +818,7 @@ __global__ void __launch_bounds__(256) k_phase_grad(const __grid_constant__ PcAr
           fence_proxy_async_smem();
           const uint32_t b = smem_addr(&bars[2]);
           mbar_expect_tx(b, (uint32_t)(kGrI * FP * sizeof(float)));
-          tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, b);
+          if (!a.fault) tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, b);
           mbar_arrive(b);
         }
       } else {
@@ -961,7 +967,7 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
           break;
         fence_proxy_async_smem();
         mbar_expect_tx(smem_addr(&ffull), (uint32_t)(kGrI * FP * sizeof(float)));
-        tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, smem_addr(&ffull));
+        if (!a.fault) tma_load_3d(smem_addr(F_s), &a.tmap, j0, i0, p * Ny + q, smem_addr(&ffull));
         mbar_arrive(smem_addr(&ffull));
         ++tiles;
         PcSub c;
@@ -977,8 +983,9 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
           fence_proxy_async_smem();
           const uint32_t b = smem_addr(&full[s]);
           mbar_expect_tx(b, (uint32_t)(GR * GP * sizeof(float)));
-          tma_load_3d(smem_addr(G_s + s * GB), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
-                      (dd.z * Nx + c.ar) * Ny + c.br, b);
+          if (!a.fault)
+            tma_load_3d(smem_addr(G_s + s * GB), &a.tmap2, j0 + c.qy - (c.qy & 3), i0 + c.qx,
+                        (dd.z * Nx + c.ar) * Ny + c.br, b);
           mbar_arrive(b);  // releases rec[s]
           ++issued;
           pc_sub_next_phase(c, p, q, Nx, Ny);
@@ -988,11 +995,12 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
         abort_flag = 1;
         if (a.status) atomicCAS(a.status, 0, kStatusTimeout);
       }
-      // nothing of this CTA may still be landing when it exits
-      for (int j = issued - 1; j >= 0 && j >= issued - kGrStages; --j)
+      // nothing of this CTA may still be landing when it exits (none were
+      // issued under the stall injection)
+      for (int j = issued - 1; !a.fault && j >= 0 && j >= issued - kGrStages; --j)
         mbar_wait_bounded(smem_addr(&full[j % kGrStages]), (uint32_t)((j / kGrStages) & 1), nullptr,
                           kPcWaitNs);
-      if (tiles > 0)
+      if (tiles > 0 && !a.fault)
         mbar_wait_bounded(smem_addr(&ffull), (uint32_t)((tiles - 1) & 1), nullptr, kPcWaitNs);
     }
     return;
@@ -1394,6 +1402,14 @@ struct Planes {
   int Pi = 0, Pjp = 0, nplanes = 0;
 };
 
+// LFBP_FAULT=stall: the TMA-path kernels register their copies' bytes without
+// issuing them, so every wait on those copies runs out (tests of the timeout
+// path; the cp.async path is not affected).
+int stall_injected() {
+  const char* s = std::getenv("LFBP_FAULT");
+  return s && !std::strcmp(s, "stall");
+}
+
 bool pipe_enabled() {
   const char* s = std::getenv("LFBP_PROJ_PIPE");
   return !(s && s[0] == '0');
@@ -1552,6 +1568,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   PcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.status = status;
+  a.fault = stall_injected();
   a.A = A;
   a.in = in;
   a.in_zstride = in_zstride;
@@ -1697,6 +1714,7 @@ int launch_phase_grad(const float* f, const float* dg, int Nx, int Ny, int Nz, c
   PcArgs a;
   std::memset(&a, 0, sizeof(a));
   a.status = status;
+  a.fault = stall_injected();
   a.in = f;
   a.g = dg;
   a.out_zstride = (long long)Wx * Wy;

@@ -86,3 +86,37 @@ def test_injected_plan_failure_through_the_binding(lf, monkeypatch):
     with pytest.raises(lf.LfbpError) as ei:
         lf.Plan(*SHAPE, torch.float32)
     assert ei.value.code == -8
+
+
+@pytest.mark.parametrize("pipe", ["1", "0"])
+def test_projector_tma_waits_time_out_and_recover(lf, monkeypatch, pipe):
+    """The projectors' TMA-path waits are bounded too.  Under LFBP_FAULT=stall
+    their TMA copies register their bytes without being issued, so the waits
+    on those copies run out.  The pipelined kernels (producer, consumers,
+    pair barriers) and the barrier kernels (LFBP_PROJ_PIPE=0) both end with
+    LFBP_ERR_TIMEOUT, and the next call without the injection is correct."""
+    Nx, Ny, Ks, W = 3, 3, [9, 3], 12
+    plan = lf.Plan(Nx, Ny, Ks, Ks, torch.float32)
+    rng = np.random.default_rng(33)
+    H = rng.uniform(0, 1, plan.elems).astype(np.float32)
+    f = rng.uniform(0.1, 1, (W, W)).astype(np.float32)
+    dg = rng.uniform(-1, 1, (len(Ks), W, W)).astype(np.float32)
+    Hd, fd, dgd = (torch.from_numpy(x).cuda() for x in (H, f, dg))
+    monkeypatch.setenv("LFBP_PROJ_PIPE", pipe)
+    lf.sync_status()
+    for call in (lambda: lf.backproject_volume_from_h(plan, Hd, fd),
+                 lambda: lf.backproject_volume_grad(plan, fd, dgd)):
+        monkeypatch.setenv("LFBP_FAULT", "stall")
+        t0 = time.monotonic()
+        call()
+        with pytest.raises(lf.LfbpError) as ei:
+            lf.sync_status()
+        assert ei.value.code == -7
+        assert time.monotonic() - t0 <= 60.0
+        monkeypatch.delenv("LFBP_FAULT")
+    Hp = oracle.transpose(H, Nx, Ny, Ks, Ks)
+    want = oracle.backproject(Hp, Nx, Ny, Ks, Ks, f)
+    got = lf.backproject_volume_from_h(plan, Hd, fd).cpu().numpy()
+    lf.sync_status()
+    n2 = (np.array([a * a for a in Ks]) * 2.0 ** -23)[:, None, None]
+    assert (np.abs(got - want) <= n2 * np.abs(want) + 1e-30).all()
