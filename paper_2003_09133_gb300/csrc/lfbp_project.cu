@@ -1641,13 +1641,10 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
 namespace {
 template <int S, bool kTma>
 int launch_grad_t(const PcArgs& a, dim3 grid, cudaStream_t st) {
-  static bool attr_set = false;  // per instance; setting it twice is harmless
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_phase_grad<S, kTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)GradGeom<S, kTma>::smem) != cudaSuccess)
-      return -6;
-    attr_set = true;
-  }
+  // (set at every launch: the attribute belongs to the current device)
+  if (cudaFuncSetAttribute(k_phase_grad<S, kTma>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)GradGeom<S, kTma>::smem) != cudaSuccess)
+    return -6;
   k_phase_grad<S, kTma><<<grid, 256, GradGeom<S, kTma>::smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
@@ -1656,13 +1653,9 @@ template <int S>
 int launch_grad_pipe(const PcArgs& a, dim3 grid, cudaStream_t st) {
   using Gm = GradGeom<S, true>;
   const size_t smem = sizeof(float) * (kGrI * Gm::FP + kGrStages * Gm::GB) + 128;
-  static bool attr_set = false;
-  if (!attr_set) {
-    if (cudaFuncSetAttribute(k_phase_grad_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return -6;
-    attr_set = true;
-  }
+  if (cudaFuncSetAttribute(k_phase_grad_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
+    return -6;
   k_phase_grad_pipe<S><<<grid, kPcPipeThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
