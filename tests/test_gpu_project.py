@@ -39,6 +39,8 @@ CASES = [  # Nx, Ny, Ks, Kt, Wx, Wy
     (5, 5, [15, 5, 25], [15, 5, 25], 37, 40),
     (1, 1, [3], [5], 9, 7),
     (11, 11, [33, 99], [33, 99], 66, 77),
+    (95, 55, [95], [165], 190, 110),   # the R29 elementary cell (Sec. 5), two cells per axis
+    (31, 31, [249], [249], 62, 93),     # a Table 1 size: K not a multiple of N (S = 9)
 ]
 
 
