@@ -373,3 +373,24 @@ def test_centred_cropping_commutes_with_the_map(Nx, Ny, K, Kt, m, mt):
     # the central entry alone: H'[p, q, 0, 0] = H[p, q, 0, 0] for a 1 x 1 cut-out
     c = np.ascontiguousarray(H[:, :, (K - 1) // 2:(K + 1) // 2, (Kt - 1) // 2:(Kt + 1) // 2])
     np.testing.assert_array_equal(oracle.transpose(c.reshape(-1), Nx, Ny, [1], [1]), c.reshape(-1))
+
+
+@pytest.mark.parametrize("fname,N,K", [("eqs4to9_nx3_ns4_even.txt", 3, 4),
+                                       ("eqs4to9_nx3_ns6_even.txt", 3, 6)])
+def test_golden_even_cutout_literal_equations(golden_dir, fname, N, K):
+    """Even n_s (reading A2): the literal Eqs. (4)-(9) drop s = n_s and never
+    write s' = n_s.  The oracle's paper-window evaluation must give the hand
+    evaluations in tests/golden/ (n_s = 4: no offset; n_s = 6: offset 1)
+    entry by entry."""
+    rows = {}
+    with open(os.path.join(golden_dir, fname)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            rows[(int(tok[0]), int(tok[1]))] = None if tok[2] == "-" else (int(tok[2]), int(tok[3]))
+    assert len(rows) == N * K
+    pw = oracle.paper_window(_tagged_1d(N, K), N, 1, [K], [1])
+    for (p, u), src in rows.items():
+        assert pw[p * K + u] == (0 if src is None else _tag(*src)), (p, u)
