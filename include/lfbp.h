@@ -77,10 +77,14 @@ int lfbp_plan_create(lfbp_plan* out, int Nnum, int Nz, const int* Kz, lfbp_dtype
 /*
  * General cell (Sec. 4: the x and y axes are mapped independently, so the
  * cell may be non-square, n_x != n_y, as for hexagonal MLAs): Nx x Ny source
- * positions, per-depth cut-outs of Ks[z] x Kt[z] pixels.  All odd and >= 1;
- * Nx, Ny <= 1023 and Ks, Kt <= 16383.  Even cut-out sizes are rejected
- * (LFBP_ERR_BAD_SHAPE): Eq. (8) then drops one pixel row and the map is not
- * a permutation.
+ * positions, per-depth cut-outs of Ks[z] x Kt[z] pixels.  Nx, Ny odd, all
+ * >= 1; Nx, Ny <= 1023 and Ks, Kt <= 16383.  Cut-outs must be odd for
+ * LFBP_MAP_TRANSPOSE (LFBP_ERR_BAD_SHAPE otherwise).  In LFBP_MAP_PAPER_WINDOW
+ * mode they may be even: Eq. (8) then drops one pixel row (s = n_s) and never
+ * writes s' = n_s, and the map is the literal Eqs. (4)-(9) loop, a partial
+ * injection.  A plan with an even cut-out is taken by lfbp_backproject_array
+ * and lfbp_adjoint only (element by element, not tiled); the other entry
+ * points reject it with LFBP_ERR_BAD_SHAPE.
  */
 int lfbp_plan_create2(lfbp_plan* out, int Nx, int Ny, int Nz, const int* Ks, const int* Kt,
                       lfbp_dtype dt, lfbp_mode mode);

@@ -255,6 +255,9 @@ struct lfbp_plan_s {
   int es = 4;
   std::vector<size_t> off;  // Nz + 1
   unsigned long long uid = 0;
+  // an even cut-out (paper-window mode only): the map is the literal
+  // Eqs. (4)-(9) loop, run by the element kernel of lfbp_window.cu
+  bool literal = false;
   // per-depth tilings by tile-size target (built lazily; entries stay put)
   std::mutex mu;
   std::map<int, std::vector<lfbp::DepthTiling>> tilings;
@@ -406,7 +409,26 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
 int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st) {
   int rc = check_buffers(p, in, out);
   if (rc) return rc;
+  if (p->literal) {  // even cut-outs: the literal loop, depth by depth (mode 2: its adjoint)
+    for (int z = 0; z < p->Nz; ++z) {
+      const size_t o = p->off[z] * (size_t)p->es;
+      if (launch_window_literal((const unsigned char*)in + o, (unsigned char*)out + o, p->es,
+                                p->Nx, p->Ny, p->Ks[z], p->Kt[z], mode == 2 ? 1 : 0, st))
+        return fail(LFBP_ERR_CUDA, "k_window_literal launch failed");
+    }
+    return LFBP_OK;
+  }
   return launch_plain(p, (const unsigned char*)in, (unsigned char*)out, mode, 0, p->Nz, st);
+}
+
+// Entry points other than lfbp_backproject_array and lfbp_adjoint take odd
+// cut-outs only.
+int reject_literal(int n, const lfbp_plan* plans) {
+  for (int i = 0; i < n; ++i)
+    if (plans[i] && plans[i]->literal)
+      return fail(LFBP_ERR_BAD_SHAPE,
+                  "even cut-outs are taken by lfbp_backproject_array and lfbp_adjoint only");
+  return LFBP_OK;
 }
 
 // --------------------------------------------------- host-to-host pipeline --
@@ -449,6 +471,7 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
              cudaStream_t st) {
   int rc = check_buffers(p, dH, dHp);
   if (rc) return rc;
+  if ((rc = reject_literal(1, &p))) return rc;
   const size_t bytes = p->off.back() * (size_t)p->es;
   if (bytes == 0) return LFBP_OK;
   if (!H_host || !Hp_host) return fail(LFBP_ERR_NULL, "host buffer pointer is NULL");
@@ -640,6 +663,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     int rc = check_buffers(plans[i], in[i], out[i]);
     if (rc) return rc;
   }
+  if (int rc = reject_literal(n, plans)) return rc;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       const size_t bi = plans[i]->off.back() * plans[i]->es;
@@ -764,6 +788,7 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     int rc = check_buffers(plans[i], in[i], out[i]);
     if (rc) return rc;
   }
+  if (int rc = reject_literal(n, plans)) return rc;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       const size_t bi = plans[i]->off.back() * plans[i]->es;
@@ -976,6 +1001,7 @@ int check_projector(lfbp_plan p, const void* a, const void* b, const void* out, 
   if (Wx < 1 || Wy < 1) return fail(LFBP_ERR_BAD_SHAPE, "sensor must be at least 1 x 1");
   for (int z = 0; z < p->Nz; ++z)
     if (p->Kt[z] > 3072) return fail(LFBP_ERR_BAD_SHAPE, "projectors need Kt <= 3072");
+  if (p->literal) return fail(LFBP_ERR_BAD_SHAPE, "projectors need odd cut-outs");
   if ((p->Nz > 0 && !a) || !b || !out) return fail(LFBP_ERR_NULL, "buffer pointer is NULL");
   if (((uintptr_t)a | (uintptr_t)b | (uintptr_t)out) & 3)
     return fail(LFBP_ERR_ALIGN, "buffers must be 4-byte aligned");
@@ -1007,8 +1033,16 @@ int make_plan(lfbp_plan* out, int Nx, int Ny, int Nz, const int* Ks, const int* 
   p->off.push_back(0);
   for (int z = 0; z < Nz; ++z) {
     const int ks = Ks[z], kt = Kt[z];
-    if (ks < 1 || kt < 1 || ks % 2 == 0 || kt % 2 == 0)
-      return fail(LFBP_ERR_BAD_SHAPE, "every Ks and Kt must be odd and >= 1");
+    if (ks < 1 || kt < 1) return fail(LFBP_ERR_BAD_SHAPE, "every Ks and Kt must be >= 1");
+    if (ks % 2 == 0 || kt % 2 == 0) {
+      // Eq. 8 with even n_s is a partial map (reading A2): only the literal
+      // paper window defines it
+      if (mode != LFBP_MAP_PAPER_WINDOW)
+        return fail(LFBP_ERR_BAD_SHAPE,
+                    "even Ks or Kt: the transpose needs odd cut-outs (use LFBP_MAP_PAPER_WINDOW "
+                    "for the literal Eq. 8)");
+      p->literal = true;
+    }
     if (ks > 16383 || kt > 16383) return fail(LFBP_ERR_BAD_SHAPE, "Ks and Kt must be <= 16383");
     p->Ks.push_back(ks);
     p->Kt.push_back(kt);

@@ -294,3 +294,45 @@ def test_table1_shapes_full_size(lf, K, Nx, Ny):
     _assert_same_bits(lf.backproject_batched([plan], [H])[0], want, "batched")
     _assert_same_bits(lf.backproject_array(plan, H), want, "plain")
     lf.sync_status()
+
+
+EVEN_SHAPES = [  # Nx, Ny, Ks, Kt: the literal Eq. 8 with even n_s / n_t (paper-window mode)
+    (3, 1, [4], [1]),
+    (3, 3, [6, 4], [4, 9]),
+    (5, 3, [14, 15], [15, 6]),
+    (1, 1, [2, 8], [6, 3]),
+    (19, 19, [76, 57], [76, 58]),
+    (95, 55, [96], [110]),
+]
+
+
+def _window_sources(Nx, Ny, Ks, Kt):
+    """For every H' entry the 1-based H index the literal loop copies into it
+    (0: never written), from the oracle run on an index array."""
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    idx = np.arange(1, n + 1, dtype=np.int64)
+    return oracle.paper_window(idx, Nx, Ny, Ks, Kt)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("shape", EVEN_SHAPES, ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}x{s[3][0]}")
+def test_even_cutouts_literal_window(lf, shape, dtype):
+    """Even cut-outs, literal Eqs. (4)-(9): H' bit for bit against the oracle's
+    paper-window evaluation, and the adjoint moves each written entry back to
+    its source (zero elsewhere)."""
+    Nx, Ny, Ks, Kt = shape
+    plan = lf.Plan(Nx, Ny, Ks, Kt, dtype, mode=lf.MAP_PAPER_WINDOW)
+    H = _random_bits(plan.elems, dtype, 15)
+    Hn = H.cpu().numpy()
+    _assert_same_bits(lf.backproject_array(plan, H), oracle.paper_window(Hn, Nx, Ny, Ks, Kt),
+                      "literal window")
+    src = _window_sources(Nx, Ny, Ks, Kt)
+    dHp = _random_bits(plan.elems, dtype, 16)
+    d = dHp.cpu().numpy()
+    want = np.zeros_like(d)
+    w = src > 0
+    want[src[w] - 1] = d[w]
+    _assert_same_bits(lf.adjoint(plan, dHp), want, "literal window adjoint")
+    with pytest.raises(lf.LfbpError):
+        lf.backproject_batched([plan], [H])
+    lf.sync_status()
