@@ -539,9 +539,25 @@ def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
     tb, _, _ = timed(lambda: lf.backproject_batched(pw, Hs, outs), steps, 3)
     tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(pw, Hs, outs)],
                      steps, 3)
-    return {"mode": "MAP_PAPER_WINDOW", "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
-            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
-            "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+    res = {"mode": "MAP_PAPER_WINDOW", "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
+           "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
+           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+    # even cut-outs (the literal Eq. 8): the same depths with every K one larger,
+    # plain entry point only (element-by-element kernel)
+    if len(specs) == 1:
+        s = specs[0]
+        ke, kte = [k + 1 for k in s.Ks], [k + 1 for k in s.Kt]
+        pe = lf.Plan(s.Nx, s.Ny, ke, kte, torch.float32, mode=lf.MAP_PAPER_WINDOW)
+        He = torch.empty(pe.elems, dtype=torch.float32, device="cuda").uniform_()
+        Oe = torch.empty_like(He)
+        te, _, _ = timed(lambda: lf.backproject_array(pe, He, Oe), steps, 3)
+        nbe = 2 * pe.elems * 4
+        res["even_K"] = {"K": "every highres K + 1", "bytes_per_step": nbe,
+                         "plain_GBps": round(world * nbe / (te * 1e-3) / 1e9, 1),
+                         "plain_ms": round(te, 4), "kernel": "k_window_literal"}
+        del He, Oe
+        torch.cuda.empty_cache()
+    return res
 
 
 # Table 1 of the paper: n_s = n_t, n_x, n_y and the paper's own time in seconds
