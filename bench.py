@@ -325,13 +325,20 @@ def _pick_specs(args):
     return specs
 
 
-def _config(args, specs):
+def _config(args, specs, world=1):
     import lfgen
     elems = sum(lfgen.array_elems(s) for s in specs)
-    return {"workload": _workload_desc(specs, args.dtype), "arrays": len(specs),
-            "elements_per_rank": elems, "form": "batched persistent (1 launch, CUDA graph)",
-            "l2": "inputs larger than L2 (no flush)" if elems * 2 > 129e6 else
-                  "L2 flushed between steps"}
+    cfg = {"workload": _workload_desc(specs, args.dtype), "arrays": len(specs),
+           "elements_per_rank": elems, "form": "batched persistent (1 launch, CUDA graph)",
+           "l2": "inputs larger than L2 (no flush)" if elems * 2 > 129e6 else
+                 "L2 flushed between steps"}
+    if args.scaling == "strong":
+        cfg["elements_per_rank"] = None
+        cfg["elements_per_job"] = elems
+        cfg["parallelism"] = f"depths split across {world} rank(s) (lfbp_plan_partition)"
+    else:
+        cfg["parallelism"] = f"{world} independent array(s), one per rank"
+    return cfg
 
 
 def run_ours(args):
@@ -343,16 +350,33 @@ def run_ours(args):
     world, rank, local = _dist()
     torch.cuda.set_device(local)
     lf.load()
-    specs = rank_specs(_pick_specs(args), rank)
+    strong = args.scaling == "strong"
+    # weak: every rank maps its own array (seeds offset per rank); strong: the
+    # ranks split the depths of one array (lfbp_plan_partition) and map their part
+    specs = _pick_specs(args) if strong else rank_specs(_pick_specs(args), rank)
     plans, Hs, outs = [], [], []
+    job_bytes = 0
     for s in specs:
         dt = _torch_dtype(args, s)
-        plans.append(lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, dt))
-        Hs.append(lfgen.generate(s, device="cuda").to(dt))
+        full = lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, dt)
+        H = lfgen.generate(s, device="cuda").to(dt)
+        job_bytes += 2 * H.numel() * H.element_size()
+        if strong:
+            z0, z1 = full.partition(world, rank)
+            if z1 <= z0:
+                continue
+            plans.append(full.sub_plan(z0, z1))
+            Hs.append(H[full.depth_offset(z0):full.depth_offset(z1)].clone())  # 16-byte aligned
+            del H
+        else:
+            plans.append(full)
+            Hs.append(H)
         outs.append(torch.empty_like(Hs[-1]))
     torch.cuda.synchronize()
     step_bytes = sum(2 * h.numel() * h.element_size() for h in Hs)
     step_elems = sum(h.numel() for h in Hs)
+    # whole-job bytes per step: every rank's own array (weak) or the one shared array (strong)
+    job_total = job_bytes if strong else world * step_bytes
     flush = None
     if step_bytes < 2 * 129e6:
         flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
@@ -413,20 +437,21 @@ def run_ours(args):
         n_e2e = max(3, min(args.steps, 20))
         t_e2e, _, _ = timed(step_e2e, n_e2e, 2)
         nbytes = sum(h.numel() * h.element_size() for h in Hs)
-        e2e = {"value": round(world * step_bytes / (t_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
+        e2e = {"value": round(job_total / (t_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": round(t_e2e, 3)}
         del hosts, host_out, dev_in
 
     peak, peak_kind = _peaks()
     achieved = step_bytes / (t_batched * 1e-3) / 1e9
-    value = aggregate_gbs(step_bytes, t_batched, world)
-    traffic = _traffic_record(args.workload, _dtype_name(args, specs))
+    value = job_total / (t_batched * 1e-3) / 1e9
+    traffic = None if strong else _traffic_record(args.workload, _dtype_name(args, specs))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batched, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": _dtype_name(args, specs), "data": "synthetic", "config": _config(args, specs),
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
+        "dtype": _dtype_name(args, specs), "data": "synthetic",
+        "config": _config(args, specs, world),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -435,17 +460,18 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": step_bytes},
         "pct_of_8TBps_spec": round(100 * achieved / SPEC_GBS, 2),
         "launch_shape": _tuned_desc(tuned) or "default (3 CTAs/SM, 32 KB tiles)",
-        "elements_per_s": round(world * step_elems / (t_batched * 1e-3), 1),
+        "elements_per_s": round(job_total * step_elems / step_bytes / (t_batched * 1e-3), 1)
+        if step_bytes else 0.0,
         "best_ms_per_step": round(best_batched, 4),
         "plain": {"ms_per_step": round(t_plain, 4),
-                  "value": round(world * step_bytes / (t_plain * 1e-3) / 1e9, 3),
+                  "value": round(job_total / (t_plain * 1e-3) / 1e9, 3),
                   "best_ms_per_step": round(best_plain, 4),
                   "launches_per_step": sum(p.Nz for p in plans), "kernel": "k_gather_depth"},
         "e2e": e2e,
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps if plans else 0,
         "clocks": clocks,
     }
-    if not args.no_extra and args.workload == "highres" and args.dtype in (None, "f32"):
+    if not args.no_extra and not strong and args.workload == "highres" and args.dtype in (None, "f32"):
         line["extra"] = _extra_forms(lf, plans, specs, Hs, outs, timed, args, world)
     if rank == 0 and not args.no_cpu_baseline:
         Hh = [h.cpu().numpy() for h in Hs]
@@ -692,6 +718,9 @@ def _rl_extra(lf, timed, steps):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="weak: every rank maps its own array; strong: the ranks split the "
+                         "depths of one array (lfbp_plan_partition)")
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")

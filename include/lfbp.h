@@ -99,6 +99,16 @@ size_t lfbp_plan_depth_offset(lfbp_plan p, int z);
 int lfbp_plan_esize(lfbp_plan p);
 
 /*
+ * Split the plan's depths into nparts contiguous ranges of about equal
+ * element counts (Sec. 4: the depths are independent), e.g. one per GPU:
+ * part `part` (0 <= part < nparts) is depths [*z0, *z1), possibly empty.
+ * Every boundary is the depth start nearest to its share; the ranges cover
+ * 0..Nz without overlap.  Host only.  LFBP_ERR_NULL / LFBP_ERR_INVALID on bad
+ * arguments.
+ */
+int lfbp_plan_partition(lfbp_plan p, int nparts, int part, int* z0, int* z1);
+
+/*
  * H -> H' with one kernel launch per depth (Sec. 4: the z-planes are
  * independent).  dH, dHp: device buffers of lfbp_plan_elems(p) elements,
  * 16-byte aligned, not overlapping (in-place is rejected with

@@ -33,6 +33,7 @@ SIGNATURES = {
     "lfbp_plan_elems": ([_P], _S),
     "lfbp_plan_depth_offset": ([_P, _I], _S),
     "lfbp_plan_esize": ([_P], _I),
+    "lfbp_plan_partition": ([_P, _I, _I, _P, _P], _I),
     "lfbp_backproject_array": ([_P, _P, _P, _P], _I),
     "lfbp_backproject_array_host": ([_P, _P, _P, _P, _P, _P], _I),
     "lfbp_backproject_batched": ([_I, _P, _P, _P, _P], _I),
@@ -148,6 +149,18 @@ class Plan:
 
     def depth_offset(self, z: int) -> int:
         return int(self._lib.lfbp_plan_depth_offset(self._h, int(z)))
+
+    def partition(self, nparts: int, part: int):
+        """Depth range [z0, z1) of part `part` of `nparts` (``lfbp_plan_partition``)."""
+        z0, z1 = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.lfbp_plan_partition(self._h, int(nparts), int(part), ctypes.byref(z0),
+                                             ctypes.byref(z1)), "lfbp_plan_partition")
+        return int(z0.value), int(z1.value)
+
+    def sub_plan(self, z0: int, z1: int) -> "Plan":
+        """A plan of depths z0 .. z1-1 alone; its arrays are the slice
+        [depth_offset(z0), depth_offset(z1)) of this plan's arrays."""
+        return Plan(self.Nx, self.Ny, self.Ks[z0:z1], self.Kt[z0:z1], self.dtype, self.mode)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -1103,6 +1104,27 @@ size_t lfbp_plan_depth_offset(lfbp_plan p, int z) {
 }
 
 int lfbp_plan_esize(lfbp_plan p) { return p ? p->es : 0; }
+
+int lfbp_plan_partition(lfbp_plan p, int nparts, int part, int* z0, int* z1) {
+  if (!p || !z0 || !z1) return fail(LFBP_ERR_NULL, "NULL argument");
+  if (nparts < 1 || part < 0 || part >= nparts) return fail(LFBP_ERR_INVALID, "part out of range");
+  // boundary k sits at the depth start nearest to k/nparts of the elements
+  // (non-decreasing in k: the targets grow and ties keep the first depth); the
+  // depths are independent (Sec. 4), so a part is any contiguous range
+  const double total = (double)p->off.back();
+  auto boundary = [&](int k) {
+    if (k <= 0) return 0;
+    if (k >= nparts) return p->Nz;
+    const double target = total * k / nparts;
+    int best = 0;
+    for (int z = 1; z <= p->Nz; ++z)
+      if (std::fabs((double)p->off[z] - target) < std::fabs((double)p->off[best] - target)) best = z;
+    return best;
+  };
+  *z0 = boundary(part);
+  *z1 = std::max(*z0, boundary(part + 1));
+  return LFBP_OK;
+}
 
 int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_stream) {
   if (!p) return fail(LFBP_ERR_NULL, "plan is NULL");

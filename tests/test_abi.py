@@ -184,3 +184,28 @@ def test_even_cutouts_need_the_paper_window(lib):
     assert b"even" in lib.lfbp_last_error()
     assert lib.lfbp_backproject_volume_from_h(h, A, B, 12, 12, 0x30000000, None) in (-1, -5)
     lib.lfbp_plan_destroy(h)
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 4, 8, 64])
+def test_plan_partition_covers_and_balances(lib, nparts):
+    """Contiguous depth ranges covering every depth once, each boundary at the
+    depth start nearest to its share of the elements (host only)."""
+    Ks = [15 * (3 + 2 * (abs(z - 25) // 5)) for z in range(51)]   # the mid workload's cut-outs
+    rc, h = _plan(lib, 15, 15, Ks, Ks)
+    assert rc == 0
+    off = [lib.lfbp_plan_depth_offset(h, z) for z in range(len(Ks) + 1)]
+    total = off[-1]
+    z0, z1 = ctypes.c_int(), ctypes.c_int()
+    prev = 0
+    for part in range(nparts):
+        assert lib.lfbp_plan_partition(h, nparts, part, ctypes.byref(z0), ctypes.byref(z1)) == 0
+        assert z0.value == prev and z1.value >= z0.value
+        if part + 1 < nparts:
+            target = total * (part + 1) / nparts
+            best = min(abs(o - target) for o in off)
+            assert abs(off[z1.value] - target) == best
+        prev = z1.value
+    assert prev == len(Ks)
+    assert lib.lfbp_plan_partition(h, 0, 0, ctypes.byref(z0), ctypes.byref(z1)) == -9
+    assert lib.lfbp_plan_partition(h, 2, 2, ctypes.byref(z0), ctypes.byref(z1)) == -9
+    lib.lfbp_plan_destroy(h)
