@@ -166,3 +166,100 @@ def test_rl_composition_slip_is_caught(kind):
     np.testing.assert_allclose(ok, want, rtol=1e-12)
     bad = _rl_variant(kind)(H, Hp, Nx, Ny, [K], [K], g, f).reshape(-1)
     assert not np.allclose(bad, want, rtol=1e-6)
+
+
+# ------------------------------------------------------- projector slips --
+
+PROJ_MUTATIONS = {
+    # forward model, Eq. (1): the cut-out flipped, or the wrong voxel's pattern
+    "forward_flip": ("long Sx = X + s - cs;                 /* pixel of entry s */",
+                     "long Sx = X - s + cs;"),
+    "forward_cell": ("int a = (int)(X % Nx), b = (int)(Y % Ny);",
+                     "int a = (int)((X + 1) % Nx), b = (int)(Y % Ny);"),
+    # backprojection: the window walked the wrong way, or the wrong pixel's slice
+    "backproject_window_sign": (
+        "                const double* win = Hp + off + ((size_t)p * Ny + q) * ks * kt;\n"
+        "                for (int u = 0; u < ks; ++u) {\n"
+        "                    long X = Sx + u - cs;",
+        "                const double* win = Hp + off + ((size_t)p * Ny + q) * ks * kt;\n"
+        "                for (int u = 0; u < ks; ++u) {\n"
+        "                    long X = Sx - u + cs;"),
+    "backproject_cell": ("                int p = (int)(Sx % Nx), q = (int)(Sy % Ny);\n"
+                         "                const double* win",
+                         "                int p = (int)(Sx % Nx), q = (int)((Sy + 1) % Ny);\n"
+                         "                const double* win"),
+    # gradient with respect to H': the voxel offset with the wrong sign
+    "grad_offset_sign": ("                for (long Sx = p; Sx < Wx; Sx += Nx) {\n"
+                         "                    long X = Sx + u - cs;",
+                         "                for (long Sx = p; Sx < Wx; Sx += Nx) {\n"
+                         "                    long X = Sx - u + cs;"),
+}
+
+
+def _build_proj_variant(tmp_path, name):
+    src = open(SRC).read()
+    if name is not None:
+        old, new = PROJ_MUTATIONS[name]
+        assert src.count(old) == 1, name
+        src = src.replace(old, new)
+    path = tmp_path / f"{name or 'plain'}_proj.c"
+    path.write_text(src)
+    so = tmp_path / f"{name or 'plain'}_proj.so"
+    subprocess.check_call(["gcc", "-O1", "-fopenmp", "-shared", "-fPIC", "-o", str(so), str(path)])
+    lib = ctypes.CDLL(str(so))
+    P, I = ctypes.c_void_p, ctypes.c_int
+    lib.oracle_transpose.argtypes = [P, P, I, I, I, I, P, P, I]
+    lib.oracle_forward_f64.argtypes = [P, I, I, I, P, P, P, I, I, P]
+    lib.oracle_backproject_f64.argtypes = [P, I, I, I, P, P, P, I, I, P]
+    lib.oracle_grad_hp_f64.argtypes = [P, P, I, I, I, P, P, I, I, P, I]
+    return lib
+
+
+def _proj_pins_pass(lib):
+    """True iff the variant's projectors pass the dense-matrix pins (forward =
+    A g, backprojection = A^T f, A built by pattern placement) and the gradient
+    passes the bilinear identity <dL/dH', dH'> = <r, dH' f> against the pinned
+    backprojection."""
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    Nx, Ny, K = 3, 3, 9
+    rng = np.random.default_rng(8)
+    Hz = rng.uniform(0, 1, (Nx, Ny, K, K))
+    Mx = My = 4
+    A = oracle.measurement_matrix(Hz, Mx, My, periodic=False)
+    W = Mx * Nx
+    g = rng.uniform(0, 1, (1, W, W))
+    f = rng.uniform(0, 1, (W, W))
+    ks = np.array([K], np.int32)
+    H = np.ascontiguousarray(Hz.reshape(-1))
+    fo = np.zeros((W, W))
+    if lib.oracle_forward_f64(p(H), Nx, Ny, 1, p(ks), p(ks), p(g), W, W, p(fo)) != 0:
+        return False
+    if not np.allclose(fo.reshape(-1), A @ g.reshape(-1), rtol=1e-12, atol=1e-12):
+        return False
+    Hp = np.zeros_like(H)
+    if lib.oracle_transpose(p(H), p(Hp), 8, Nx, Ny, 1, p(ks), p(ks), 1) != 0:
+        return False
+    go = np.zeros((1, W, W))
+    if lib.oracle_backproject_f64(p(Hp), Nx, Ny, 1, p(ks), p(ks), p(f), W, W, p(go)) != 0:
+        return False
+    if not np.allclose(go.reshape(-1), A.T @ f.reshape(-1), rtol=1e-12, atol=1e-12):
+        return False
+    # gradient: L(H') = <r, H' f> is linear in H', so <dL/dH', dH'> = <r, dH' f>
+    r = rng.uniform(-1, 1, (1, W, W))
+    dHp = rng.uniform(-1, 1, H.size)
+    gr = np.zeros_like(H)
+    if lib.oracle_grad_hp_f64(p(f), p(r), Nx, Ny, 1, p(ks), p(ks), W, W, p(gr), 1) != 0:
+        return False
+    bd = np.zeros((1, W, W))
+    lib.oracle_backproject_f64(p(dHp), Nx, Ny, 1, p(ks), p(ks), p(f), W, W, p(bd))
+    lhs, rhs = float(gr @ dHp), float((r * bd).sum())
+    return abs(lhs - rhs) <= 1e-10 * max(1.0, abs(rhs))
+
+
+def test_unmutated_projectors_pass(tmp_path):
+    assert _proj_pins_pass(_build_proj_variant(tmp_path, None))
+
+
+@pytest.mark.parametrize("name", sorted(PROJ_MUTATIONS))
+def test_planted_projector_mistake_is_caught(tmp_path, name):
+    assert not _proj_pins_pass(_build_proj_variant(tmp_path, name))
