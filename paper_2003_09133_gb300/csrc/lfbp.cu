@@ -12,7 +12,6 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
-#include <cmath>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -246,6 +245,8 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
 }  // namespace lfbp
 
 // ====================================================================== host
+#include <cmath>
+
 using namespace lfbp;
 
 struct lfbp_plan_s {
