@@ -1502,22 +1502,45 @@ int launch_pc_size(int S, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) 
   }
 }
 
-constexpr int kPcDB = 4;  // depths per block of k_phase_conv_md
+constexpr int kPcDB = 4;  // most depths per block of k_phase_conv_md
 
-template <int S>
+// Depths per block for a group of n depths: the fewest idle depth slots
+// (ceil(n/DB)*DB - n), ties to the larger DB.  Idle slots cost full FMAs.
+int md_depths_per_block(int n) {
+  int best = kPcDB, waste = (n + kPcDB - 1) / kPcDB * kPcDB - n;
+  for (int db = kPcDB - 1; db >= 2; --db) {
+    const int w = (n + db - 1) / db * db - n;
+    if (w < waste) {
+      waste = w;
+      best = db;
+    }
+  }
+  return best;
+}
+
+template <int S, int DB>
 int launch_md(PcArgs& a, const Planes* pl, dim3 grid, cudaStream_t st) {
   if (pl) {
     // (the pipelined form, k_phase_conv_pipe<S, 4, kPcDB>, measured slower here:
     // 96 registers x 288 threads leave two blocks per SM, like this one)
     if (planes_map(*pl, PcBox<S>::BX, 32 + S - 1, &a.tmap)) return -6;
-    k_phase_conv_md<S, kPcDB, true><<<grid, kPcThreads, 0, st>>>(a);
+    k_phase_conv_md<S, DB, true><<<grid, kPcThreads, 0, st>>>(a);
   } else {
-    k_phase_conv_md<S, kPcDB, false><<<grid, kPcThreads, 0, st>>>(a);
+    k_phase_conv_md<S, DB, false><<<grid, kPcThreads, 0, st>>>(a);
   }
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
-int launch_pc_md(int S, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
+template <int S>
+int launch_md_db(int db, PcArgs& a, const Planes* pl, dim3 grid, cudaStream_t st) {
+  switch (db) {
+    case 2: return launch_md<S, 2>(a, pl, grid, st);
+    case 3: return launch_md<S, 3>(a, pl, grid, st);
+    default: return launch_md<S, kPcDB>(a, pl, grid, st);
+  }
+}
+
+int launch_pc_md(int S, int db, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
   // output tiles of 32 rows x kPcTJ columns per phase
   a.nTI = ((a.Wx + a.Nx - 1) / a.Nx + 31) / 32;
   a.nTJ = ((a.Wy + a.Ny - 1) / a.Ny + kPcTJ - 1) / kPcTJ;
@@ -1525,9 +1548,9 @@ int launch_pc_md(int S, PcArgs& a, const Planes* pl, int ny, cudaStream_t st) {
   if (nblocks > 0x7fffffffLL) return -1;
   const dim3 grid((unsigned)nblocks, (unsigned)ny);
   switch (S) {  // small cut-outs only: there staging dominates one depth's work
-    case 3: return launch_md<3>(a, pl, grid, st);
-    case 5: return launch_md<5>(a, pl, grid, st);
-    default: return launch_md<7>(a, pl, grid, st);
+    case 3: return launch_md_db<3>(db, a, pl, grid, st);
+    case 5: return launch_md_db<5>(db, a, pl, grid, st);
+    default: return launch_md_db<7>(db, a, pl, grid, st);
   }
 }
 }  // namespace
@@ -1607,7 +1630,8 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         }
         a.ndepth = n;
         a.epi = epi;
-        const int rc = launch_pc_md(S, a, pl, (n + kPcDB - 1) / kPcDB, st);
+        const int db = md_depths_per_block(n);
+        const int rc = launch_pc_md(S, db, a, pl, (n + db - 1) / db, st);
         if (rc) return rc;
       }
     }
