@@ -152,6 +152,8 @@ struct PcArgs {
   int* status;       // device status word (a wait that ran out: LFBP_ERR_TIMEOUT)
   int fault;         // 1 (LFBP_FAULT=stall, tests of the timeout path): TMA copies
                      // register their bytes on the barrier but are not issued
+  int gsplit;        // k_phase_grad_pipe: blocks per (cell, depth), each a share of
+                     // its (rho, tau) sub-problems (0 or 1: one block)
   const float* A;
   const float* in;
   long long in_zstride;
@@ -934,12 +936,17 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
   __shared__ int abort_flag;
   const int Nx = a.Nx, Ny = a.Ny, Wx = a.Wx, Wy = a.Wy;
   const int p = blockIdx.x / Ny, q = blockIdx.x % Ny;
-  const PcDepth dd = a.d[blockIdx.y];
+  // grid.y = depths x gsplit: part `gpart` of the depth's (rho, tau) sub-problems
+  const int gsplit = a.gsplit > 0 ? a.gsplit : 1;
+  const int gpart = (int)blockIdx.y % gsplit;
+  const PcDepth dd = a.d[blockIdx.y / gsplit];
   const int Ks = dd.Ks, Kt = dd.Kt;
   float* dA = a.out + dd.off + ((long long)p * Ny + q) * Ks * Kt;
   const int nI = (Wx - p + Nx - 1) / Nx, nJ = (Wy - q + Ny - 1) / Ny;
   const int ntile = ((nI + kGrI - 1) / kGrI) * ((nJ + kGrJ - 1) / kGrJ);
-  const int nsub = min(Nx, Ks) * min(Ny, Kt);  // sub-problems per tile
+  const int nsub_all = min(Nx, Ks) * min(Ny, Kt);
+  const int k_lo = (int)((long long)nsub_all * gpart / gsplit);
+  const int nsub = (int)((long long)nsub_all * (gpart + 1) / gsplit) - k_lo;  // per tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < kGrStages; ++s) {
@@ -972,6 +979,7 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
         ++tiles;
         PcSub c;
         pc_sub_depth(c, 0, Ks, Kt, p, q, Nx, Ny);
+        for (int k = 0; k < k_lo; ++k) pc_sub_next_phase(c, p, q, Nx, Ny);
         for (int k = 0; k < nsub; ++k) {
           const int s = issued % kGrStages;
           if (issued >= kGrStages &&
@@ -1682,7 +1690,25 @@ int launch_grad_pipe(const PcArgs& a, dim3 grid, cudaStream_t st) {
   if (cudaFuncSetAttribute(k_phase_grad_pipe<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return -6;
-  k_phase_grad_pipe<S><<<grid, kPcPipeThreads, smem, st>>>(a);
+  // enough blocks for about three waves at three blocks per SM: the cells of a
+  // depth times its depths can be fewer than the GPU holds, so each cell's
+  // sub-problems are shared among gsplit blocks (they write disjoint outputs)
+  PcArgs b = a;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -6;
+  const long long blocks = (long long)grid.x * grid.y;
+  b.gsplit = (int)std::min<long long>(8, std::max<long long>(1, (9LL * sms + blocks - 1) / blocks));
+  const int nsub_min = [&] {
+    int m = 1 << 30;
+    for (int i = 0; i < a.ndepth; ++i)
+      m = std::min(m, std::min(a.Nx, a.d[i].Ks) * std::min(a.Ny, a.d[i].Kt));
+    return m;
+  }();
+  b.gsplit = std::max(1, std::min(b.gsplit, nsub_min));
+  const dim3 g2(grid.x, grid.y * (unsigned)b.gsplit);
+  k_phase_grad_pipe<S><<<g2, kPcPipeThreads, smem, st>>>(b);
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
