@@ -1327,11 +1327,6 @@ int launch_projector(int out_cell, int epi, const float* A, int Nx, int Ny, int 
   return cudaGetLastError() == cudaSuccess ? 0 : -6;
 }
 
-int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, const float* in,
-                             int Wx, int Wy, float* out, int accumulate, cudaStream_t st) {
-  return launch_projector(0, accumulate ? kEpiAccumulate : kEpiStore, A, Nx, Ny, Ks, Kt, in, Wx,
-                          Wy, out, nullptr, nullptr, st);
-}
 
 namespace {
 constexpr int kPcSizes[] = {3, 5, 7, 9, 11, 13, 15};  // kernel instances (sub-kernel extent S)

@@ -18,8 +18,6 @@ constexpr int kEpiRL = 2;          // out = g / norm * sum, 0 where norm = 0 (Eq
 int launch_projector(int out_cell, int epi, const float* A, int Nx, int Ny, int Ks, int Kt,
                      const float* in, int Wx, int Wy, float* out, const float* g,
                      const float* norm, cudaStream_t st);
-int launch_shift_variant_sum(const float* A, int Nx, int Ny, int Ks, int Kt, const float* in,
-                             int Wx, int Wy, float* out, int accumulate, cudaStream_t st);
 // dA[p][q][u][v] = sum over pixels S of cell (p, q) of f[S] * dg[S + (u-c_s, v-c_t)]
 int launch_backproject_grad(const float* f, const float* dg, int Nx, int Ny, int Ks, int Kt,
                             int Wx, int Wy, float* dA, cudaStream_t st);
