@@ -41,6 +41,7 @@ CASES = [  # Nx, Ny, Ks, Kt, Wx, Wy
     (11, 11, [33, 99], [33, 99], 66, 77),
     (95, 55, [95], [165], 190, 110),   # the R29 elementary cell (Sec. 5), two cells per axis
     (31, 31, [249], [249], 62, 93),     # a Table 1 size: K not a multiple of N (S = 9)
+    (3, 3, [9, 15], [9, 3], 200, 151),  # cells of 67 x 51 pixels: two gradient tiles per cell
 ]
 
 

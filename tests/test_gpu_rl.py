@@ -53,6 +53,7 @@ CASES = [  # Nx, Ny, Ks, Kt, Wx, Wy
     (1, 1, [3], [5], 9, 7),
     (11, 11, [33, 99], [33, 99], 66, 77),
     (3, 5, [9] * 5 + [15], [15] * 5 + [5], 30, 41),  # five equal cut-outs: several depths per block
+    (3, 3, [9, 15, 9, 9], [9, 3, 9, 9], 200, 151),  # 67 x 51 pixels per cell: several tiles per phase
 ]
 
 
