@@ -26,34 +26,10 @@
 #include <cstdint>
 
 #include "lfbp_project.h"
+#include "lfbp_window.cuh"
 
 namespace lfbp {
 namespace {
-
-__device__ __forceinline__ int floor_div_dev(int a, int b) {
-  int q = a / b;
-  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
-  return q;
-}
-
-// Eq. 5: alpha wrapped into 1..n
-__device__ __forceinline__ int eq5_wrap_dev(int alpha, int n) {
-  const int r = alpha - floor_div_dev(alpha - 1, n) * n;
-  return r;
-}
-
-// Source (0-based cell position a, cut-out index s0) of output (p, u) on one
-// axis, or -1 when the literal loop never writes it.
-__device__ __forceinline__ int window_source(int p, int u, int n, int K, int* s0) {
-  const int xp = p + 1, sp = u + 1;
-  const int s = K - sp + (K & 1);
-  if (s < 1 || s > K) return -1;
-  const int dS = floor_div_dev(K - n, 2);
-  const int m = xp - s + n + 2 * dS - (n - 1) / 2;
-  if (m < 1 || m > K) return -1;
-  *s0 = s - 1;
-  return eq5_wrap_dev(m - dS, n) - 1;
-}
 
 // out[z][p][q][u][v] = in[z][a][b][s][t] through window_source on both axes,
 // 0 where either axis has no source (forward); with kAdjoint the same pairs
