@@ -580,7 +580,8 @@ def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
         nbe = 2 * pe.elems * 4
         res["even_K"] = {"K": "every highres K + 1", "bytes_per_step": nbe,
                          "plain_GBps": round(world * nbe / (te * 1e-3) / 1e9, 1),
-                         "plain_ms": round(te, 4), "kernel": "k_window_literal"}
+                         "plain_ms": round(te, 4),
+                         "kernel": "k_window_literal_rows (a row of segments through shared memory)"}
         del He, Oe
         torch.cuda.empty_cache()
     return res

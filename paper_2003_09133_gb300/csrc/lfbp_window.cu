@@ -19,8 +19,9 @@
 // source receives at most one value (the m giving valid x'_m for one s are
 // n consecutive values, whose x(m) are distinct).
 //
-// One thread per output element; reads are gathered.  This form is for
-// completeness of the literal equations, not speed.
+// The forward map runs a row at a time through shared memory when a row's Ny
+// source segments fit (k_window_literal_rows: coalesced reads and writes);
+// otherwise, and for the adjoint, one thread per element with gathered reads.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,11 +60,52 @@ __global__ void k_window_literal(const T* __restrict__ in, T* __restrict__ out, 
   }
 }
 
+// The forward map a row at a time: block (p, u) loads the Ny source rows
+// (a, b = 0..Ny-1, s0) of its output row u, Kt elements each and contiguous in
+// H, into shared memory with coalesced reads, then writes the Ny x Kt output
+// plane (q, v) of (p, u) with coalesced writes.  Needs Ny * Kt elements of
+// shared memory.
+template <typename T>
+__global__ void k_window_literal_rows(const T* __restrict__ in, T* __restrict__ out, int Nx,
+                                      int Ny, int Ks, int Kt) {
+  extern __shared__ __align__(16) unsigned char wsm[];
+  T* rows = reinterpret_cast<T*>(wsm);
+  const int u = (int)(blockIdx.x % Ks), p = (int)(blockIdx.x / Ks);
+  int s0 = 0;
+  const int a = window_source(p, u, Nx, Ks, &s0);
+  const long long plane = (long long)Ny * Kt;
+  T* dst = out + ((long long)p * Ny * Ks + u) * Kt;  // element (p, q = 0, u, v = 0)
+  if (a < 0) {  // the literal loop writes nothing in this row
+    for (long long e = threadIdx.x; e < plane; e += blockDim.x) {
+      const int q = (int)(e / Kt), v = (int)(e - (long long)q * Kt);
+      dst[(long long)q * Ks * Kt + v] = T(0);
+    }
+    return;
+  }
+  for (long long e = threadIdx.x; e < plane; e += blockDim.x) {
+    const int b = (int)(e / Kt), t = (int)(e - (long long)b * Kt);
+    rows[e] = in[(((long long)a * Ny + b) * Ks + s0) * Kt + t];
+  }
+  __syncthreads();
+  for (long long e = threadIdx.x; e < plane; e += blockDim.x) {
+    const int q = (int)(e / Kt), v = (int)(e - (long long)q * Kt);
+    int t0 = 0;
+    const int b = window_source(q, v, Ny, Kt, &t0);
+    dst[(long long)q * Ks * Kt + v] = b >= 0 ? rows[(long long)b * Kt + t0] : T(0);
+  }
+}
+
 template <typename T>
 int launch_t(const void* in, void* out, int Nx, int Ny, int Ks, int Kt, int adjoint,
              cudaStream_t st) {
   const long long n = (long long)Nx * Ny * Ks * Kt;
   if (n == 0) return 0;
+  const long long row_bytes = (long long)Ny * Kt * (long long)sizeof(T);
+  if (!adjoint && row_bytes <= 48 * 1024 && (long long)Nx * Ks <= 0x7fffffffLL) {
+    k_window_literal_rows<T><<<(unsigned)((long long)Nx * Ks), 256, (size_t)row_bytes, st>>>(
+        static_cast<const T*>(in), static_cast<T*>(out), Nx, Ny, Ks, Kt);
+    return cudaGetLastError() == cudaSuccess ? 0 : -6;
+  }
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   if (adjoint) {
