@@ -132,11 +132,13 @@ __global__ void __launch_bounds__(kSvTI* kSvTJ)
 // and out(i, j) += sum_{sigma,upsilon} I(i-i0+sigma, j-j0+upsilon) * w[Nx sigma+rho][Ny upsilon+tau]:
 // a dense correlation with an at most S x S kernel.  The subgrid tile and the
 // sub-kernel (zero-padded to S x S) are staged in shared memory; each thread
-// accumulates RI x 2 outputs in registers, reusing each loaded input row
-// for every kernel row it meets.  Terms are summed in a fixed order
-// (deterministic); padded taps add exact zeros.
+// accumulates RI/2 rows x 4 columns of outputs in registers (half a warp per
+// row group), reusing each loaded input row for every kernel row it meets.
+// Terms are summed in a fixed order (deterministic); padded taps add exact
+// zeros.  The subgrid arrives by TMA from the input laid out by phase, or by
+// 4-byte cp.async copies (see the staging sections below).
 constexpr int kPcThreads = 256;
-constexpr int kPcTJ = 64;                // output columns per block (2 per lane)
+constexpr int kPcTJ = 64;                // output columns per block (4 per lane, 16 lanes)
 constexpr int kPcMaxDepths = 64;
 
 struct PcDepth {
