@@ -27,7 +27,13 @@
  *
  * LFBP_MAP_PAPER_WINDOW reproduces the loop ranges of Eqs. (4)-(9) literally
  * (m = 1..n_s): entries with p+u < h_x, p+u > Ks-1+h_x, q+v < h_y or
- * q+v > Kt-1+h_y (h = (N-1)/2) are written as zero bits instead.
+ * q+v > Kt-1+h_y (h = (N-1)/2) are written as zero bits instead.  In this
+ * mode even cut-outs are taken as well (Eq. 8 then drops s = n_s and never
+ * writes s' = n_s; see lfbp_plan_create2).
+ *
+ * Beside the map, the projectors that consume H' (Eqs. 1 and 2) and the
+ * gradient with respect to H' run on fp32 plans (lfbp_backproject_volume and
+ * the calls after it).
  *
  * CONVENTIONS.  All device pointers are owned by the caller and must stay
  * valid until the stream work completes.  Every call that takes a stream
