@@ -209,3 +209,25 @@ def test_plan_partition_covers_and_balances(lib, nparts):
     assert lib.lfbp_plan_partition(h, 0, 0, ctypes.byref(z0), ctypes.byref(z1)) == -9
     assert lib.lfbp_plan_partition(h, 2, 2, ctypes.byref(z0), ctypes.byref(z1)) == -9
     lib.lfbp_plan_destroy(h)
+
+
+def test_binding_has_no_cpu_path():
+    """The binding refuses host tensors before calling the library: there is no
+    CPU fallback for any step of the path."""
+    import torch
+    import paper_2003_09133_gb300 as lf
+    lf.load(build_if_missing=True)
+    plan = lf.Plan(3, 3, [9], [9], torch.float32)
+    H = torch.zeros(plan.elems)                      # a host tensor
+    with pytest.raises(ValueError, match="CUDA"):
+        lf.backproject_array(plan, H)
+    with pytest.raises(ValueError, match="CUDA"):
+        lf.backproject_batched([plan], [H])
+    with pytest.raises(ValueError, match="CUDA"):
+        lf.adjoint(plan, H)
+    f, g = torch.zeros((12, 12)), torch.zeros((1, 12, 12))
+    for call in (lambda: lf.backproject_volume_from_h(plan, H, f),
+                 lambda: lf.forward_project(plan, H, g),
+                 lambda: lf.backproject_volume_grad(plan, f, g)):
+        with pytest.raises((ValueError, TypeError)):
+            call()
