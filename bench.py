@@ -736,9 +736,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default launch shape instead of the autotuner's")
-    ap.add_argument("--only", choices=["rl", "autograd"], default=None,
-                    help="time only one RL update (Eq. 2) or the autograd step on the "
-                         "differentiation workload and print that (for profiling)")
+    ap.add_argument("--only", choices=["rl", "autograd", "table1", "window"], default=None,
+                    help="time only one of the extra measurements and print that (for "
+                         "profiling): the RL update (Eq. 2) or the autograd step on the "
+                         "differentiation workload, the Table 1 sizes, or the paper-window "
+                         "mode (odd and even cut-outs)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
@@ -769,8 +771,20 @@ def run_only(args):
         lf.sync_status()
         return a.elapsed_time(b) / n, None, None
 
-    fn = _rl_extra if args.only == "rl" else _autograd_extra
-    print(json.dumps({"only": args.only, **fn(lf, timed, args.steps)}), flush=True)
+    if args.only == "table1":
+        res = _table1_extra(lf, 1, args.no_tune)
+    elif args.only == "window":
+        import lfgen
+        specs = lfgen.config_specs("highres")
+        s = specs[0]
+        plans = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float32)]
+        Hs = [lfgen.generate(s, device="cuda")]
+        outs = [torch.empty_like(Hs[0])]
+        res = _paper_window_extra(lf, specs, Hs, outs, timed, max(3, args.steps // 4), 1)
+    else:
+        fn = _rl_extra if args.only == "rl" else _autograd_extra
+        res = fn(lf, timed, args.steps)
+    print(json.dumps({"only": args.only, **res}), flush=True)
     return 0
 
 
