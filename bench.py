@@ -210,12 +210,21 @@ def _cpu_oracle_rate(specs, Hs_host, dtype_override, budget_s=12.0, max_passes=3
     oracle.transpose(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
     t1 = time.perf_counter() - t0
     oracle.threads(cores)
+    # the paper's own loop (Eqs. 4-9 with the loop ranges of Sec. 4, one element
+    # per innermost iteration, single-threaded) on the same depth: the paper's
+    # CPU algorithm as written, for context beside its published timings
+    t0 = time.perf_counter()
+    oracle.paper_window(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
+    t2 = time.perf_counter() - t0
     return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "seconds": round(t_total, 3),
             "sample": f"{done_bytes / 2 / 1e9:.2f} GB of H mapped by oracle.transpose "
                       f"({passes} pass(es) over {'+'.join(sample_desc)}; C, OpenMP {cores} threads)",
             "single_thread_GBps": round(2 * Hz.nbytes / t1 / 1e9, 3),
-            "single_thread_sample": f"depth {z} of {s.name} (K = {s.Ks[z]}), 1 thread"}
+            "single_thread_sample": f"depth {z} of {s.name} (K = {s.Ks[z]}), 1 thread",
+            "paper_loop_single_thread_GBps": round(2 * Hz.nbytes / t2 / 1e9, 3),
+            "paper_loop_sample": "the same depth through oracle.paper_window (the paper's "
+                                 "loop of Sec. 4 in C), 1 thread"}
 
 
 def _reference_sample(specs, budget_elems=48_000_000):

@@ -25,3 +25,18 @@ def test_reference_arm_json_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_cpu_baseline_object_of_the_gpu_line():
+    """The cpu_baseline object of the GPU arm's line: the oracle on all host
+    threads, its one-thread rate and the paper's own loop on one depth."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import lfgen
+    specs = lfgen.config_specs("tiny")
+    Hs = [lfgen.generate(s).numpy() for s in specs]
+    d = bench._cpu_oracle_rate(specs, Hs, None, budget_s=0.5, max_passes=4)
+    assert d["kind"] == "oracle" and d["unit"] == "GB/s" and d["cores"] >= 1
+    for key in ("value", "single_thread_GBps", "paper_loop_single_thread_GBps"):
+        assert d[key] > 0, key
+    assert "oracle.transpose" in d["sample"] and "oracle.paper_window" in d["paper_loop_sample"]
