@@ -32,6 +32,11 @@ MUTATIONS = {
                  "if (alpha <= 0) return alpha + floor_div(1 - alpha, n) * n + n;"),
     "eq4_alpha": ("long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);",
                   "long dS = floor_div(ns - nx + 2, 2), dT = floor_div(nt - ny, 2);"),
+    # slips that only even cut-outs see (reading A2): the odd-K form of Eq. (8),
+    # and Eq. (4)'s floor taken as a ceiling (equal when n_s - n_x is even)
+    "eq8_even_as_odd": ("long sp = ns - s + (ns % 2);", "long sp = ns - s + 1;"),
+    "eq4_even_ceil": ("long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);",
+                      "long dS = ceil_div(ns - nx, 2), dT = floor_div(nt - ny, 2);"),
 }
 
 
@@ -59,8 +64,22 @@ def _run(fn, H, Nx, Ny, Ks, Kt, *extra):
     return rc, out
 
 
+def _read_golden_even(path):
+    """(p, u) -> source (a, s) or None, from a hand-evaluated even-n_s table."""
+    rows = {}
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                tok = line.split()
+                rows[(int(tok[0]), int(tok[1]))] = (None if tok[2] == "-"
+                                                    else (int(tok[2]), int(tok[3])))
+    return rows
+
+
 def _pins_pass(lib):
-    """True iff the variant passes the golden tables and the dense-matrix pin."""
+    """True iff the variant passes the golden tables (odd and even n_s) and the
+    dense-matrix pin."""
     from test_oracle import _read_golden, _tagged_1d, _tag
     gold = os.path.join(os.path.dirname(__file__), "golden")
     for fname, N, K in [("eqs4to9_nx3_ns5.txt", 3, 5), ("eqs4to9_nx3_ns3.txt", 3, 3)]:
@@ -74,6 +93,13 @@ def _pins_pass(lib):
             if tr[p * K + u] != _tag(*trans):
                 return False
             if pw[p * K + u] != (0 if paper is None else _tag(*paper)):
+                return False
+    for fname, N, K in [("eqs4to9_nx3_ns4_even.txt", 3, 4), ("eqs4to9_nx3_ns6_even.txt", 3, 6)]:
+        rc_p, pw = _run(lib.oracle_paper_window, _tagged_1d(N, K), N, 1, [K], [1])
+        if rc_p != 0:
+            return False
+        for (p, u), src in _read_golden_even(os.path.join(gold, fname)).items():
+            if pw[p * K + u] != (0 if src is None else _tag(*src)):
                 return False
     Nx, Ny, Ks, Kt = 5, 3, 15, 9
     Hz = np.random.default_rng(1).uniform(-1, 1, (Nx, Ny, Ks, Kt))
