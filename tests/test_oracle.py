@@ -394,3 +394,34 @@ def test_golden_even_cutout_literal_equations(golden_dir, fname, N, K):
     pw = oracle.paper_window(_tagged_1d(N, K), N, 1, [K], [1])
     for (p, u), src in rows.items():
         assert pw[p * K + u] == (0 if src is None else _tag(*src)), (p, u)
+
+
+@pytest.mark.parametrize("Nx,Ny,K,Kt", [(3, 1, 4, 1), (5, 3, 2, 9), (5, 5, 4, 4), (3, 5, 10, 7),
+                                        (7, 3, 8, 12), (1, 1, 4, 6), (9, 5, 6, 15), (5, 7, 16, 2)])
+def test_even_cutout_loop_is_a_cropped_odd_transpose(Nx, Ny, K, Kt):
+    """Even n_s (reading A2) against the brute-force transpose.  Solving
+    Eqs. (4)-(8) for even n_s = K (0-based p = x'-1, u = s'-1, s0 = s-1):
+    Eq. (8) gives u = K-2-s0, so s0 = K-1 is dropped and u = K-1 never
+    written; Eqs. (4)-(6) give a = p+u-(K/2-1+n) = p+u-(K/2-1) (mod n), using
+    dS = (K-n-1)/2 for odd n, and m = p+u+1-h.  That is the transpose of the
+    odd (K-1)-pixel cut-out s0 < K-1 (centre (K-2)/2 = K/2-1), written at
+    u < K-1, with the loop's range 1 <= m <= K as the usual window
+    h <= p+u <= K-1+h.  An odd axis keeps its own transpose and window.  The
+    two sides are separate oracle functions: the literal loop and the
+    measurement-matrix transpose."""
+    rng = np.random.default_rng(Nx * 1000 + K * 10 + Kt)
+    H = rng.uniform(0.5, 1.0, Nx * Ny * K * Kt)
+    H4 = H.reshape(Nx, Ny, K, Kt)
+    Ke, Kte = K - 1 + K % 2, Kt - 1 + Kt % 2
+    sub = np.ascontiguousarray(H4[:, :, :Ke, :Kte]).reshape(-1)
+    T = oracle.transpose(sub, Nx, Ny, [Ke], [Kte]).reshape(Nx, Ny, Ke, Kte)
+    want = np.zeros_like(H4)
+    want[:, :, :Ke, :Kte] = T
+    hx, hy = (Nx - 1) // 2, (Ny - 1) // 2
+    p = np.arange(Nx)[:, None, None, None]
+    q = np.arange(Ny)[None, :, None, None]
+    u = np.arange(K)[None, None, :, None]
+    v = np.arange(Kt)[None, None, None, :]
+    keep = (p + u >= hx) & (p + u <= K - 1 + hx) & (q + v >= hy) & (q + v <= Kt - 1 + hy)
+    want = np.where(keep, want, 0.0).reshape(-1)
+    np.testing.assert_array_equal(oracle.paper_window(H, Nx, Ny, [K], [Kt]), want)
