@@ -34,6 +34,43 @@ def test_binding_covers_header():
     assert sorted(_lib.SIGNATURES) == _declared()
 
 
+def _c_kind(decl):
+    """'p' (pointer or opaque plan handle), 'i' (int or enum), 's' (size_t),
+    'c' (const char*) or '' (void) for one C type or parameter."""
+    decl = decl.strip()
+    if decl in ("void", ""):
+        return ""
+    if re.match(r"const\s+char\s*\*", decl):
+        return "c"
+    if "*" in decl or re.match(r"(const\s+)?lfbp_plan\b", decl):
+        return "p"
+    if decl.startswith("size_t"):
+        return "s"
+    if re.match(r"(int|lfbp_dtype|lfbp_mode)\b", decl):
+        return "i"
+    raise AssertionError(f"unexpected C type in the header: {decl!r}")
+
+
+def test_binding_signatures_match_the_header():
+    """Every argument and return type the binding marshals has the kind the
+    header declares (a pointer passed as an int, or a size_t as an int, would
+    be truncated on a 64-bit host)."""
+    from paper_2003_09133_gb300 import _lib
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    decls = re.findall(r"^\s*((?:const\s+)?[a-z_]+\s*\**)\s*(lfbp_[a-z0-9_]+)\s*\(([^)]*)\)\s*;",
+                       text, flags=re.M)
+    assert sorted(d[1] for d in decls) == _declared()
+    kinds = {ctypes.c_void_p: "p", ctypes.c_int: "i", ctypes.c_size_t: "s",
+             ctypes.c_char_p: "c", None: ""}
+    for ret, name, params in decls:
+        args, res = _lib.SIGNATURES[name]
+        want = [_c_kind(a) for a in params.split(",")] if params.strip() != "void" else []
+        got = [kinds.get(a, "p" if isinstance(a, type) and issubclass(a, ctypes._Pointer) else "?")
+               for a in args]
+        assert got == want, (name, got, want)
+        assert kinds[res] == _c_kind(ret), (name, res, ret)
+
+
 def _plan(lib, Nx, Ny, Ks, Kt, dt=0, mode=0):
     h = ctypes.c_void_p()
     n = len(Ks)
