@@ -84,6 +84,11 @@ SHAPES = [
     (3, 3, [1, 1], [1, 1], 32768),
     (17, 17, [255], [255], 32768),
     (15, 15, [45, 75], [45, 75], 65536),  # the plain form's tile target: up to 64 rows
+    # wide cells as in the large Table 1 sizes and the 95 x 55 cell (cut-outs scaled down)
+    (5, 55, [181], [181], 32768),         # a row of 55 x 181 fp32 exceeds the stage: column split
+    (51, 51, [53], [53], 32768),
+    (95, 3, [19, 21], [97, 9], 32768),    # Ny below a chunk: element walk
+    (3, 95, [11], [191], 32768),
 ]
 
 
