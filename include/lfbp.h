@@ -74,7 +74,9 @@ typedef struct lfbp_plan_s* lfbp_plan; /* opaque; owned by the library */
 /*
  * Square elementary cell (Nx = Ny = Nnum, Ks = Kt = Kz[z]).  Nnum and every
  * Kz[z] must be odd and >= 1 (Sec. 4: n_x, n_y odd; odd n_s makes Eq. (8) a
- * flip, see lfbp_plan_create2).  Kz is copied.  Nz = 0 makes an empty plan.
+ * flip, see lfbp_plan_create2).  Kz is copied.  Nz = 0 makes an empty plan:
+ * the map calls (plain, batched, host, adjoint) return LFBP_OK for it at once,
+ * with no CUDA call, and its buffers may be NULL.
  * On success *out receives a plan to be released with lfbp_plan_destroy.
  */
 int lfbp_plan_create(lfbp_plan* out, int Nnum, int Nz, const int* Kz, lfbp_dtype dt,

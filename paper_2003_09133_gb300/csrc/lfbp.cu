@@ -411,6 +411,7 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
 int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st) {
   int rc = check_buffers(p, in, out);
   if (rc) return rc;
+  if (p->off.back() == 0) return LFBP_OK;  // an empty plan: no CUDA call at all
   if (p->literal) {  // even cut-outs: the literal loop, depth by depth (mode 2: its adjoint)
     for (int z = 0; z < p->Nz; ++z) {
       const size_t o = p->off[z] * (size_t)p->es;
@@ -421,6 +422,13 @@ int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st)
     return LFBP_OK;
   }
   return launch_plain(p, (const unsigned char*)in, (unsigned char*)out, mode, 0, p->Nz, st);
+}
+
+// True when no array of the batch has an element.
+bool batch_empty(int n, const lfbp_plan* plans) {
+  for (int i = 0; i < n; ++i)
+    if (plans[i]->off.back() != 0) return false;
+  return true;
 }
 
 // Entry points other than lfbp_backproject_array and lfbp_adjoint take odd
@@ -675,6 +683,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
       if (k != i && bi && bk && overlaps(out[i], bi, out[k], bk))
         return fail(LFBP_ERR_ALIAS, "two outputs overlap");
     }
+  if (batch_empty(n, plans)) return LFBP_OK;  // nothing to map: no CUDA call at all
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
@@ -800,6 +809,7 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
       if (k != i && bi && bk && overlaps(out[i], bi, out[k], bk))
         return fail(LFBP_ERR_ALIAS, "two outputs overlap");
     }
+  if (batch_empty(n, plans)) return LFBP_OK;  // nothing to map: no CUDA call at all
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

@@ -119,6 +119,23 @@ def test_empty_plan(lib):
     lib.lfbp_plan_destroy(h)
 
 
+def test_empty_inputs_return_before_any_cuda_call(lib):
+    """An empty plan (no depths) and batches of empty plans succeed with NULL
+    buffers on a machine without a GPU: the map entry points return before
+    their first CUDA call, so nothing is launched or allocated."""
+    rc, h = _plan(lib, 5, 5, [], [])
+    assert rc == 0
+    assert lib.lfbp_backproject_array(h, None, None, None) == 0
+    assert lib.lfbp_adjoint(h, None, None, None) == 0
+    assert lib.lfbp_backproject_array_host(h, None, None, None, None, None) == 0
+    plans = (ctypes.c_void_p * 3)(h, h, h)
+    nul = (ctypes.c_void_p * 3)(None, None, None)
+    assert lib.lfbp_backproject_batched(3, plans, nul, nul, None) == 0
+    assert lib.lfbp_backproject_batched_noalloc(3, plans, nul, nul, None) == 0
+    assert lib.lfbp_backproject_batched(0, None, None, None, None) == 0
+    lib.lfbp_plan_destroy(h)
+
+
 def test_buffer_validation_before_any_launch(lib):
     rc, h = _plan(lib, 5, 5, [15], [15])
     assert rc == 0
