@@ -32,6 +32,7 @@ SHAPES = [  # Nx, Ny, Ks, Kt: even, odd and mixed cut-outs, K < N and K > N
     (3, 1, [4], [1]), (3, 1, [6], [1]), (3, 3, [6, 4], [4, 9]), (5, 3, [14, 15], [15, 6]),
     (1, 1, [2, 8], [6, 3]), (7, 5, [2, 21, 16], [10, 5, 3]), (5, 5, [15, 5], [15, 25]),
     (9, 13, [26, 3], [40, 12]),
+    (19, 19, [76, 57], [76, 58]), (95, 55, [12, 96], [10, 7]),  # the GPU test's cells
 ]
 
 
