@@ -87,3 +87,26 @@ def test_noalloc_rejects_too_many_tiles(lf):
                                               ctypes.cast((P * 1)(fake_out), P), None)
     assert rc == -1
     assert b"no-allocation path holds at most 262144" in lib.lfbp_last_error()
+
+
+def test_empty_arrays_alone_and_inside_a_batch(lf):
+    """Empty inputs: a plan without depths maps to an empty H' through every
+    entry point, and an empty array inside a batch leaves the others exact."""
+    import oracle
+    empty = lf.Plan(5, 5, [], [], torch.float32)
+    E = torch.empty(0, dtype=torch.float32, device="cuda")
+    assert lf.backproject_array(empty, E).numel() == 0
+    assert lf.adjoint(empty, E).numel() == 0
+    assert lf.backproject_batched([empty], [E])[0].numel() == 0
+    lf.sync_status()
+    plan = lf.Plan(5, 3, [15, 9], [9, 21], torch.float32)
+    H = _bits(plan.elems, torch.float32, 11)
+    want = oracle.transpose(H.cpu().numpy(), 5, 3, [15, 9], [9, 21])
+    got = lf.backproject_batched([empty, plan, empty], [E, H, E])
+    lf.sync_status()
+    assert got[0].numel() == 0 and got[2].numel() == 0
+    assert np.array_equal(got[1].cpu().numpy().view(np.uint32), want.view(np.uint32))
+    outs = [torch.empty_like(E), torch.full_like(H, float("nan"))]
+    assert _noalloc(lf, [empty, plan], [E, H], outs) == 0
+    lf.sync_status()
+    assert np.array_equal(outs[1].cpu().numpy().view(np.uint32), want.view(np.uint32))
