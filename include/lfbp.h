@@ -145,7 +145,10 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
 
 /*
  * H -> H' for n arrays at once, in one persistent launch over a ragged work
- * list of all depths of all arrays (mixed fp32 / fp16 plans allowed).  The
+ * list of all depths of all arrays (mixed fp32 / fp16 plans allowed).  Sec. 4
+ * maps each z-plane on its own (the index relations of Eqs. 4-9 never mix
+ * depths), so the depths of several arrays form one list of independent
+ * pieces of work, whatever their cell and cut-out sizes.  The
  * work list, launch shape and a CUDA graph of the launch are built on the
  * first call for a given list of plans and reused while the same plans (by
  * handle) come back; pointers may change between calls.  The first call for
@@ -166,9 +169,9 @@ int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* d
  * kernel's work list in a fixed array of device memory that is part of the
  * library image: 262,144 tile descriptors (8 MiB), held on every GPU that
  * loads the library until the process exits.  A batch that needs more tiles
- * (even with 48 KiB tiles) is rejected with LFBP_ERR_BAD_SHAPE before any work
- * is queued.  The call never calls cudaMalloc or cudaFree and builds no CUDA
- * graph; it launches the kernel directly on cuda_stream.
+ * (even with tiles of at least 48 KiB) is rejected with LFBP_ERR_BAD_SHAPE
+ * before any CUDA call.  The call never calls cudaMalloc or cudaFree and
+ * builds no CUDA graph; it launches the kernel directly on cuda_stream.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) and reads device attributes; make that first call
@@ -179,8 +182,14 @@ int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* d
  * the entries the current list occupies).  Calls whose work overlaps on the
  * GPU -- on different streams, or from threads that do not order their
  * streams -- race on the array and may map with the wrong list; keep such
- * calls on one stream or order them with events.  Arguments, layout and
- * results are those of lfbp_backproject_batched.
+ * calls on one stream or order them with events.  This holds for a call that
+ * follows another on a different stream even when both name the same plans:
+ * the later call finds the list already loaded and launches at once, so it
+ * must be ordered after the earlier call (an event recorded after it) for the
+ * earlier call's copy of the list to have landed.  A call that has to copy a
+ * new list in returns LFBP_ERR_INVALID, without queuing work, while
+ * cuda_stream is capturing: the copy reads host memory owned by the call.
+ * Arguments, layout and results are those of lfbp_backproject_batched.
  */
 int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* const* dH,
                                      void* const* dHp, void* cuda_stream);

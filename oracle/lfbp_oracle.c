@@ -26,7 +26,8 @@
  *                           voxels that reach it).
  *   oracle_transpose_adjoint  the adjoint (scatter) of that permutation.
  *   oracle_paper_window     Eqs. (4)-(9) evaluated in the paper's 1-based
- *                           notation and loop ranges (Sec. 4, Fig. 10).
+ *                           notation and loop ranges (Sec. 4), source by
+ *                           source.
  *   oracle_forward_f64      f = H g, Eq. (1): copies of the cut-outs of H,
  *                           scaled by the voxel values, summed on the sensor.
  *   oracle_backproject_f64  g = H' f, the backprojection used in Eq. (2).
@@ -181,25 +182,43 @@ int oracle_transpose_adjoint(const void* dHp, void* dH, int esize, int Nx, int N
 }
 
 /*
- * Eqs. (4)-(9) in the paper's 1-based notation, with the loop ranges the
- * paper states (m = 1..n_s, n = 1..n_t, s = 1..n_s, t = 1..n_t) and the
- * validity conditions 0 < x' <= n_x, 0 < y' <= n_y, 0 < s', 0 < t'.
- * Entries of H' that no (s, t, m, n) reaches stay zero.
+ * Eqs. (4)-(9) in the paper's 1-based notation, with the paper's loop ranges
+ * (its m = 1..n_s and n = 1..n_t) and validity conditions (0 < x' <= n_x,
+ * 0 < s'), read from the source side: for every element H(s, t, x, y) the
+ * equations give the H' position it is assigned to, or none.
  *
- * Eq. (4):  alpha = m - floor((n_s - n_x)/2)
- * Eq. (5):  x = alpha - floor((alpha-1)/n_x) n_x   if alpha > n_x
- *             = alpha + ceil((1-alpha)/n_x) n_x    if alpha <= 0
- *             = alpha                              otherwise
- * Eq. (6):  x' = s - n_x + alpha + floor((n_x-1)/2) - floor((n_s-n_x)/2)
- * Eq. (8):  s' = n_s - s + (n_s mod 2)
- * and likewise Eqs. (7), (9) for y', t' with n_t, n_y, beta.
- * Assignment: H'(s', t', x', y') = H(s, t, x, y) at each depth.
+ * One axis (x with s; y with t is the same with n_y, n_t):
+ *   Eq. (4):  alpha = m - floor((n_s - n_x)/2)      for a loop index m
+ *   Eq. (5):  x(alpha) = alpha wrapped into 1..n_x  (the cell alpha lands in)
+ *   Eq. (6):  x' = s - n_x + alpha + floor((n_x-1)/2) - floor((n_s-n_x)/2)
+ *   Eq. (8):  s' = n_s - s + (n_s mod 2)
+ * Source (x, s) is assigned to (x', s') for the m in 1..n_s whose wrapped
+ * alpha is x and whose x' is in 1..n_x, provided s' > 0.  The m with the
+ * same x(alpha) differ by n_x, so their x' differ by n_x and at most one of
+ * them is valid: every source has at most one target per axis.  The element
+ * moves when both axes give a target; H' positions that no source reaches
+ * stay zero, and a position reached twice is reported (-3).
  * Even n_s or n_t are accepted here exactly as the equations read.
  */
 static long eq5_wrap(long alpha, long n) {
     if (alpha > n) return alpha - floor_div(alpha - 1, n) * n;
     if (alpha <= 0) return alpha + ceil_div(1 - alpha, n) * n;
     return alpha;
+}
+
+/* The target (x', s') of source (x, s) on one axis (n cells, cut-out K):
+ * returns x' (and *sp = s'), or 0 when the equations assign it nowhere. */
+static long axis_target(long x, long s, long n, long K, long* sp) {
+    *sp = K - s + (K % 2);
+    if (*sp <= 0) return 0;
+    long dS = floor_div(K - n, 2);
+    for (long m = 1; m <= K; ++m) {
+        long alpha = m - dS;
+        if (eq5_wrap(alpha, n) != x) continue;
+        long xp = s - n + alpha + floor_div(n - 1, 2) - dS;
+        if (xp >= 1 && xp <= n) return xp;
+    }
+    return 0;
 }
 
 int oracle_paper_window(const void* H, void* Hp, int esize, int Nx, int Ny, int Nz,
@@ -209,51 +228,51 @@ int oracle_paper_window(const void* H, void* Hp, int esize, int Nx, int Ny, int 
     const char* src = (const char*)H;
     char* dst = (char*)Hp;
     size_t off = 0;
+    int twice = 0;
     for (int z = 0; z < Nz; ++z) {
-        long ns = Ks[z], nt = Kt[z], nx = Nx, ny = Ny;
+        long ns = Ks[z], nt = Kt[z];
         if (ns < 1 || nt < 1) return -1;
         size_t n = depth_elems(Nx, Ny, (int)ns, (int)nt);
         memset(dst + off * esize, 0, n * (size_t)esize);
-        long* alpha = (long*)malloc(sizeof(long) * (size_t)(ns + 1));
-        long* xm = (long*)malloc(sizeof(long) * (size_t)(ns + 1));
-        long* beta = (long*)malloc(sizeof(long) * (size_t)(nt + 1));
-        long* yn = (long*)malloc(sizeof(long) * (size_t)(nt + 1));
-        long* xp = (long*)malloc(sizeof(long) * (size_t)(ns + 1));
-        long* yp = (long*)malloc(sizeof(long) * (size_t)(nt + 1));
-        if (!alpha || !xm || !beta || !yn || !xp || !yp) {
-            free(alpha); free(xm); free(beta); free(yn); free(xp); free(yp);
+        /* per-axis targets of every source, tabulated: [x-1][s-1] -> x', s' */
+        long* tx = (long*)malloc(sizeof(long) * (size_t)(Nx * ns));
+        long* ts = (long*)malloc(sizeof(long) * (size_t)(Nx * ns));
+        long* ty = (long*)malloc(sizeof(long) * (size_t)(Ny * nt));
+        long* tt = (long*)malloc(sizeof(long) * (size_t)(Ny * nt));
+        unsigned char* hit = (unsigned char*)calloc(n, 1);
+        if (!tx || !ts || !ty || !tt || !hit) {
+            free(tx); free(ts); free(ty); free(tt); free(hit);
             return -2;
         }
-        long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);
-        for (long m = 1; m <= ns; ++m) { alpha[m] = m - dS; xm[m] = eq5_wrap(alpha[m], nx); }
-        for (long k = 1; k <= nt; ++k) { beta[k] = k - dT; yn[k] = eq5_wrap(beta[k], ny); }
-        for (long s = 1; s <= ns; ++s) {
-            long sp = ns - s + (ns % 2);
-            for (long m = 1; m <= ns; ++m)
-                xp[m] = s - nx + alpha[m] + floor_div(nx - 1, 2) - dS;
-            for (long t = 1; t <= nt; ++t) {
-                long tp = nt - t + (nt % 2);
-                for (long k = 1; k <= nt; ++k)
-                    yp[k] = t - ny + beta[k] + floor_div(ny - 1, 2) - dT;
-                if (sp <= 0 || tp <= 0) continue;
-                for (long m = 1; m <= ns; ++m) {
-                    if (xp[m] <= 0 || xp[m] > nx) continue;
-                    for (long k = 1; k <= nt; ++k) {
-                        if (yp[k] <= 0 || yp[k] > ny) continue;
-                        /* H(s,t,x,y) lives at [x-1][y-1][s-1][t-1] */
-                        size_t i_in = off + ((((size_t)(xm[m] - 1)) * Ny + (size_t)(yn[k] - 1)) * ns
-                                             + (size_t)(s - 1)) * nt + (size_t)(t - 1);
-                        size_t i_out = off + ((((size_t)(xp[m] - 1)) * Ny + (size_t)(yp[k] - 1)) * ns
-                                              + (size_t)(sp - 1)) * nt + (size_t)(tp - 1);
-                        memcpy(dst + i_out * esize, src + i_in * esize, (size_t)esize);
+        for (long x = 1; x <= Nx; ++x)
+            for (long s = 1; s <= ns; ++s)
+                tx[(x - 1) * ns + (s - 1)] = axis_target(x, s, Nx, ns, &ts[(x - 1) * ns + (s - 1)]);
+        for (long y = 1; y <= Ny; ++y)
+            for (long t = 1; t <= nt; ++t)
+                ty[(y - 1) * nt + (t - 1)] = axis_target(y, t, Ny, nt, &tt[(y - 1) * nt + (t - 1)]);
+        /* H(s, t, x, y) lives at [x-1][y-1][s-1][t-1]; so does H'(s', t', x', y') */
+        for (long x = 1; x <= Nx; ++x)
+            for (long y = 1; y <= Ny; ++y)
+                for (long s = 1; s <= ns; ++s) {
+                    long xp = tx[(x - 1) * ns + (s - 1)], sp = ts[(x - 1) * ns + (s - 1)];
+                    if (xp == 0) continue;
+                    for (long t = 1; t <= nt; ++t) {
+                        long yp = ty[(y - 1) * nt + (t - 1)], tp = tt[(y - 1) * nt + (t - 1)];
+                        if (yp == 0) continue;
+                        size_t i_in = ((((size_t)(x - 1)) * Ny + (size_t)(y - 1)) * ns
+                                       + (size_t)(s - 1)) * nt + (size_t)(t - 1);
+                        size_t i_out = ((((size_t)(xp - 1)) * Ny + (size_t)(yp - 1)) * ns
+                                        + (size_t)(sp - 1)) * nt + (size_t)(tp - 1);
+                        twice |= hit[i_out];
+                        hit[i_out] = 1;
+                        memcpy(dst + (off + i_out) * esize, src + (off + i_in) * esize,
+                               (size_t)esize);
                     }
                 }
-            }
-        }
-        free(alpha); free(xm); free(beta); free(yn); free(xp); free(yp);
+        free(tx); free(ts); free(ty); free(tt); free(hit);
         off += n;
     }
-    return 0;
+    return twice ? -3 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -790,6 +790,23 @@ int noalloc_setup(int dev, NoAllocDev** out) {
   return LFBP_OK;
 }
 
+// Tile-size target and tile count of a batch on the no-allocation path: the
+// default target, or larger tiles (fewer descriptors) when the list would not
+// fit the array.  Host only: no CUDA call.
+void noalloc_target(int n, const lfbp_plan* plans, const Tuning& dflt, int* target,
+                    long long* need) {
+  *target = dflt.tile_bytes;
+  for (int t : {dflt.tile_bytes, std::max(dflt.tile_bytes, 49152)}) {
+    *target = t;
+    *need = 0;
+    for (int i = 0; i < n; ++i) {
+      const std::vector<DepthTiling>& tl = plan_tiling(plans[i], t);
+      for (int z = 0; z < plans[i]->Nz; ++z) *need += (long long)plans[i]->Nx * tl[z].nU * tl[z].nV;
+    }
+    if (*need <= kNoAllocMaxTiles) return;
+  }
+}
+
 int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, void* const* out,
                         cudaStream_t st) {
   if (n < 0 || n > kMaxBatch) return fail(LFBP_ERR_INVALID, "batch size must be in [0, 64]");
@@ -810,25 +827,11 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
         return fail(LFBP_ERR_ALIAS, "two outputs overlap");
     }
   if (batch_empty(n, plans)) return LFBP_OK;  // nothing to map: no CUDA call at all
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  std::lock_guard<std::mutex> lk(g_mu);
-  NoAllocDev* nd = nullptr;
-  int rc = noalloc_setup(dev, &nd);
-  if (rc) return rc;
-  // the default tile size, or larger tiles when the list would not fit
+  // the size check comes before any CUDA call, so a batch too large for the
+  // array is refused without touching the device or the buffers
   Tuning tu = default_tuning();
   long long need = 0;
-  for (int target : {tu.tile_bytes, 49152}) {
-    tu.tile_bytes = target;
-    need = 0;
-    for (int i = 0; i < n; ++i) {
-      const std::vector<DepthTiling>& tl = plan_tiling(plans[i], target);
-      for (int z = 0; z < plans[i]->Nz; ++z) need += (long long)plans[i]->Nx * tl[z].nU * tl[z].nV;
-    }
-    if (need <= kNoAllocMaxTiles) break;
-  }
+  noalloc_target(n, plans, tu, &tu.tile_bytes, &need);
   if (need > kNoAllocMaxTiles) {
     char msg[160];
     std::snprintf(msg, sizeof(msg),
@@ -837,22 +840,41 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     return fail(LFBP_ERR_BAD_SHAPE, msg);
   }
   if (need == 0) return LFBP_OK;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  NoAllocDev* nd = nullptr;
+  int rc = noalloc_setup(dev, &nd);
+  if (rc) return rc;
   bool loaded = nd->tile_bytes == tu.tile_bytes && same_uids(nd->uids, n, plans);
   if (!loaded) {
+    // the new list is copied from host memory owned by this call; such a copy
+    // cannot be ordered into a stream that is being captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess)
+      return cuda_fail(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+      return fail(LFBP_ERR_INVALID,
+                  "the work list must be replaced, which cannot be done while the stream is "
+                  "capturing");
     std::vector<TileDesc> tiles;
     tiles.reserve((size_t)need);
     int max_tile = 0;
     build_tiles(n, plans, tu.tile_bytes, tiles, &max_tile);
     const int stage_bytes = (max_tile + 127) & ~127;
     const int per_cta_budget = std::min(nd->optin, (227 * 1024) / tu.ctas_per_sm - 1024);
-    int nst = per_cta_budget / (stage_bytes + kInfoBytes + 16);
-    if (nst < 2) nst = std::min(2, nd->optin / (stage_bytes + kInfoBytes + 16));
+    const int per_stage = stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
+    int nst = per_cta_budget / per_stage;
+    if (tu.stages > 0) nst = std::min(nst, tu.stages);
+    if (nst < 2) nst = std::min(2, nd->optin / per_stage);
     if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
     // stream-ordered: the kernels of earlier calls on this stream have read
     // the previous list before this copy overwrites it
     if ((e = cudaMemcpyAsync(nd->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(work list)");
+    // the copy reads `tiles` (pageable host memory) before returning
     nd->uids.clear();
     for (int i = 0; i < n; ++i) nd->uids.push_back(plans[i]->uid);
     nd->tile_bytes = tu.tile_bytes;

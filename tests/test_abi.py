@@ -240,6 +240,41 @@ def test_even_cutouts_need_the_paper_window(lib):
     lib.lfbp_plan_destroy(h)
 
 
+def test_noalloc_size_check_before_any_cuda_call(lib, monkeypatch):
+    """The no-allocation batched entry point counts a batch's tiles and refuses
+    one that its fixed work-list array cannot hold before its first CUDA call,
+    so the (never dereferenced) buffer addresses below are safe on a machine
+    without a GPU.  One depth of 51 x 51 cells with 1001 x 1001 cut-outs needs
+    459,459 tiles at the default 32 KiB target but 255,255 with 48 KiB tiles:
+    it fits through the larger-tile fallback; two such depths do not."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("fake buffer addresses may only meet a library that has no GPU")
+    monkeypatch.delenv("LFBP_TILE_BYTES", raising=False)
+    P = ctypes.c_void_p
+    A, B = 1 << 40, (1 << 40) + (1 << 39)
+    ins = ctypes.cast((P * 1)(A), P)
+    outs = ctypes.cast((P * 1)(B), P)
+    rc, two = _plan(lib, 51, 51, [1001] * 2, [1001] * 2)
+    assert rc == 0
+    assert lib.lfbp_backproject_batched_noalloc(1, ctypes.cast((P * 1)(two), P), ins, outs,
+                                                None) == -1
+    assert b"needs 510510 tiles" in lib.lfbp_last_error()
+    assert b"at most 262144" in lib.lfbp_last_error()
+    rc, one = _plan(lib, 51, 51, [1001], [1001])
+    assert rc == 0
+    for tile_bytes in (None, "16384", "65536"):
+        if tile_bytes:
+            monkeypatch.setenv("LFBP_TILE_BYTES", tile_bytes)
+        # past the size check: the next step is the first CUDA call, which
+        # fails here for want of a device
+        assert lib.lfbp_backproject_batched_noalloc(1, ctypes.cast((P * 1)(one), P), ins, outs,
+                                                    None) == -6, tile_bytes
+        assert b"cudaGetDevice" in lib.lfbp_last_error()
+    lib.lfbp_plan_destroy(one)
+    lib.lfbp_plan_destroy(two)
+
+
 @pytest.mark.parametrize("nparts", [1, 2, 3, 4, 8, 64])
 def test_plan_partition_covers_and_balances(lib, nparts):
     """Contiguous depth ranges covering every depth once, each boundary at the

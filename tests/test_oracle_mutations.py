@@ -25,18 +25,16 @@ MUTATIONS = {
                               "int a = (int)floor_mod(Xx + 1, Nx);"),
     "transpose_axes": ("int b = (int)floor_mod(Xy, Ny);\n                    int s = cutout_index(Sx, Xx, ks);",
                        "int b = (int)floor_mod(Xx, Ny);\n                    int s = cutout_index(Sx, Xx, ks);"),
-    "eq8_no_flip": ("long sp = ns - s + (ns % 2);", "long sp = s;"),
-    "eq6_offset": ("xp[m] = s - nx + alpha[m] + floor_div(nx - 1, 2) - dS;",
-                   "xp[m] = s - nx + alpha[m] + floor_div(nx - 1, 2) - dS + 1;"),
+    "eq8_no_flip": ("*sp = K - s + (K % 2);", "*sp = s;"),
+    "eq6_offset": ("long xp = s - n + alpha + floor_div(n - 1, 2) - dS;",
+                   "long xp = s - n + alpha + floor_div(n - 1, 2) - dS + 1;"),
     "eq5_wrap": ("if (alpha <= 0) return alpha + ceil_div(1 - alpha, n) * n;",
                  "if (alpha <= 0) return alpha + floor_div(1 - alpha, n) * n + n;"),
-    "eq4_alpha": ("long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);",
-                  "long dS = floor_div(ns - nx + 2, 2), dT = floor_div(nt - ny, 2);"),
+    "eq4_alpha": ("long dS = floor_div(K - n, 2);", "long dS = floor_div(K - n + 2, 2);"),
     # slips that only even cut-outs see (reading A2): the odd-K form of Eq. (8),
     # and Eq. (4)'s floor taken as a ceiling (equal when n_s - n_x is even)
-    "eq8_even_as_odd": ("long sp = ns - s + (ns % 2);", "long sp = ns - s + 1;"),
-    "eq4_even_ceil": ("long dS = floor_div(ns - nx, 2), dT = floor_div(nt - ny, 2);",
-                      "long dS = ceil_div(ns - nx, 2), dT = floor_div(nt - ny, 2);"),
+    "eq8_even_as_odd": ("*sp = K - s + (K % 2);", "*sp = K - s + 1;"),
+    "eq4_even_ceil": ("long dS = floor_div(K - n, 2);", "long dS = ceil_div(K - n, 2);"),
 }
 
 
