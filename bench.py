@@ -210,21 +210,44 @@ def _cpu_oracle_rate(specs, Hs_host, dtype_override, budget_s=12.0, max_passes=3
     oracle.transpose(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
     t1 = time.perf_counter() - t0
     oracle.threads(cores)
-    # the paper's own loop (Eqs. 4-9 with the loop ranges of Sec. 4, one element
-    # per innermost iteration, single-threaded) on the same depth: the paper's
-    # CPU algorithm as written, for context beside its published timings
-    t0 = time.perf_counter()
-    oracle.paper_window(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]])
-    t2 = time.perf_counter() - t0
     return {"value": done_bytes / t_total / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
             "seconds": round(t_total, 3),
             "sample": f"{done_bytes / 2 / 1e9:.2f} GB of H mapped by oracle.transpose "
                       f"({passes} pass(es) over {'+'.join(sample_desc)}; C, OpenMP {cores} threads)",
             "single_thread_GBps": round(2 * Hz.nbytes / t1 / 1e9, 3),
             "single_thread_sample": f"depth {z} of {s.name} (K = {s.Ks[z]}), 1 thread",
-            "paper_loop_single_thread_GBps": round(2 * Hz.nbytes / t2 / 1e9, 3),
-            "paper_loop_sample": "the same depth through oracle.paper_window (the paper's "
-                                 "loop of Sec. 4 in C), 1 thread"}
+            "closed_form": _cpu_closed_form_rate(specs, Hs_host)}
+
+
+def _cpu_closed_form_rate(specs, Hs_host, budget_s=6.0, max_passes=8):
+    """The paper's method on the host cores: the closed-form rearrangement of
+    Sec. 4 in C with OpenMP (oracle/lfbp_cpu_rearrange.c), over the whole
+    workload on all cores, and on one depth on one core."""
+    import numpy as np
+    import oracle
+    import lfgen
+    cores = oracle.cpu_rearrange_threads(0)
+    done, t_total, passes = 0, 0.0, 0
+    while passes < max_passes and t_total < budget_s:
+        for s, H in zip(specs, Hs_host):
+            t0 = time.perf_counter()
+            oracle.cpu_rearrange(H, s.Nx, s.Ny, s.Ks, s.Kt)
+            t_total += time.perf_counter() - t0
+            done += 2 * H.nbytes
+        passes += 1
+    s, H = specs[0], Hs_host[0]
+    off = lfgen.depth_offsets(s)
+    z = s.Nz // 2
+    Hz = np.ascontiguousarray(H[off[z]:off[z + 1]])
+    t0 = time.perf_counter()
+    oracle.cpu_rearrange(Hz, s.Nx, s.Ny, [s.Ks[z]], [s.Kt[z]], 1)
+    t1 = time.perf_counter() - t0
+    oracle.cpu_rearrange_threads(cores)
+    return {"value": round(done / t_total / 1e9, 3), "unit": "GB/s", "cores": cores,
+            "kind": "the paper's closed-form rearrangement (Sec. 4), C with OpenMP",
+            "sample": f"{passes} pass(es) over the whole workload ({done / 2 / 1e9:.2f} GB of H)",
+            "single_thread_GBps": round(2 * Hz.nbytes / t1 / 1e9, 3),
+            "single_thread_sample": f"depth {z} of {s.name} (K = {s.Ks[z]}), 1 thread"}
 
 
 def _reference_sample(specs, budget_elems=48_000_000):
@@ -485,12 +508,53 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         Hh = [h.cpu().numpy() for h in Hs]
         line["cpu_baseline"] = _cpu_oracle_rate(specs, Hh, args.dtype)
+    line["summary"] = _summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def _summary(line):
+    """The forms side by side in GB/s (batched / plain), last on the line."""
+    out = {"headline": {"batched": line["value"], "plain": line["plain"]["value"],
+                        "frac_of_measured_hbm": line["roofline"]["frac"]}}
+    ex = line.get("extra") or {}
+    for key in ("highres_fp16", "ragged", "mid", "highres_dense"):
+        if key in ex:
+            out[key] = {"batched": ex[key]["batched_GBps"], "plain": ex[key]["plain_GBps"]}
+    ek = (ex.get("paper_window") or {}).get("even_K")
+    if ek:
+        out["even_K"] = {"batched": ek.get("batched_GBps"), "plain": ek.get("plain_GBps")}
+    cb = line.get("cpu_baseline")
+    if cb:
+        out["cpu_GBps"] = {"oracle": round(cb["value"], 2), "cores": cb["cores"],
+                           "closed_form": cb["closed_form"]["value"],
+                           "closed_form_1_core": cb["closed_form"]["single_thread_GBps"]}
+    return out
+
+
+def _mid_extra(lf, timed, steps, world):
+    """The mid-resolution array (N = 15, 51 depths, K 45..165, fp32): the plain
+    form (one launch per depth) beside the batched form."""
+    import torch
+    import lfgen
+    s = lfgen.config_specs("mid")[0]
+    plan = lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float32)
+    H = lfgen.generate(s, device="cuda")
+    O = torch.empty_like(H)
+    nb = 2 * H.numel() * 4
+    tb, _, _ = timed(lambda: lf.backproject_batched([plan], [H], [O]), steps, 3)
+    tp, _, _ = timed(lambda: lf.backproject_array(plan, H, O), steps, 3)
+    res = {"workload": "mid: N=15, 51 depths, K_z 45..165, fp32", "bytes_per_step": nb,
+           "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
+           "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
+           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4), "plain_launches_per_step": s.Nz}
+    del H, O
+    torch.cuda.empty_cache()
+    return res
 
 
 def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
@@ -558,6 +622,7 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                      "tuned": _tuned_desc(rtuned)}
     del rH, rO
     torch.cuda.empty_cache()
+    res["mid"] = _mid_extra(lf, timed, steps, world)
     res["paper_window"] = _paper_window_extra(lf, specs, Hs, outs, timed, steps, world)
     res["table1"] = _table1_extra(lf, world, args.no_tune)
     res["rl_step"] = _rl_extra(lf, timed, steps)
@@ -578,19 +643,21 @@ def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
            "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
     # even cut-outs (the literal Eq. 8): the same depths with every K one larger,
-    # plain entry point only (element-by-element kernel)
+    # through the same tiled gather (the cropped odd cut-out under the window)
     if len(specs) == 1:
         s = specs[0]
         ke, kte = [k + 1 for k in s.Ks], [k + 1 for k in s.Kt]
         pe = lf.Plan(s.Nx, s.Ny, ke, kte, torch.float32, mode=lf.MAP_PAPER_WINDOW)
         He = torch.empty(pe.elems, dtype=torch.float32, device="cuda").uniform_()
         Oe = torch.empty_like(He)
+        tbe, _, _ = timed(lambda: lf.backproject_batched([pe], [He], [Oe]), steps, 3)
         te, _, _ = timed(lambda: lf.backproject_array(pe, He, Oe), steps, 3)
         nbe = 2 * pe.elems * 4
         res["even_K"] = {"K": "every highres K + 1", "bytes_per_step": nbe,
+                         "batched_GBps": round(world * nbe / (tbe * 1e-3) / 1e9, 1),
                          "plain_GBps": round(world * nbe / (te * 1e-3) / 1e9, 1),
-                         "plain_ms": round(te, 4),
-                         "kernel": "k_window_literal_rows (a row of segments through shared memory)"}
+                         "batched_ms": round(tbe, 4), "plain_ms": round(te, 4),
+                         "kernel": "k_gather_persistent / k_gather_depth (masked chunk path)"}
         del He, Oe
         torch.cuda.empty_cache()
     return res

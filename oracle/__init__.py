@@ -69,6 +69,52 @@ def _ints(xs: Sequence[int]) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(xs, dtype=np.int32))
 
 
+_CPU_SRC = os.path.join(_HERE, "lfbp_cpu_rearrange.c")
+_CPU_LIB_PATH = os.path.join(_HERE, "_build", "libcpu_rearrange.so")
+_cpu_lib = None
+
+
+def build_cpu_baseline(force: bool = False) -> str:
+    """Compile lfbp_cpu_rearrange.c into _build/libcpu_rearrange.so (gcc, OpenMP)."""
+    os.makedirs(os.path.dirname(_CPU_LIB_PATH), exist_ok=True)
+    if force or not os.path.exists(_CPU_LIB_PATH) or \
+            os.path.getmtime(_CPU_LIB_PATH) < os.path.getmtime(_CPU_SRC):
+        tmp = _CPU_LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC",
+                               "-o", tmp, _CPU_SRC])
+        os.replace(tmp, _CPU_LIB_PATH)
+    return _CPU_LIB_PATH
+
+
+def cpu_rearrange(H: np.ndarray, Nx: int, Ny: int, Ks, Kt=None, nthreads: int = 0) -> np.ndarray:
+    """The paper's closed-form rearrangement (Sec. 4) on the host cores: the CPU
+    baseline the benchmark times beside the oracle (not part of the oracle;
+    checked against ``transpose`` by the tests).  Odd cut-outs, 2- or 4-byte
+    elements."""
+    global _cpu_lib
+    if _cpu_lib is None:
+        lib = ctypes.CDLL(build_cpu_baseline())
+        P, I = ctypes.c_void_p, ctypes.c_int
+        lib.cpu_rearrange.argtypes = [P, P, I, I, I, I, P, P, I]
+        lib.cpu_rearrange.restype = I
+        lib.cpu_rearrange_threads.argtypes = [I]
+        lib.cpu_rearrange_threads.restype = I
+        _cpu_lib = lib
+    Kt = Ks if Kt is None else Kt
+    H = np.ascontiguousarray(H)
+    out = np.empty_like(H)
+    ks, kt = _ints(Ks), _ints(Kt)
+    _check(_cpu_lib.cpu_rearrange(_ptr(H), _ptr(out), H.itemsize, Nx, Ny, len(ks), _ptr(ks),
+                                  _ptr(kt), nthreads), "cpu_rearrange")
+    return out
+
+
+def cpu_rearrange_threads(n: int = 0) -> int:
+    """Threads the CPU baseline uses (n > 0 sets it)."""
+    cpu_rearrange(np.zeros(1, np.float32), 1, 1, [1], [1])  # loads the library
+    return _cpu_lib.cpu_rearrange_threads(int(n))
+
+
 def threads(n: int = 0) -> int:
     """Worker threads the oracle's OpenMP loops use (n > 0 sets it)."""
     return _load().oracle_threads(int(n))

@@ -18,8 +18,8 @@ LIB = os.path.join(BUILD, "liblfbp.so")
 # self-checking variant (-DLFBP_CHECK): bounds/alignment checks on every access
 LIB_CHECK = os.path.join(BUILD, "liblfbp_check.so")
 
-SOURCES = ["lfbp.cu", "lfbp_project.cu", "lfbp_window.cu"]
-HEADERS = ["lfbp_device.cuh", "lfbp_project.h", "lfbp_window.cuh"]
+SOURCES = ["lfbp.cu", "lfbp_project.cu"]
+HEADERS = ["lfbp_device.cuh", "lfbp_stripes.cuh", "lfbp_project.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

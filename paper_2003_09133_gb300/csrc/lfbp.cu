@@ -130,7 +130,10 @@ __global__ void __launch_bounds__(kPlainThreads)
 // out and the kernel ends with LFBP_ERR_TIMEOUT in the status word.  The
 // normal instantiation is kStall = false.
 template <bool kStall>
-__global__ void __launch_bounds__(kPersistentThreads, 3)
+#ifndef LFBP_PERSIST_MINB
+#define LFBP_PERSIST_MINB 3
+#endif
+__global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
     k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
                         const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
                         int nstages) {
@@ -194,14 +197,16 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
         issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
                          kProducerWarps);
       }
-      // the tile context is built while the copies are in flight
-      if (warp == 0) {
+      // the tile context is built while the copies are in flight, in eight
+      // parts shared by the producer warps (each part's branch runs on its own)
+      {
         unsigned char* info = info_base + (size_t)s * kInfoBytes;
-        if (lane == 0) *reinterpret_cast<int*>(info) = 0;
-        if (lane < 8)
+        if (warp == 0 && lane == 0) *reinterpret_cast<int*>(info) = 0;
+        constexpr int kParts = 8 / kProducerWarps;
+        if (lane < kParts)
           make_ctx_lane(*reinterpret_cast<TileCtx*>(info + 16), td, smem + (size_t)s * stage_bytes,
                         in_depth, ptrs.out[td.arr] + td.off_bytes,
-                        reinterpret_cast<int*>(info + 16 + kCtxBytes), lane);
+                        reinterpret_cast<int*>(info + 16 + kCtxBytes), warp * kParts + lane);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(fb);
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kPersistentThreads, 3)
       if (*reinterpret_cast<const int*>(info) != 0) break;
       // rotate the step-to-warp assignment by the tile's step count
       const TileCtx& tc = *reinterpret_cast<const TileCtx*>(info + 16);
-      const int nsteps = tc.fast ? tc.nunits : tc.items;
+      const int nsteps = tc.stripe ? tc.nsteps_s : (tc.fast ? tc.nunits : tc.items);
       gather_tile_ctx(tc, cw, kConsumerWarps, lane, (it * nsteps) % kConsumerWarps);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -258,7 +263,8 @@ struct lfbp_plan_s {
   std::vector<size_t> off;  // Nz + 1
   unsigned long long uid = 0;
   // an even cut-out (paper-window mode only): the map is the literal
-  // Eqs. (4)-(9) loop, run by the element kernel of lfbp_window.cu
+  // Eqs. (4)-(9) loop, which the gather runs as the cropped odd cut-out
+  // under the loop ranges' window; the projectors need odd cut-outs
   bool literal = false;
   // per-depth tilings by tile-size target (built lazily; entries stay put)
   std::mutex mu;
@@ -373,7 +379,8 @@ TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr)
   t.Kt = (unsigned short)p->Kt[z];
   t.P = (unsigned short)d.P;
   t.arr = (unsigned char)arr;
-  t.flags = (unsigned char)((p->es == 2 ? 1 : 0) | (mode << 1));
+  t.flags = (unsigned char)((p->es == 2 ? 1 : 0) | (mode << 1) | ((p->Ks[z] % 2 == 0) << 3) |
+                            ((p->Kt[z] % 2 == 0) << 4));
   return t;
 }
 
@@ -412,15 +419,6 @@ int run_plain(lfbp_plan p, const void* in, void* out, int mode, cudaStream_t st)
   int rc = check_buffers(p, in, out);
   if (rc) return rc;
   if (p->off.back() == 0) return LFBP_OK;  // an empty plan: no CUDA call at all
-  if (p->literal) {  // even cut-outs: the literal loop, depth by depth (mode 2: its adjoint)
-    for (int z = 0; z < p->Nz; ++z) {
-      const size_t o = p->off[z] * (size_t)p->es;
-      if (launch_window_literal((const unsigned char*)in + o, (unsigned char*)out + o, p->es,
-                                p->Nx, p->Ny, p->Ks[z], p->Kt[z], mode == 2 ? 1 : 0, st))
-        return fail(LFBP_ERR_CUDA, "k_window_literal launch failed");
-    }
-    return LFBP_OK;
-  }
   return launch_plain(p, (const unsigned char*)in, (unsigned char*)out, mode, 0, p->Nz, st);
 }
 
@@ -429,16 +427,6 @@ bool batch_empty(int n, const lfbp_plan* plans) {
   for (int i = 0; i < n; ++i)
     if (plans[i]->off.back() != 0) return false;
   return true;
-}
-
-// Entry points other than lfbp_backproject_array and lfbp_adjoint take odd
-// cut-outs only.
-int reject_literal(int n, const lfbp_plan* plans) {
-  for (int i = 0; i < n; ++i)
-    if (plans[i] && plans[i]->literal)
-      return fail(LFBP_ERR_BAD_SHAPE,
-                  "even cut-outs are taken by lfbp_backproject_array and lfbp_adjoint only");
-  return LFBP_OK;
 }
 
 // --------------------------------------------------- host-to-host pipeline --
@@ -481,7 +469,6 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
              cudaStream_t st) {
   int rc = check_buffers(p, dH, dHp);
   if (rc) return rc;
-  if ((rc = reject_literal(1, &p))) return rc;
   const size_t bytes = p->off.back() * (size_t)p->es;
   if (bytes == 0) return LFBP_OK;
   if (!H_host || !Hp_host) return fail(LFBP_ERR_NULL, "host buffer pointer is NULL");
@@ -673,7 +660,6 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     int rc = check_buffers(plans[i], in[i], out[i]);
     if (rc) return rc;
   }
-  if (int rc = reject_literal(n, plans)) return rc;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       const size_t bi = plans[i]->off.back() * plans[i]->es;
@@ -816,7 +802,6 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     int rc = check_buffers(plans[i], in[i], out[i]);
     if (rc) return rc;
   }
-  if (int rc = reject_literal(n, plans)) return rc;
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
       const size_t bi = plans[i]->off.back() * plans[i]->es;

@@ -78,7 +78,49 @@ __device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) {
 __device__ __forceinline__ uint32_t fmod_(uint32_t n, FastDiv f) { return n - fdiv(n, f) * f.d; }
 
 inline int lfbp_min(int a, int b) { return a < b ? a : b; }
+__host__ __device__ inline int lfbp_dmin(int a, int b) { return a < b ? a : b; }
 inline int lfbp_max(int a, int b) { return a > b ? a : b; }
+
+#ifndef LFBP_STRIPE_SMAX
+#define LFBP_STRIPE_SMAX 5
+#endif
+#ifndef LFBP_STRIPES
+#define LFBP_STRIPES 1  // 0: every tile takes the chunk or element-walk path
+#endif
+constexpr int kStripeMaxS = LFBP_STRIPE_SMAX;  // run blocks per stripe (template instances 1..)
+
+// Run blocks per stripe for nrb = ceil(Ny/4) run blocks: all of them up to
+// five; beyond, the size in 3..5 whose bands waste the fewest chunk slots
+// (ties: the larger).
+__host__ __device__ inline int stripe_S(int nrb) {
+  if (nrb <= kStripeMaxS) return nrb;
+  int best = kStripeMaxS, best_slots = 1 << 30;
+  for (int s = kStripeMaxS; s >= 3; --s) {
+    const int slots = ((nrb + s - 1) / s) * s;
+    if (slots < best_slots) {
+      best_slots = slots;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// 16-byte vectors a lane loads per stripe (the stretch of S windows plus the
+// segment phase, up to E-1 elements).
+__host__ __device__ constexpr int stripe_nv(int ES, int S) { return (16 / ES - 1 + 4 * S + 16 / ES - 1) / (16 / ES); }
+
+// Cut-out sizes of the map.  An even cut-out (the paper-window mode only,
+// flags bits 3 and 4 for Ks and Kt) is mapped as the odd cut-out one pixel
+// smaller: Eqs. 4-8 with even n_s read the pixels s < n_s - 1 and write the
+// positions s' < n_s - 1, as the transpose of that cropped cut-out would
+// (under the loop ranges' window); the last row or column stays zero.
+__host__ __device__ inline int map_ks(const TileDesc& td) { return td.Ks - ((td.flags >> 3) & 1); }
+__host__ __device__ inline int map_kt(const TileDesc& td) { return td.Kt - ((td.flags >> 4) & 1); }
+// Source pixels of a tile's columns v0 .. v0+ncols-1: those with v < Ktm.
+__host__ __device__ inline int tile_nseg(const TileDesc& td) {
+  const int n = map_kt(td) - (int)td.v0;
+  return n < 0 ? 0 : (n > (int)td.ncols ? (int)td.ncols : n);
+}
 
 // Row pitch (elements) of a tile whose slots have pitch P.
 __host__ __device__ inline int row_pitch(int Ny, int P, int es) {
@@ -134,10 +176,65 @@ inline double pitch_cost(int Ny, int Ks, int Kt, int ncols, int es, int P) {
   return count ? (double)total / count : 0.0;
 }
 
+// The same for the stripe path (lfbp_stripes.cuh): lane 4s + g of a warp
+// loads NV consecutive 16-byte vectors of segment (B + 4s + g) mod Ny from
+// stage element R + ncols - 1 + b*P - V - 4s - g on (rounded down to 16
+// bytes); each quarter-warp of a 16-byte load is one wavefront per distinct
+// vector that shares a bank group with another.
+inline double pitch_cost_stripes(int Ny, int ncols, int es, int P) {
+  const int E = 16 / es;
+  const int NV = stripe_nv(es, stripe_S((Ny + 3) >> 2));
+  uint32_t rng = 0x85ebca6bu ^ (uint32_t)((uint32_t)P * 2246822519u);
+  long long total = 0;
+  int count = 0;
+  for (int trial = 0; trial < 48; ++trial) {
+    rng = rng * 1664525u + 1013904223u;
+    const int B0 = (int)((rng >> 8) % (uint32_t)Ny);
+    rng = rng * 1664525u + 1013904223u;
+    const int R = (int)((rng >> 8) % (uint32_t)E);
+    rng = rng * 1664525u + 1013904223u;
+    const int V0 = (int)((rng >> 8) % (uint32_t)lfbp_max(1, ncols));
+    long long unit[32];
+    for (int l = 0; l < 32; ++l) {
+      const int gs = l >> 2, g = l & 3;
+      const int b = (B0 + 4 * gs + g) % Ny;
+      const long long X = (long long)R + ncols - 1 + (long long)b * P - (V0 + 4 * gs) - g;
+      const long long A = X >= 0 ? X / E : -((-X + E - 1) / E);  // floor(X / E)
+      unit[l] = A;
+    }
+    for (int v = 0; v < NV; ++v) {
+      for (int h = 0; h < 4; ++h) {
+        int worst = 0;
+        for (int bank = 0; bank < 8; ++bank) {
+          long long seen[8];
+          int ns = 0;
+          for (int l = 8 * h; l < 8 * h + 8; ++l) {
+            const long long u = unit[l] + v;
+            if ((int)(((u % 8) + 8) % 8) != bank) continue;
+            bool dup = false;
+            for (int s2 = 0; s2 < ns; ++s2) dup = dup || seen[s2] == u;
+            if (!dup) seen[ns++] = u;
+          }
+          worst = lfbp_max(worst, ns);
+        }
+        total += worst;
+      }
+      ++count;
+    }
+  }
+  return count ? (double)total / count : 0.0;
+}
+
+// Tiles taken by the stripe consumer (lfbp_stripes.cuh) in either map mode.
+__host__ __device__ inline bool stripe_shape(int Ny, int Ks, int Kt, int ncols) {
+  return LFBP_STRIPES && (((long long)Ks * Kt) & 3) == 1 && Ny >= 3 && ncols >= 8;
+}
+
 // Slot pitch for segments of ncols elements: P >= ncols + 2E - 2 (room for a
 // copy widened to 16-byte boundaries), P = Ks*Kt (mod E), fewest conflicts.
 inline int choose_pitch(int Ny, int Ks, int Kt, int ncols, int es) {
   const int E = 16 / es;
+  const bool stripes = stripe_shape(Ny, Ks, Kt, ncols);
   const int KKm = (int)(((long long)Ks * Kt) % E);
   int P0 = ncols + 2 * E - 2;
   P0 += ((KKm - P0) % E + E) % E;
@@ -145,7 +242,8 @@ inline int choose_pitch(int Ny, int Ks, int Kt, int ncols, int es) {
   double best_cost = 1e30;
   for (int x = 0; x < 8; ++x) {
     const int P = P0 + x * E;
-    const double cost = pitch_cost(Ny, Ks, Kt, ncols, es, P);
+    const double cost =
+        stripes ? pitch_cost_stripes(Ny, ncols, es, P) : pitch_cost(Ny, Ks, Kt, ncols, es, P);
     if (cost < best_cost - 1e-9) {
       best_cost = cost;
       best = P;
@@ -279,6 +377,13 @@ __device__ __forceinline__ uint16_t lds<uint16_t>(uint32_t addr) {
   asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(addr));
+  return v;
+}
 // shared-memory load at a compile-time byte offset from a 32-bit address
 template <class T, int OFF>
 __device__ __forceinline__ T lds_off(uint32_t addr) {
@@ -353,9 +458,10 @@ __device__ __forceinline__ uint32_t tile_copies(const TileDesc& td, const unsign
   const int Nx = td.Nx, Ny = td.Ny, Ks = td.Ks, Kt = td.Kt, P = td.P;
   const int RP = row_pitch(Ny, P, es);
   const int nslots = td.nrows * Ny;
-  const int cs = (Ks - 1) / 2;
-  const int t_lo = Kt - td.v0 - td.ncols;
-  const uint32_t seg_bytes = (uint32_t)td.ncols * es;
+  const int Ksm = map_ks(td), nseg = tile_nseg(td);
+  const int cs = (Ksm - 1) / 2;
+  const int t_lo = map_kt(td) - td.v0 - nseg;
+  const uint32_t seg_bytes = (uint32_t)nseg * es;
   const unsigned long long KK = (unsigned long long)Ks * Kt;
   const unsigned long long NKK = (unsigned long long)Ny * KK;
   const FastDiv fNy = make_fastdiv(Ny), fNx = make_fastdiv(Nx);
@@ -366,16 +472,20 @@ __device__ __forceinline__ uint32_t tile_copies(const TileDesc& td, const unsign
   const unsigned char* in_array = in_depth - td.off_bytes;
 #endif
   // slot i = (row j, segment b): row j reads H[a_j][b][s_j][t_lo..], with
-  // a_j = (p + u0 + j - c_s) mod Nx and s_j = Ks - 1 - u0 - j
+  // a_j = (p + u0 + j - c_s) mod Nx and s_j = Ksm - 1 - u0 - j (no copy for
+  // the zero row of an even cut-out, s_j < 0, nor for an empty segment)
   const int slot0 = pw * 32 + lane, slot_step = 32 * np;
+  const int jmax = (int)td.nrows < Ksm - (int)td.u0 ? (int)td.nrows : Ksm - (int)td.u0;  // rows with a source
+  const int ncopy = nseg > 0 && jmax > 0 ? jmax * Ny : 0;
+  (void)nslots;
   uint32_t my_bytes = 0;
   if (count_only) {
-    for (int i = slot0; i < nslots; i += slot_step) {
+    for (int i = slot0; i < ncopy; i += slot_step) {
       const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
       const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
       const unsigned long long seg =
           (unsigned long long)a * NKK + (unsigned long long)b * KK +
-          (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
+          (unsigned long long)(Ksm - 1 - td.u0 - j) * Kt + t_lo;
       const uintptr_t src = (uintptr_t)(in_depth + seg * es);
       const uintptr_t lo = src & ~(uintptr_t)15;
       uintptr_t hi = (src + seg_bytes + 15) & ~(uintptr_t)15;
@@ -385,11 +495,11 @@ __device__ __forceinline__ uint32_t tile_copies(const TileDesc& td, const unsign
     return my_bytes;
   }
   bool fixed = false;
-  for (int i = slot0; i < nslots; i += slot_step) {
+  for (int i = slot0; i < ncopy; i += slot_step) {
     const int j = (int)fdiv((uint32_t)i, fNy), b = i - j * Ny;
     const int a = (int)fmod_((uint32_t)(a0 + j), fNx);
     const unsigned long long seg0 =
-        (unsigned long long)a * NKK + (unsigned long long)(Ks - 1 - td.u0 - j) * Kt + t_lo;
+        (unsigned long long)a * NKK + (unsigned long long)(Ksm - 1 - td.u0 - j) * Kt + t_lo;
     const unsigned long long seg = seg0 + (unsigned long long)b * KK;
     const uintptr_t src = (uintptr_t)(in_depth + seg * es);
     // phases (elements mod E) of segments (j, 0) and (j, b)
@@ -461,6 +571,12 @@ struct alignas(16) TileCtx {
   unsigned char* out_lo;    // the depth's output bytes [out_lo, out_hi)
   unsigned char* out_hi;
   int Nx, Ny, Ks, Kt, ncols, L, P, RP;
+  int Ksm, Ktm;  // cut-out sizes of the map (Ks, Kt, or one less when even)
+  int nseg;      // source pixels per segment: the columns v < Ktm of the tile
+  int even;      // nonzero: an even cut-out (zero row / column, clamped reads)
+  // paper-window masks (modes 1 and 2), as per-tile bounds on row j, column
+  // vl, run q and cells a, b (see keep_elem)
+  int m1_j0, m1_jw, m1_q0, m2_a, m2_b, Ks1, Kt1, jlim, vlim;
   int p, u0, v0;
   int cb;    // (v0 - c_t) mod Ny
   int ap0;   // (p + u0 - c_s) mod Nx
@@ -488,6 +604,14 @@ struct alignas(16) TileCtx {
   uint32_t W;      // bytes of Ny slots: Ny * P * es
   int fast;        // 1: chunk path (mode 0 or 1, ncols >= 16/es, Ny >= 16/es)
   FastDiv fncols, fNy, fNx, fngc, fngm;
+  // stripe path (lfbp_stripes.cuh)
+  int stripe;      // 1: stripe path (mode 0 or 1, Ks*Kt = 1 mod 4, Ny >= 3, ncols >= 8)
+  int S;           // run blocks of 4 runs per stripe
+  int ns;          // stripes per row and band
+  int rowns;       // nrows * ns
+  int nitems_s;    // stripes of the tile: bands * nrows * ns
+  int nsteps_s;    // warp steps: ceil(nitems_s / 8)
+  FastDiv fns, frowns, fnb;  // by ns, rowns, nrows + 1
 };
 
 // Row base of tile row j (elements): the stage index of element t_lo + ncols - 1
@@ -498,11 +622,12 @@ struct alignas(16) TileCtx {
 __device__ __forceinline__ int row_base(const TileDesc& td, const unsigned char* in_depth, int j) {
   const int ES = (td.flags & 1) ? 2 : 4, E = 16 / ES;
   const long long KK = (long long)td.Ks * td.Kt;
-  const int a = pos_mod((int)td.p + (int)td.u0 + j - (td.Ks - 1) / 2, td.Nx);
-  const long long t_lo = (long long)td.Kt - td.v0 - td.ncols;
-  const long long seg0 = (long long)a * td.Ny * KK + (long long)(td.Ks - 1 - td.u0 - j) * td.Kt + t_lo;
+  const int Ksm = map_ks(td), nseg = tile_nseg(td);
+  const int a = pos_mod((int)td.p + (int)td.u0 + j - (Ksm - 1) / 2, td.Nx);
+  const long long t_lo = (long long)map_kt(td) - td.v0 - nseg;
+  const long long seg0 = (long long)a * td.Ny * KK + (long long)(Ksm - 1 - td.u0 - j) * td.Kt + t_lo;
   const int ph = (int)(((long long)((uintptr_t)in_depth / ES) + seg0) & (E - 1));
-  return j * row_pitch(td.Ny, td.P, ES) + ph + td.ncols - 1;
+  return j * row_pitch(td.Ny, td.P, ES) + ph + nseg - 1;
 }
 
 // Lane `lane` (0..7) of a warp fills its share of the tile context; the
@@ -534,8 +659,26 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       c.p = td.p;
       c.u0 = td.u0;
       c.v0 = td.v0;
-      c.s0 = td.Ks - 1 - td.u0;
+      c.Ksm = map_ks(td);
+      c.Ktm = map_kt(td);
+      c.nseg = tile_nseg(td);
+      c.even = (td.flags >> 3) & 3;
+      c.s0 = c.Ksm - 1 - td.u0;
       c.nrows = td.nrows;
+      if (c.mode != 0) {
+        const int hx = (td.Nx - 1) >> 1, hy = (td.Ny - 1) >> 1;
+        c.Ks1 = td.Ks - 1;
+        c.Kt1 = td.Kt - 1;
+        c.jlim = c.Ksm - (int)td.u0;
+        c.vlim = c.Ktm - (int)td.v0;
+        const int j0 = hx - (int)td.p - (int)td.u0;
+        const int j1 = lfbp_dmin(td.Ks - 1 + j0, c.jlim - 1);
+        c.m1_j0 = j1 >= j0 ? j0 : (1 << 20);  // no row kept: an empty range
+        c.m1_jw = j1 >= j0 ? j1 - j0 : 0;
+        c.m1_q0 = hy - (int)td.v0;
+        c.m2_a = c.s0 - hx;
+        c.m2_b = c.Ktm - 1 - (int)td.v0 - hy;
+      }
       c.tab_s = smem_addr(tab);
       c.fast = c.mode <= 1 && td.ncols >= E && td.Ny >= E;
       break;
@@ -552,9 +695,26 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       c.sbn = GE % td.Ny;
       c.cmn = td.ncols % td.Ny;
       break;
-    case 3:
+    case 3: {
       c.fNx = make_fastdiv(td.Nx);
+      c.stripe = ((td.flags >> 1) & 3) <= 1 && stripe_shape(td.Ny, td.Ks, td.Kt, td.ncols);
+      if (!c.stripe) break;
+      const int nrb = (td.Ny + 3) >> 2;
+      const int S = stripe_S(nrb);
+      const int nbands = (nrb + S - 1) / S;
+      const int ns = (td.ncols - 1 + 4 * (S - 1)) / 4 + 1;
+      const long long items = (long long)nbands * td.nrows * ns;
+      c.S = S;
+      c.ns = ns;
+      c.rowns = td.nrows * ns;
+      c.nitems_s = (int)(items < 65535 ? items : 65535);
+      c.nsteps_s = (c.nitems_s + 7) >> 3;
+      c.fns = make_fastdiv(ns);
+      c.frowns = make_fastdiv(c.rowns < 65535 ? c.rowns : 65535);
+      c.fnb = make_fastdiv(td.nrows + 1);
+      c.stripe = items < 65535 && c.rowns < 65535;
       break;
+    }
     case 4: {
       const int ng = (L + 2 * GE - 2) / GE;  // groups per run, any alignment
       const int ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
@@ -567,9 +727,9 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       break;
     }
     case 5:
-      c.cb = pos_mod((int)td.v0 - (td.Kt - 1) / 2, td.Ny);
+      c.cb = pos_mod((int)td.v0 - (map_kt(td) - 1) / 2, td.Ny);
       c.cbb = c.cb + ((GE + td.Ny - 1) / td.Ny) * td.Ny;
-      c.ap0 = pos_mod((int)td.p + (int)td.u0 - (td.Ks - 1) / 2, td.Nx);
+      c.ap0 = pos_mod((int)td.p + (int)td.u0 - (map_ks(td) - 1) / 2, td.Nx);
       break;
     case 6: {
       const unsigned long long run0 =
@@ -583,7 +743,7 @@ __device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
       break;
     }
     case 7: {
-      const int t_lo = td.Kt - td.v0 - td.ncols;
+      const int t_lo = map_kt(td) - td.v0 - tile_nseg(td);
       c.inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
       c.nkk = (int)(((unsigned long long)td.Ny * KK) & (E - 1));
       c.ktm = td.Kt & (E - 1);
@@ -653,6 +813,34 @@ __device__ __forceinline__ void store_out16(const TileCtx& c, unsigned char* p, 
   st_global(reinterpret_cast<uint4*>(p), v);
 }
 
+__device__ __forceinline__ void store_out8(const TileCtx& c, unsigned char* p, uint32_t lo,
+                                           uint32_t hi) {
+#if LFBP_CHECKED
+  if (p < c.out_lo || p + 8 > c.out_hi || ((uintptr_t)p & 7)) {
+    check_fail(2, (long long)(p - c.out_lo), (long long)(c.out_hi - c.out_lo));
+    return;
+  }
+#endif
+  (void)c;
+  uint2 v;
+  v.x = lo;
+  v.y = hi;
+  st_global(reinterpret_cast<uint2*>(p), v);
+}
+
+// 16-byte shared-memory load of the tile's stage at a 16-byte-aligned address.
+__device__ __forceinline__ uint4 lds_v4(const TileCtx& c, uint32_t addr) {
+#if LFBP_CHECKED
+  const long long rel = (long long)addr - (long long)c.stage_s;
+  if (rel < 0 || rel + 16 > c.tile_bytes || (rel & 15)) {
+    check_fail(1, rel, c.tile_bytes);
+    return make_uint4(0, 0, 0, 0);
+  }
+#endif
+  (void)c;
+  return lds128(addr);
+}
+
 template <class T>
 __device__ __forceinline__ void store_out(const TileCtx& c, T* p, T v) {
 #if LFBP_CHECKED
@@ -677,20 +865,23 @@ __device__ __forceinline__ int src_index(const TileCtx& c, int q, int e, int& j,
   a = (int)fmod_((uint32_t)(c.ap0 + j), c.fNx);
   const int ph = (c.inm + a * c.nkk + (c.s0 - j) * c.ktm) & (E - 1);
   b = (int)fmod_((uint32_t)(q + c.cb + vl), c.fNy);
-  return j * c.RP + ph + b * c.P + c.ncols - 1 - vl;
+  return j * c.RP + ph + b * c.P + c.nseg - 1 - vl;
 }
 
 template <int MODE>
 __device__ __forceinline__ bool keep_elem(const TileCtx& c, int q, int j, int vl, int b, int a) {
   if (MODE == 0) return true;
-  const int hx = (c.Nx - 1) >> 1, hy = (c.Ny - 1) >> 1;
-  if (MODE == 1) {  // forward paper window: on the output position (p, u, q, v)
-    const int pu = c.p + c.u0 + j, qv = q + c.v0 + vl;
-    return pu >= hx && pu <= c.Ks - 1 + hx && qv >= hy && qv <= c.Kt - 1 + hy;
+  // rows and columns past the map's cut-out (the last of an even one) are zero
+  if (MODE == 1) {
+    // forward paper window, on the output position (p, u, q, v):
+    // p + u0 + j - h_x in [0, Ks-1], u0 + j < Ksm, q + v0 + vl - h_y in [0, Kt-1], v0 + vl < Ktm
+    return (unsigned)(j - c.m1_j0) <= (unsigned)c.m1_jw &&
+           (unsigned)(q + vl - c.m1_q0) <= (unsigned)c.Kt1 && vl < c.vlim;
   }
-  // adjoint of the paper window: on the source position (a, s, b, t)
-  const int as = a + c.s0 - j, bt = b + c.Kt - 1 - c.v0 - vl;
-  return as >= hx && as <= c.Ks - 1 + hx && bt >= hy && bt <= c.Kt - 1 + hy;
+  // adjoint of the paper window, on the source position (a, s, b, t):
+  // a + s - h_x in [0, Ks-1], b + t - h_y in [0, Kt-1], and the output inside the map's cut-out
+  return j < c.jlim && vl < c.vlim && (unsigned)(a - j + c.m2_a) <= (unsigned)c.Ks1 &&
+         (unsigned)(b - vl + c.m2_b) <= (unsigned)c.Kt1;
 }
 
 // n / d for d >= 2 (no special case for d = 1); exact while n*d < 2^32.
@@ -787,9 +978,8 @@ __device__ __forceinline__ bool chunk_keep(const TileCtx& c, const ChunkAddr& s,
   const bool nxt = !ONEROW && k >= s.kx;
   const int j = nxt ? s.j + 1 : s.j;
   const int vl = nxt ? k - s.kx : s.vl + k;
-  const int pu = c.p + c.u0 + j - ((c.Nx - 1) >> 1);
-  const int qv = q + c.v0 + vl - ((c.Ny - 1) >> 1);
-  return (unsigned)pu <= (unsigned)(c.Ks - 1) && (unsigned)qv <= (unsigned)(c.Kt - 1);
+  return (unsigned)(j - c.m1_j0) <= (unsigned)c.m1_jw &&
+         (unsigned)(q + vl - c.m1_q0) <= (unsigned)c.Kt1 && vl < c.vlim;
 }
 
 template <class T, bool MASK, bool ONEROW>
@@ -810,6 +1000,15 @@ __device__ __forceinline__ uint32_t chunk_elem(const TileCtx& c, const ChunkAddr
   uint32_t a = (nxt ? s.B : s.A) + (uint32_t)k * c.D;
   if (k >= (nxt ? s.kwB : s.kwA)) a -= c.W;
   return a;
+}
+
+// The same, for a chunk whose elements may be masked: a masked element in
+// the zero column of an even cut-out can sit one element before the stage;
+// it is read inside the stage instead (the value is dropped either way).
+template <bool MASK, bool ONEROW>
+__device__ __forceinline__ uint32_t chunk_elem_c(const TileCtx& c, const ChunkAddr& s, int k) {
+  const uint32_t a = chunk_elem<ONEROW>(c, s, k);
+  return MASK && (int)(a - c.stage_s) < 0 ? c.stage_s : a;
 }
 
 template <int ES, bool ONEROW, bool MASK>
@@ -842,7 +1041,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
       T v[EPL];
       static_for<0, EPL>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        v[k] = masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k)));
+        v[k] = masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem_c<MASK, ONEROW>(c, s, k)));
       });
       store_out16(c, dst, pack16(v));
     } else {
@@ -850,7 +1049,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
       for (int k = 0; k < EPL; ++k) {
         if (e + k < 0 || e + k >= L) continue;
         store_out(c, reinterpret_cast<T*>(dst) + k,
-                  masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k))));
+                  masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem_c<MASK, ONEROW>(c, s, k))));
       }
     }
   }
@@ -876,7 +1075,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
     for (int k = 0; k < EPL; ++k) {
       if (e + k < 0 || e + k >= L) continue;
       store_out(c, reinterpret_cast<T*>(dst) + k,
-                masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem<ONEROW>(c, s, k))));
+                masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem_c<MASK, ONEROW>(c, s, k))));
     }
   }
 }
@@ -942,7 +1141,8 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
         for (int ii = 0; ii < EPL; ++ii) {
           v[ii] = 0;
           if (ii < i0 || e + ii >= L) continue;
-          T x = smem_load<T>(c, trb + tb * P - tv);
+          const int ix = trb + tb * P - tv;  // -1 only for a masked zero-column element
+          T x = smem_load<T>(c, ix < 0 ? 0 : ix);
           if (!keep_elem<MODE>(c, q, tj, tv, tb, ta)) x = 0;
           v[ii] = x;
           if (!allv) store_out(c, reinterpret_cast<T*>(orow) + (e + ii), x);
@@ -952,7 +1152,7 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
             tv = 0;
             ++tj;
             ta = ta + 1 == Nx ? 0 : ta + 1;
-            trb = tj * RP + ((c.inm + ta * c.nkk + (c.s0 - tj) * c.ktm) & (E - 1)) + ncols - 1;
+            trb = tj * RP + ((c.inm + ta * c.nkk + (c.s0 - tj) * c.ktm) & (E - 1)) + c.nseg - 1;
             tb = bq0;
           }
         }
@@ -971,15 +1171,27 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
           b -= c.cmn;
           if (b < 0) b += Ny;
         } while (vl >= ncols);
-        rb = j * RP + ((c.inm + a * c.nkk + (c.s0 - j) * c.ktm) & (E - 1)) + ncols - 1;
+        rb = j * RP + ((c.inm + a * c.nkk + (c.s0 - j) * c.ktm) & (E - 1)) + c.nseg - 1;
       }
     }
   }
 }
 
+}  // namespace lfbp
+
+#include "lfbp_stripes.cuh"
+
+namespace lfbp {
+
 // Consumer side, given the tile's context (in shared memory).
 __device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane,
                                                 int rot = 0) {
+#if !defined(LFBP_HOST_EMULATION) && LFBP_STRIPES
+  if (cs.stripe) {
+    gather_stripes_ctx(cs, w, nwarps, lane, rot);
+    return;
+  }
+#endif
   const TileCtx c = cs;  // into registers, once per tile
   if (c.fast) {
     if (c.mode == 0) {

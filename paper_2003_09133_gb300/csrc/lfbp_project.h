@@ -50,12 +50,4 @@ int launch_rl_sum_quotient(const float* parts, int Nz, long long n, const float*
                            cudaStream_t st);
 int launch_fill(float* x, long long n, float v, cudaStream_t st);
 
-// (lfbp_window.cu) One depth of the paper-window map with the literal loop
-// ranges of Eqs. (4)-(9), for cut-outs of either parity (even ones: Eq. 8's
-// partial map), element by element: adjoint = 0 gathers H -> H' (0 where the
-// loop writes nothing), adjoint = 1 zeroes `out` and moves each written
-// entry of the H'-shaped `in` back to its source.  esize 2 or 4.
-int launch_window_literal(const void* in_depth, void* out_depth, int esize, int Nx, int Ny, int Ks,
-                          int Kt, int adjoint, cudaStream_t st);
-
 }  // namespace lfbp

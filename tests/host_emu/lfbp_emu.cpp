@@ -20,10 +20,14 @@
 #define __device__
 #define __host__
 #define __forceinline__ inline
+#define __noinline__
 #define LFBP_HOST_EMULATION 1
 
 struct uint4 {
   unsigned x, y, z, w;
+};
+struct uint2 {
+  unsigned x, y;
 };
 
 namespace {
@@ -114,6 +118,15 @@ template <class T, int OFF>
 static inline T lds_off(uint32_t addr) {
   return lds<T>(addr + OFF);
 }
+static inline uint4 lds128(uint32_t addr) {
+  uint4 v{0, 0, 0, 0};
+  if (addr >= kTabBase || (size_t)addr + 16 > g_stage_bytes || (addr & 15)) {
+    err("16-byte lds outside stage or misaligned", addr, (long long)g_stage_bytes);
+    return v;
+  }
+  std::memcpy(&v, g_stage + addr, 16);
+  return v;
+}
 template <class T>
 static inline void st_global(T* p, T v) {
   if ((uintptr_t)p & (sizeof(T) - 1)) err("store misaligned", (long long)((uintptr_t)p & 15), (long long)sizeof(T));
@@ -129,10 +142,87 @@ using namespace lfbp;
 
 extern "C" const char* emu_message() { return g_msg; }
 
+// The stripe consumer of one tile with the lanes of each warp run in lock
+// step: per warp step and stripe, the four lanes of the group load and cut
+// out their windows, exchange them through arrays with the same per-lane
+// stage functions the kernel uses between its shuffles, and store; then the
+// edge pass, lane by lane.
+template <int ES, int S, bool MASK>
+static void emu_stripes(const TileCtx& c, int nwarps, int rot) {
+  for (int w = 0; w < nwarps; ++w) {
+    int first = (w - rot) % nwarps;
+    if (first < 0) first += nwarps;
+    for (int u = first; u < c.nsteps_s; u += nwarps)
+      for (int gs = 0; gs < 8; ++gs) {
+        int item = u * 8 + gs;
+        const bool ok = item < c.nitems_s;
+        if (!ok) item = c.nitems_s - 1;
+        StripeStream st[4];
+        StripePos sp[4];
+        for (int g = 0; g < 4; ++g) {
+          sp[g] = stripe_pos<S>(c, item);
+          stripe_begin<ES>(c, sp[g], g, st[g]);
+        }
+        static_for<0, S>([&](auto ic) {
+          constexpr int i = decltype(ic)::value;
+          uint32_t x[4][ES == 4 ? 4 : 2];
+          for (int g = 0; g < 4; ++g) stripe_window<ES, i>(c, st[g], x[g]);
+          if constexpr (ES == 4) {
+            uint32_t snd[4][2], rcv[2];
+            for (int g = 0; g < 4; ++g) xs_a32(x[g], g, snd[g]);
+            for (int g = 0; g < 4; ++g) {
+              rcv[0] = snd[g ^ 2][0];
+              rcv[1] = snd[g ^ 2][1];
+              xr_a32(x[g], g, rcv);
+            }
+            for (int g = 0; g < 4; ++g) xs_b32(x[g], g, snd[g]);
+            for (int g = 0; g < 4; ++g) {
+              rcv[0] = snd[g ^ 1][0];
+              rcv[1] = snd[g ^ 1][1];
+              xr_b32(x[g], g, rcv);
+            }
+          } else {
+            uint32_t snd[4];
+            for (int g = 0; g < 4; ++g) snd[g] = xs_a16(x[g], g);
+            for (int g = 0; g < 4; ++g) xr_a16(x[g], g, snd[g ^ 2]);
+            for (int g = 0; g < 4; ++g) snd[g] = xs_b16(x[g], g);
+            for (int g = 0; g < 4; ++g) xr_b16(x[g], g, snd[g ^ 1]);
+          }
+          for (int g = 0; g < 4; ++g) stripe_store<ES, i, MASK>(c, sp[g], g, ok, x[g]);
+        });
+      }
+  }
+  for (int w = 0; w < nwarps; ++w)
+    for (int lane = 0; lane < 32; ++lane) stripe_edges<ES, MASK>(c, w, nwarps, lane, rot);
+}
+
+template <int ES, bool MASK>
+static void emu_stripes_s(const TileCtx& c, int nwarps, int rot) {
+  switch (c.S) {
+    case 1: emu_stripes<ES, 1, MASK>(c, nwarps, rot); break;
+    case 2: emu_stripes<ES, 2, MASK>(c, nwarps, rot); break;
+    case 3: emu_stripes<ES, 3, MASK>(c, nwarps, rot); break;
+    case 4: emu_stripes<ES, 4, MASK>(c, nwarps, rot); break;
+    case 5: emu_stripes<ES, 5, MASK>(c, nwarps, rot); break;
+    default: err("stripe length beyond the instances", c.S, 0); break;
+  }
+}
+
+static void emu_stripes_ctx(const TileCtx& c, int nwarps, int rot) {
+  if (c.es == 4) {
+    if (c.mode == 0) emu_stripes_s<4, false>(c, nwarps, rot);
+    else emu_stripes_s<4, true>(c, nwarps, rot);
+  } else {
+    if (c.mode == 0) emu_stripes_s<2, false>(c, nwarps, rot);
+    else emu_stripes_s<2, true>(c, nwarps, rot);
+  }
+}
+
 // Runs every tile of every depth of one array through the tile code.
 // Returns the number of violations (0 = clean); stats[0] = tiles, stats[1] =
 // bytes copied by bulk copies, stats[2] = max tile bytes, stats[3] = tiles
-// that took the chunk path.  nthr = consumer warps.
+// whose context selects the chunk path, stats[4] = tiles that took the stripe
+// path (which comes first).  nthr = consumer warps.
 extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned char* counts,
                         int Nx, int Ny, int Nz, const int* Ks, const int* Kt, int es, int mode,
                         int target, int nthr, unsigned long long* stats) {
@@ -150,7 +240,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
   g_out_bytes = total;
   g_counts = counts;
   const unsigned char* safe_end = in + (total & ~(size_t)15);
-  unsigned long long tiles = 0, copied = 0, maxb = 0, nfast = 0;
+  unsigned long long tiles = 0, copied = 0, maxb = 0, nfast = 0, nstripe = 0;
   for (int z = 0; z < Nz && g_errors == 0; ++z) {
     DepthTiling d = tile_depth(Ny, Ks[z], Kt[z], es, target);
     if ((unsigned long long)d.max_tile_bytes > maxb) maxb = d.max_tile_bytes;
@@ -162,7 +252,8 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
     base.Ks = (unsigned short)Ks[z];
     base.Kt = (unsigned short)Kt[z];
     base.P = (unsigned short)d.P;
-    base.flags = (unsigned char)((es == 2 ? 1 : 0) | (mode << 1));
+    base.flags = (unsigned char)((es == 2 ? 1 : 0) | (mode << 1) | ((Ks[z] % 2 == 0) << 3) |
+                                 ((Kt[z] % 2 == 0) << 4));
     if ((d.P - (long long)Ks[z] * Kt[z]) % (16 / es) != 0) err("pitch not congruent to Ks*Kt", d.P, 0);
     if (d.P < d.V + 2 * (16 / es) - 2) err("pitch too small", d.P, d.V);
     std::vector<unsigned char> stage((size_t)d.max_tile_bytes + 64);
@@ -202,10 +293,15 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           g_tab_bytes = (size_t)(td.nrows + 1) * sizeof(int);
           make_ctx(ctx, td, stage.data(), in_depth, out_depth, tab.data());
           nfast += ctx.fast ? 1 : 0;
-          for (int w = 0; w < nwarps; ++w)
-            for (int lane = 0; lane < 32; ++lane)
-              gather_tile_ctx(ctx, w, nwarps, lane,
-                              (int)((tiles * (unsigned long long)(ctx.fast ? ctx.nunits : ctx.items)) % nwarps));
+          nstripe += ctx.stripe ? 1 : 0;
+          const int nsteps = ctx.stripe ? ctx.nsteps_s : (ctx.fast ? ctx.nunits : ctx.items);
+          const int rot = (int)((tiles * (unsigned long long)nsteps) % nwarps);
+          if (ctx.stripe) {
+            emu_stripes_ctx(ctx, nwarps, rot);
+          } else {
+            for (int w = 0; w < nwarps; ++w)
+              for (int lane = 0; lane < 32; ++lane) gather_tile_ctx(ctx, w, nwarps, lane, rot);
+          }
           g_tab = nullptr;  // the table dies with this tile
           g_tab_bytes = 0;
           ++tiles;
@@ -218,6 +314,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
     stats[1] = copied;
     stats[2] = maxb;
     stats[3] = nfast;
+    stats[4] = nstripe;
   }
   return g_errors;
 }

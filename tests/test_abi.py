@@ -221,22 +221,16 @@ def test_gradient_validation_sizes_the_gradient_volume(lib):
 
 def test_even_cutouts_need_the_paper_window(lib):
     """Even Ks or Kt: Eq. 8 then defines a partial map, so only the literal
-    paper-window mode takes it; entry points other than the plain map and its
-    adjoint reject such a plan before any launch."""
+    paper-window mode takes it (every map entry point does); the projectors,
+    which need a cut-out centre, reject such a plan before any launch."""
     rc, h = _plan(lib, 5, 3, [14, 15], [15, 6], 0, 0)
     assert rc == -1 and not h.value
     rc, h = _plan(lib, 5, 3, [14, 15], [15, 6], 0, 1)
     assert rc == 0 and h.value
     assert lib.lfbp_plan_elems(h) == 5 * 3 * (14 * 15 + 15 * 6)
-    A, B = 0x10000000, 0x20000000
-    arr = (ctypes.c_void_p * 1)(h)
-    ins = (ctypes.c_void_p * 1)(A)
-    outs = (ctypes.c_void_p * 1)(B)
-    P = ctypes.c_void_p
-    assert lib.lfbp_backproject_batched(1, ctypes.cast(arr, P), ctypes.cast(ins, P),
-                                        ctypes.cast(outs, P), None) == -1
-    assert b"even" in lib.lfbp_last_error()
+    A, B = 0x10000000, 0x20000000   # never dereferenced: validation fails first
     assert lib.lfbp_backproject_volume_from_h(h, A, B, 12, 12, 0x30000000, None) in (-1, -5)
+    assert lib.lfbp_rl_normaliser(h, A, None, 12, 12, B, 0x30000000, None) in (-1, -5)
     lib.lfbp_plan_destroy(h)
 
 

@@ -22,11 +22,15 @@ lib = lf.load(build_if_missing=True)
 assert lib._name.endswith("liblfbp_check.so"), lib._name
 torch.cuda.set_device(0)
 SHAPES = [(5, 5, [15, 25], [15, 25]), (19, 19, [399, 95], [399, 95]), (51, 51, [153], [153]),
-          (95, 55, [181], [181]), (3, 5, [9, 3, 15], [15, 5, 5]), (11, 11, [99, 33], [99, 33])]
+          (95, 55, [181], [181]), (3, 5, [9, 3, 15], [15, 5, 5]), (11, 11, [99, 33], [99, 33]),
+          (7, 27, [21, 35], [21, 35]),                       # stripes in bands
+          (19, 19, [96, 20], [96, 20]), (5, 3, [14, 15], [15, 6]),  # even cut-outs
+          (11, 7, [90, 12], [34, 89])]
 for Nx, Ny, Ks, Kt in SHAPES:
+    even = any(k % 2 == 0 for k in Ks + Kt)
     for dt in (torch.float32, torch.float16):
-        # (the oracle's literal paper-window loop is O(K^4): small cut-outs only)
-        for mode in (lf.MAP_TRANSPOSE,) + ((lf.MAP_PAPER_WINDOW,) if max(Ks) <= 99 else ()):
+        modes = (lf.MAP_PAPER_WINDOW,) if even else (lf.MAP_TRANSPOSE, lf.MAP_PAPER_WINDOW)
+        for mode in modes:
             plan = lf.Plan(Nx, Ny, Ks, Kt, dt, mode=mode)
             g = torch.Generator(device="cpu").manual_seed(Nx + len(Ks))
             bits = torch.randint(-2 ** 15, 2 ** 15 - 1, (plan.elems * (2 if dt == torch.float32 else 1),),
@@ -35,10 +39,16 @@ for Nx, Ny, Ks, Kt in SHAPES:
             Hn = H.cpu().numpy()
             want = (oracle.transpose if mode == lf.MAP_TRANSPOSE else oracle.paper_window)(
                 Hn, Nx, Ny, Ks, Kt)
-            for got in (lf.backproject_array(plan, H), lf.backproject_batched([plan], [H])[0]):
+            outs = [lf.backproject_array(plan, H), lf.backproject_batched([plan], [H])[0]]
+            if mode == lf.MAP_TRANSPOSE:
+                outs.append(lf.adjoint(plan, H))  # the map is its own adjoint
+            else:
+                lf.adjoint(plan, outs[0])  # the windowed adjoint's accesses (values: test_gpu_map)
+            for got in outs:
                 lf.sync_status()  # raises on a recorded violation
                 w = np.uint32 if dt == torch.float32 else np.uint16
                 assert np.array_equal(got.cpu().numpy().view(w), want.view(w)), (Nx, Ks, dt, mode)
+            lf.sync_status()
 print("checked ok")
 """
 

@@ -333,6 +333,42 @@ def test_even_cutouts_literal_window(lf, shape, dtype):
     w = src > 0
     want[src[w] - 1] = d[w]
     _assert_same_bits(lf.adjoint(plan, dHp), want, "literal window adjoint")
-    with pytest.raises(lf.LfbpError):
-        lf.backproject_batched([plan], [H])
+    # the batched form takes even cut-outs too, beside an odd array of the same mode
+    odd = lf.Plan(5, 5, [15], [15], dtype, mode=lf.MAP_PAPER_WINDOW)
+    H2 = _random_bits(odd.elems, dtype, 17)
+    got = lf.backproject_batched([plan, odd], [H, H2])
+    _assert_same_bits(got[0], oracle.paper_window(Hn, Nx, Ny, Ks, Kt), "literal window batched")
+    _assert_same_bits(got[1], oracle.paper_window(H2.cpu().numpy(), 5, 5, [15], [15]),
+                      "paper window batched (odd)")
     lf.sync_status()
+
+
+def test_highres_even_cutouts_full(lf):
+    """The highres workload with every cut-out one pixel larger (even K: the
+    literal Eq. 8), fp32, through the batched form at full size: every depth
+    bit for bit against the oracle's Eqs. 4-9, and the adjoint on every fourth
+    depth (each written entry moved back to its source, zero elsewhere)."""
+    spec = lfgen.config_specs("highres")[0]
+    Ks = [k + 1 for k in spec.Ks]
+    plan = lf.Plan(spec.Nx, spec.Ny, Ks, Ks, torch.float32, mode=lf.MAP_PAPER_WINDOW)
+    g = torch.Generator(device="cuda").manual_seed(23)
+    H = torch.randint(-2 ** 31, 2 ** 31 - 1, (plan.elems,), generator=g, device="cuda",
+                      dtype=torch.int64).to(torch.int32).view(torch.float32)
+    Hp = lf.backproject_batched([plan], [H])[0]
+    dH = lf.adjoint(plan, Hp)
+    lf.sync_status()
+    off = [0]
+    for k in Ks:
+        off.append(off[-1] + spec.Nx * spec.Ny * k * k)
+    for z in range(len(Ks)):
+        a, b = off[z], off[z + 1]
+        Hz = H[a:b].cpu().numpy()
+        want = oracle.paper_window(Hz, spec.Nx, spec.Ny, [Ks[z]], [Ks[z]])
+        _assert_same_bits(Hp[a:b], want, f"even highres depth {z}")
+        if z % 4 == 0 or z == len(Ks) - 1:
+            src = oracle.paper_window(np.arange(1, b - a + 1, dtype=np.int32), spec.Nx, spec.Ny,
+                                      [Ks[z]], [Ks[z]])
+            w = src > 0
+            back = np.zeros_like(Hz)
+            back[src[w] - 1] = want[w]
+            _assert_same_bits(dH[a:b], back, f"even highres adjoint depth {z}")

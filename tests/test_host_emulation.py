@@ -51,7 +51,7 @@ def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=8):
     counts = np.zeros(nbytes, dtype=np.uint8)
     ks = np.asarray(Ks, dtype=np.int32)
     kt = np.asarray(Kt, dtype=np.int32)
-    stats = np.zeros(4, dtype=np.uint64)
+    stats = np.zeros(5, dtype=np.uint64)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     nerr = emu.emu_run(p(hin), p(out), p(counts), Nx, Ny, len(ks), p(ks), p(kt), es, mode,
                        target, nthr, p(stats))
@@ -89,6 +89,13 @@ SHAPES = [
     (51, 51, [53], [53], 32768),
     (95, 3, [19, 21], [97, 9], 32768),    # Ny below a chunk: element walk
     (3, 95, [11], [191], 32768),
+    # the stripe consumer: run blocks of 4 runs, 1 to 5 per stripe, bands beyond
+    (11, 11, [33, 55], [33, 55], 32768),  # 3 run blocks
+    (13, 13, [39, 65], [39, 65], 32768),  # 4
+    (19, 19, [57, 399], [57, 399], 32768),  # 5, and a one-row tile per stage in fp32
+    (3, 7, [9, 21], [9, 21], 32768),      # 1 and 2
+    (7, 27, [21, 35], [21, 35], 32768),   # 7 run blocks: bands of 4
+    (5, 3, [13, 21], [9, 17], 8192),      # Ks*Kt = 1 mod 4 with Ks != Kt, multi-row tiles
 ]
 
 
@@ -104,6 +111,20 @@ def test_tiles_transpose(emu, shape, dtype):
     # the chunk path takes every tile whose rows and cells are at least a chunk long
     if Ny >= 16 // H.itemsize and min(Kt) >= 16 // H.itemsize and target >= 32768:
         assert stats[3] == stats[0]
+    # the stripe path takes the tiles whose run stride Ks*Kt is 1 mod 4
+    if Ny >= 3 and all((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt)) and target >= 32768:
+        assert stats[4] == stats[0]
+
+
+def _stripe_shape(Ny, Ks, Kt):
+    return Ny >= 3 and any((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt))
+
+
+def test_stripe_shapes_are_covered():
+    """The shape list reaches the stripe consumer with every run-block count
+    per stripe (1 to 5) and with bands of several stripes (Ny > 20)."""
+    nrb = sorted({(Ny + 3) // 4 for _, Ny, Ks, Kt, _ in SHAPES if _stripe_shape(Ny, Ks, Kt)})
+    assert {1, 2, 3, 4, 5} <= set(nrb) and max(nrb) > 5
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float16])
@@ -124,6 +145,43 @@ def test_tiles_paper_window_and_adjoint(emu, shape, dtype):
     Y[~keep] = 0
     got2, _ = _run(emu, H, Nx, Ny, Ks, Kt, 2, target)
     want2 = oracle.transpose_adjoint(Y, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(got2.view(np.uint8), want2.view(np.uint8))
+
+
+EVEN_SHAPES = [
+    # even cut-outs in the paper-window mode (the literal Eq. 8): even, odd and
+    # mixed parities, K < N, non-square cells, multi-row tiles, column splits
+    # (small targets) and the zero column alone in a column block
+    (3, 3, [4, 6], [4, 6], 32768),
+    (5, 3, [14, 15], [15, 6], 32768),
+    (19, 19, [96, 20], [96, 20], 32768),
+    (11, 7, [90, 12], [34, 89], 4096),
+    (5, 5, [16, 2], [16, 2], 600),
+    (95, 5, [182], [18], 32768),
+    (19, 19, [400], [400], 32768),
+    (3, 5, [10], [10], 300),
+]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float16])
+@pytest.mark.parametrize("shape", EVEN_SHAPES, ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}x{s[3][0]}_t{s[4]}")
+def test_tiles_even_cutouts(emu, shape, dtype):
+    """Even cut-outs on the tiled gather: the map as the cropped odd cut-out
+    under the loop ranges' window, and its adjoint, against the oracle's
+    evaluation of Eqs. 4-9."""
+    Nx, Ny, Ks, Kt, target = shape
+    n = sum(Nx * Ny * a * b for a, b in zip(Ks, Kt))
+    H = _random_bits(n, dtype, 4)
+    got, _ = _run(emu, H, Nx, Ny, Ks, Kt, 1, target)
+    want = oracle.paper_window(H, Nx, Ny, Ks, Kt)
+    np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
+    # the adjoint moves every written entry back to its source, zero elsewhere
+    idx = np.arange(1, n + 1, dtype=np.int64)
+    fwd = oracle.paper_window(idx, Nx, Ny, Ks, Kt)
+    want2 = np.zeros_like(H)
+    written = fwd != 0
+    want2[fwd[written] - 1] = H[written]
+    got2, _ = _run(emu, H, Nx, Ny, Ks, Kt, 2, target)
     np.testing.assert_array_equal(got2.view(np.uint8), want2.view(np.uint8))
 
 
