@@ -65,10 +65,15 @@ __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_status, 0, c
 // CTA.  `base` carries the depth's shape, pitch and flags; the CTA fills in
 // its own p, u0, v0, nrows, ncols.
 // smem: [stage: tile bytes][mbarrier][TileCtx][row-base table]
+// The four tile shapes of one depth: index (last row block) + 2 (last column block).
+struct DepthShapes {
+  TileShape s[4];
+};
+
 __global__ void __launch_bounds__(kPlainThreads)
-    k_gather_depth(TileDesc base, const unsigned char* __restrict__ in_depth,
-                   const unsigned char* in_safe_end, unsigned char* __restrict__ out_depth, int J,
-                   int V, int stage_bytes) {
+    k_gather_depth(TileDesc base, const __grid_constant__ DepthShapes shapes,
+                   const unsigned char* __restrict__ in_depth, const unsigned char* in_safe_end,
+                   unsigned char* __restrict__ out_depth, int J, int V, int stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* stage = smem;
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes);
@@ -102,7 +107,15 @@ __global__ void __launch_bounds__(kPlainThreads)
   issue_tile_loads(td, in_depth, in_safe_end, stage, b, lane, warp, kWarps);
   __syncwarp();
   if (lane == 0) mbar_arrive(b);
-  if (warp == 1 && lane < 8) make_ctx_lane(*ctx, td, stage, in_depth, out_depth, tab, lane);
+  // the tile context: warp 0 copies the shape record, warps 1..4 each build
+  // one part of the tile fields (in parallel)
+  {
+    const int si = (blockIdx.z + 1 == gridDim.z ? 1 : 0) + (blockIdx.x + 1 == gridDim.x ? 2 : 0);
+    const TileShape* shp = &shapes.s[si];
+    if (warp == 0) copy_shape(*ctx, shp, lane);
+    if (warp >= 1 && warp <= 4 && lane == 0)
+      make_ctx_tile(*ctx, td, shp, stage, in_depth, out_depth, tab, warp - 1);
+  }
   __syncthreads();
   if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
     set_status(kStatusTimeout);
@@ -135,8 +148,8 @@ template <bool kStall>
 #endif
 __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
     k_gather_persistent(const __grid_constant__ BatchPtrs ptrs,
-                        const TileDesc* __restrict__ tiles, int ntiles, int stage_bytes,
-                        int nstages) {
+                        const TileDesc* __restrict__ tiles, const TileShape* __restrict__ shapes,
+                        int ntiles, int stage_bytes, int nstages) {
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned char* info_base = smem + (size_t)nstages * stage_bytes;  // per stage: flag, TileCtx, table
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)nstages * (stage_bytes + kInfoBytes));
@@ -153,6 +166,8 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
     for (int s = 0; s < nstages; ++s) {
       mbar_init(smem_addr(&full[s]), kProducerWarps);
       mbar_init(smem_addr(&empty[s]), kConsumerWarps);
+      // the shape index held by the stage's context slot: none yet
+      reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes)[1] = -1;
     }
     fence_mbar_init();
   }
@@ -197,16 +212,25 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
         issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
                          kProducerWarps);
       }
-      // the tile context is built while the copies are in flight, in eight
-      // parts shared by the producer warps (each part's branch runs on its own)
-      {
+      // the tile context, built by warp 0 while the copies are in flight: the
+      // shape record is copied only when the slot holds another one (the tiles
+      // of one CTA come from one depth for long stretches), then lanes 0..3
+      // build the tile fields from the slot's copy of the shape
+      if (warp == 0) {
         unsigned char* info = info_base + (size_t)s * kInfoBytes;
-        if (warp == 0 && lane == 0) *reinterpret_cast<int*>(info) = 0;
-        constexpr int kParts = 8 / kProducerWarps;
-        if (lane < kParts)
-          make_ctx_lane(*reinterpret_cast<TileCtx*>(info + 16), td, smem + (size_t)s * stage_bytes,
-                        in_depth, ptrs.out[td.arr] + td.off_bytes,
-                        reinterpret_cast<int*>(info + 16 + kCtxBytes), warp * kParts + lane);
+        TileCtx& ctx = *reinterpret_cast<TileCtx*>(info + 16);
+        int* held = reinterpret_cast<int*>(info) + 1;
+        if (lane == 0) reinterpret_cast<int*>(info)[0] = 0;
+        if (*held != (int)td.shape) {
+          copy_shape(ctx, shapes + td.shape, lane);
+          __syncwarp();
+          if (lane == 0) *held = td.shape;
+        }
+        __syncwarp();
+        if (lane < 4)
+          make_ctx_tile(ctx, td, &ctx, smem + (size_t)s * stage_bytes, in_depth,
+                        ptrs.out[td.arr] + td.off_bytes,
+                        reinterpret_cast<int*>(info + 16 + kCtxBytes), lane);
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(fb);
@@ -384,6 +408,13 @@ TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr)
   return t;
 }
 
+// The four tile shapes of depth z for a tiling: index (last row block) +
+// 2 (last column block).
+void depth_shapes(lfbp_plan p, int z, const DepthTiling& d, const TileDesc& base, TileShape* out) {
+  for (int cls = 0; cls < 4; ++cls)
+    out[cls] = depth_shape(d, p->Nx, p->Ny, p->Ks[z], p->Kt[z], p->es, base.flags, cls);
+}
+
 // One launch per depth of the plain kernel, for depths [z0, z1).
 // Tile-size target of the plain form: one tile per CTA and no pipeline, so
 // larger tiles than the persistent form's pay (measured on highres: 64 KB
@@ -405,10 +436,12 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
   for (int z = z0; z < z1; ++z) {
     const DepthTiling& d = tl[z];
     const TileDesc base = depth_desc(p, z, d, mode, 0);
+    DepthShapes ds;
+    depth_shapes(p, z, d, base, ds.s);
     dim3 grid(d.nV, p->Nx, d.nU);
     const int smem = (d.max_tile_bytes + 15) & ~15;
     k_gather_depth<<<grid, kPlainThreads, plain_smem_bytes(smem), st>>>(
-        base, inb + base.off_bytes, safe_end, outb + base.off_bytes, d.J, d.V, smem);
+        base, ds, inb + base.off_bytes, safe_end, outb + base.off_bytes, d.J, d.V, smem);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "k_gather_depth launch");
@@ -536,7 +569,8 @@ struct BatchState {
   Tuning tuning{0, 0, 0};
   int ntiles = 0;
   int stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
-  TileDesc* d_tiles = nullptr;
+  TileDesc* d_tiles = nullptr;    // work list, followed in the same allocation by
+  TileShape* d_shapes = nullptr;  // the shape table
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   cudaGraphNode_t knode = nullptr;
@@ -577,8 +611,9 @@ constexpr size_t kMaxCachedBatches = 8;
 // Work list of all depths of all arrays: per depth, u-block major, then p,
 // then v-block, so that tiles in flight together touch neighbouring input
 // segments and neighbouring output runs.
+// With each depth come its four tile shapes (depth_shapes), referenced by index.
 void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc>& tiles,
-                 int* max_tile) {
+                 std::vector<TileShape>& shapes, int* max_tile) {
   *max_tile = 0;
   for (int i = 0; i < n; ++i) {
     lfbp_plan p = plans[i];
@@ -587,10 +622,14 @@ void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc
       const DepthTiling& d = tl[z];
       *max_tile = std::max(*max_tile, d.max_tile_bytes);
       const TileDesc base = depth_desc(p, z, d, (int)p->mode, i);
+      const size_t s0 = shapes.size();
+      shapes.resize(s0 + 4);
+      depth_shapes(p, z, d, base, &shapes[s0]);
       for (int ub = 0; ub < d.nU; ++ub)
         for (int pp = 0; pp < p->Nx; ++pp)
           for (int vb = 0; vb < d.nV; ++vb) {
             TileDesc t = base;
+            t.shape = (unsigned short)(s0 + (ub + 1 == d.nU ? 1 : 0) + (vb + 1 == d.nV ? 2 : 0));
             t.p = (unsigned short)pp;
             t.u0 = (unsigned short)(ub * d.J);
             t.v0 = (unsigned short)(vb * d.V);
@@ -608,8 +647,10 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   if (rc) return rc;
   bs.dev = dev;
   std::vector<TileDesc> tiles;
+  std::vector<TileShape> shapes;
   int max_tile = 0;
-  build_tiles(n, plans, tu.tile_bytes, tiles, &max_tile);
+  build_tiles(n, plans, tu.tile_bytes, tiles, shapes, &max_tile);
+  if (shapes.size() > 65536) return fail(LFBP_ERR_BAD_SHAPE, "more than 16384 depths in one batch");
   bs.ntiles = (int)tiles.size();
   bs.stage_bytes = (max_tile + 127) & ~127;
   const int per_cta_budget = std::min(optin, (227 * 1024) / tu.ctas_per_sm - 1024);
@@ -624,18 +665,21 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   cudaError_t e;
   if (bs.ntiles) {
     if (fault_mode() == kFaultAlloc) return fail(LFBP_ERR_NOMEM, "injected failure (LFBP_FAULT=alloc)");
-    if ((e = cudaMalloc(&bs.d_tiles, sizeof(TileDesc) * tiles.size())) != cudaSuccess)
+    const size_t tb = sizeof(TileDesc) * tiles.size(), sb = sizeof(TileShape) * shapes.size();
+    if ((e = cudaMalloc(&bs.d_tiles, tb + sb)) != cudaSuccess)
       return cuda_fail(e, "cudaMalloc(tiles)");
-    if ((e = cudaMemcpy(bs.d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
-                        cudaMemcpyHostToDevice)) != cudaSuccess)
+    bs.d_shapes = reinterpret_cast<TileShape*>(reinterpret_cast<unsigned char*>(bs.d_tiles) + tb);
+    if ((e = cudaMemcpy(bs.d_tiles, tiles.data(), tb, cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(tiles)");
+    if ((e = cudaMemcpy(bs.d_shapes, shapes.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpy(shapes)");
   }
   if ((rc = ensure_smem_attr((const void*)k_gather_persistent<false>, bs.smem))) return rc;
   // a one-node graph: relaunching it costs one cudaGraphLaunch; pointer
   // changes are patched into the node's parameters
   if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
   std::memset(&bs.ptrs, 0, sizeof(bs.ptrs));
-  void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
+  void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.d_shapes, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
   kp.func = (void*)k_gather_persistent<false>;
@@ -712,7 +756,8 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   }
   if (std::memcmp(&np, &bs->ptrs, sizeof(np)) != 0) {
     bs->ptrs = np;
-    void* args[] = {&bs->ptrs, &bs->d_tiles, &bs->ntiles, &bs->stage_bytes, &bs->nstages};
+    void* args[] = {&bs->ptrs, &bs->d_tiles, &bs->d_shapes, &bs->ntiles, &bs->stage_bytes,
+                    &bs->nstages};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.func = (void*)k_gather_persistent<false>;
@@ -727,7 +772,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     int rc = ensure_smem_attr((const void*)k_gather_persistent<true>, bs->smem);
     if (rc) return rc;
     k_gather_persistent<true><<<bs->grid, kPersistentThreads, bs->smem, st>>>(
-        bs->ptrs, bs->d_tiles, bs->ntiles, bs->stage_bytes, bs->nstages);
+        bs->ptrs, bs->d_tiles, bs->d_shapes, bs->ntiles, bs->stage_bytes, bs->nstages);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
     return LFBP_OK;
   }
@@ -742,8 +787,9 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
 // noalloc keeps the persistent kernel's work list in this file-scope device
 // array instead of a cudaMalloc'd buffer.  Every GPU that loads the library
 // holds the array until the process exits.
-constexpr int kNoAllocMaxTiles = 262144;  // 8 MiB of 32-byte tile descriptors
+constexpr int kNoAllocMaxTiles = 262144;  // 8 MiB of 32-byte slots: tiles, then their shapes
 static __device__ __align__(256) TileDesc g_noalloc_tiles[kNoAllocMaxTiles];
+constexpr int kShapeSlots = (int)((sizeof(TileShape) + sizeof(TileDesc) - 1) / sizeof(TileDesc));
 
 // Per device: the array's device address (from cudaGetSymbolAddress) and
 // which work list it holds now.
@@ -752,6 +798,7 @@ struct NoAllocDev {
   TileDesc* d_tiles = nullptr;
   int sms = 0, optin = 0;
   std::vector<unsigned long long> uids;  // plans of the list in the array
+  TileShape* d_shapes = nullptr;  // inside the array, after the tiles
   int tile_bytes = 0, ntiles = 0, stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
 };
 std::vector<std::unique_ptr<NoAllocDev>> g_noalloc;  // guarded by g_mu
@@ -787,7 +834,8 @@ void noalloc_target(int n, const lfbp_plan* plans, const Tuning& dflt, int* targ
     *need = 0;
     for (int i = 0; i < n; ++i) {
       const std::vector<DepthTiling>& tl = plan_tiling(plans[i], t);
-      for (int z = 0; z < plans[i]->Nz; ++z) *need += (long long)plans[i]->Nx * tl[z].nU * tl[z].nV;
+      for (int z = 0; z < plans[i]->Nz; ++z)
+        *need += (long long)plans[i]->Nx * tl[z].nU * tl[z].nV + 4 * kShapeSlots;  // tiles + shapes
     }
     if (*need <= kNoAllocMaxTiles) return;
   }
@@ -820,7 +868,8 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
   if (need > kNoAllocMaxTiles) {
     char msg[160];
     std::snprintf(msg, sizeof(msg),
-                  "the batch needs %lld tiles; the no-allocation path holds at most %d",
+                  "the batch needs %lld descriptor slots (tiles and tile shapes); the "
+                  "no-allocation path holds at most %d",
                   need, kNoAllocMaxTiles);
     return fail(LFBP_ERR_BAD_SHAPE, msg);
   }
@@ -844,9 +893,10 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
                   "the work list must be replaced, which cannot be done while the stream is "
                   "capturing");
     std::vector<TileDesc> tiles;
+    std::vector<TileShape> shapes;
     tiles.reserve((size_t)need);
     int max_tile = 0;
-    build_tiles(n, plans, tu.tile_bytes, tiles, &max_tile);
+    build_tiles(n, plans, tu.tile_bytes, tiles, shapes, &max_tile);
     const int stage_bytes = (max_tile + 127) & ~127;
     const int per_cta_budget = std::min(nd->optin, (227 * 1024) / tu.ctas_per_sm - 1024);
     const int per_stage = stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
@@ -856,9 +906,14 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
     // stream-ordered: the kernels of earlier calls on this stream have read
     // the previous list before this copy overwrites it
+    TileShape* d_shapes = reinterpret_cast<TileShape*>(nd->d_tiles + tiles.size());
     if ((e = cudaMemcpyAsync(nd->d_tiles, tiles.data(), sizeof(TileDesc) * tiles.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(work list)");
+    if ((e = cudaMemcpyAsync(d_shapes, shapes.data(), sizeof(TileShape) * shapes.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return cuda_fail(e, "cudaMemcpyAsync(tile shapes)");
+    nd->d_shapes = d_shapes;
     // the copy reads `tiles` (pageable host memory) before returning
     nd->uids.clear();
     for (int i = 0; i < n; ++i) nd->uids.push_back(plans[i]->uid);
@@ -880,10 +935,10 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
   if (fault_mode() == kFaultStall) {
     if ((rc = ensure_smem_attr((const void*)k_gather_persistent<true>, nd->smem))) return rc;
     k_gather_persistent<true><<<nd->grid, kPersistentThreads, nd->smem, st>>>(
-        np, nd->d_tiles, nd->ntiles, nd->stage_bytes, nd->nstages);
+        np, nd->d_tiles, nd->d_shapes, nd->ntiles, nd->stage_bytes, nd->nstages);
   } else {
     k_gather_persistent<false><<<nd->grid, kPersistentThreads, nd->smem, st>>>(
-        np, nd->d_tiles, nd->ntiles, nd->stage_bytes, nd->nstages);
+        np, nd->d_tiles, nd->d_shapes, nd->ntiles, nd->stage_bytes, nd->nstages);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
   return LFBP_OK;
@@ -970,7 +1025,7 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
         const int smem = bs.smem;
         for (int r = 0; r <= reps; ++r) {
           if (r == 1) cudaEventRecord(a, st);
-          k_gather_persistent<false><<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.ntiles,
+          k_gather_persistent<false><<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.d_shapes, bs.ntiles,
                                                                          bs.stage_bytes, bs.nstages);
         }
         cudaEventRecord(b, st);

@@ -51,8 +51,8 @@ struct TileDesc {
   unsigned short Nx, Ny, Ks, Kt;
   unsigned short P;     // slot pitch in elements
   unsigned char arr;    // array slot in BatchPtrs
-  unsigned char flags;  // bit 0: fp16 storage; bits 1-2: mode
-  unsigned short pad;
+  unsigned char flags;  // bit 0: fp16 storage; bits 1-2: mode; bits 3-4: Ks, Kt even
+  unsigned short shape; // index of the tile's TileShape in the launch's shape table
 };
 static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
 
@@ -226,15 +226,15 @@ inline double pitch_cost_stripes(int Ny, int ncols, int es, int P) {
 }
 
 // Tiles taken by the stripe consumer (lfbp_stripes.cuh) in either map mode.
-__host__ __device__ inline bool stripe_shape(int Ny, int Ks, int Kt, int ncols) {
-  return LFBP_STRIPES && (((long long)Ks * Kt) & 3) == 1 && Ny >= 3 && ncols >= 8;
+__host__ __device__ inline bool stripe_shape(int Ny, int Ks, int Kt, int ncols, int es) {
+  return LFBP_STRIPES && es == 2 && (((long long)Ks * Kt) & 3) == 1 && Ny >= 3 && ncols >= 8;
 }
 
 // Slot pitch for segments of ncols elements: P >= ncols + 2E - 2 (room for a
 // copy widened to 16-byte boundaries), P = Ks*Kt (mod E), fewest conflicts.
 inline int choose_pitch(int Ny, int Ks, int Kt, int ncols, int es) {
   const int E = 16 / es;
-  const bool stripes = stripe_shape(Ny, Ks, Kt, ncols);
+  const bool stripes = stripe_shape(Ny, Ks, Kt, ncols, es);
   const int KKm = (int)(((long long)Ks * Kt) % E);
   int P0 = ncols + 2 * E - 2;
   P0 += ((KKm - P0) % E + E) % E;
@@ -558,207 +558,253 @@ __device__ __forceinline__ void issue_tile_loads(const TileDesc& td, const unsig
 }
 #endif
 
-// Tile constants derived from the descriptor: computed once per tile by the
-// eight lanes of one warp (make_ctx_lane) into shared memory, and copied into
-// registers by every consumer thread before its gather loop (a copy in
-// registers cannot be aliased by the gather's global stores, so it is not
-// re-read after each store).
-struct alignas(16) TileCtx {
-  uint32_t stage_s;         // shared-memory address of the stage
-  int tile_bytes;           // bytes of the tile's stage
-  unsigned char* out_run0;  // byte address of run q = 0 at (u0, v0)
-  uint32_t run_stride;      // bytes between runs q and q+1 (Ks*Kt*es < 2^32)
-  unsigned char* out_lo;    // the depth's output bytes [out_lo, out_hi)
-  unsigned char* out_hi;
-  int Nx, Ny, Ks, Kt, ncols, L, P, RP;
+// Tile constants that depend only on the depth's sizes, the dtype, the mode
+// and the tile's row and column counts (and, for an even cut-out, on whether
+// the tile holds the zero column): computed on the host once per depth and
+// tile shape (make_shape), stored in a table beside the work list, and copied
+// into the tile context by one warp with coalesced loads.  All the divisions
+// of the context are here.
+struct alignas(16) TileShape {
+  int Nx, Ny, Ks, Kt, ncols, nrows, L, P, RP, tile_bytes;
   int Ksm, Ktm;  // cut-out sizes of the map (Ks, Kt, or one less when even)
   int nseg;      // source pixels per segment: the columns v < Ktm of the tile
   int even;      // nonzero: an even cut-out (zero row / column, clamped reads)
-  // paper-window masks (modes 1 and 2), as per-tile bounds on row j, column
-  // vl, run q and cells a, b (see keep_elem)
-  int m1_j0, m1_jw, m1_q0, m2_a, m2_b, Ks1, Kt1, jlim, vlim;
-  int p, u0, v0;
-  int cb;    // (v0 - c_t) mod Ny
-  int ap0;   // (p + u0 - c_s) mod Nx
-  int s0;    // Ks - 1 - u0
-  int inm;   // phase (mod E) of the input depth base + t_lo, in elements
-  int nkk;   // (Ny*Ks*Kt) mod E
-  int ktm;   // Kt mod E
-  int om0;   // absolute element index of run q = 0, mod 128/es
-  int kks;   // (Ks*Kt) mod 128/es
-  int sbn;   // (128/es) mod Ny
-  int cmn;   // ncols mod Ny
-  int ngc;   // work items per run (element-walk path)
-  int items;
+  int Ks1, Kt1;  // Ks - 1, Kt - 1
   int es, mode;
-  // chunk path
-  uint32_t tab_s;  // shared-memory address of the row-base table: nrows + 1 ints
-  int nrows;
-  int rb0;         // row base of row 0 (elements): R_0 + ncols - 1
-  uint32_t A0;     // stage_s + rb0 * es
-  uint32_t PES;    // P * es
-  int cbb;         // cb plus a multiple of Ny that is >= 128/es
-  int ngm;         // 128-byte lines per run (any alignment), at least 2
-  int nunits;      // warp steps of the tile: ceil(Ny * ngm / 4)
-  uint32_t D;      // bytes between diagonal neighbours: (P - 1) * es
-  uint32_t W;      // bytes of Ny slots: Ny * P * es
-  int fast;        // 1: chunk path (mode 0 or 1, ncols >= 16/es, Ny >= 16/es)
-  FastDiv fncols, fNy, fNx, fngc, fngm;
+  int nkk;       // (Ny*Ks*Kt) mod E
+  int ktm;       // Kt mod E
+  int kks;       // (Ks*Kt) mod 128/es
+  int sbn;       // (128/es) mod Ny
+  int cmn;       // ncols mod Ny
+  int ngc;       // work items per run (element-walk path)
+  int items;
+  int ngm;       // 128-byte lines per run (any alignment), at least 2
+  int nunits;    // warp steps of the tile (chunk path): ceil(Ny * ngm / 4)
+  int fast;      // 1: chunk path (mode 0 or 1, ncols >= 16/es, Ny >= 16/es)
+  uint32_t run_stride;  // bytes between runs q and q+1 (Ks*Kt*es < 2^32)
+  uint32_t PES;  // P * es
+  uint32_t D;    // bytes between diagonal neighbours: (P - 1) * es
+  uint32_t W;    // bytes of Ny slots: Ny * P * es
+  int cbb_add;   // a multiple of Ny that is >= 128/es
+  int ctm, csm;  // c_t mod Ny, c_s mod Nx (c from the map's cut-out)
   // stripe path (lfbp_stripes.cuh)
-  int stripe;      // 1: stripe path (mode 0 or 1, Ks*Kt = 1 mod 4, Ny >= 3, ncols >= 8)
-  int S;           // run blocks of 4 runs per stripe
-  int ns;          // stripes per row and band
-  int rowns;       // nrows * ns
-  int nitems_s;    // stripes of the tile: bands * nrows * ns
-  int nsteps_s;    // warp steps: ceil(nitems_s / 8)
+  int stripe;    // 1: stripe path (mode 0 or 1, Ks*Kt = 1 mod 4, Ny >= 3, ncols >= 8)
+  int S;         // run blocks of 4 runs per stripe
+  int ns;        // stripes per row and band
+  int rowns;     // nrows * ns
+  int nitems_s;  // stripes of the tile: bands * nrows * ns
+  int nsteps_s;  // warp steps: ceil(nitems_s / 8)
+  FastDiv fncols, fNy, fNx, fngc, fngm;
   FastDiv fns, frowns, fnb;  // by ns, rowns, nrows + 1
 };
+static_assert(sizeof(TileShape) % 16 == 0, "TileShape layout");
 
-// Row base of tile row j (elements): the stage index of element t_lo + ncols - 1
-// of segment (j, 0), i.e. j*RP + R_j + ncols - 1 with R_j the 16-byte phase of
-// that segment's first element.  Row j of segment b then holds output column
-// vl at  row_base(j) + b*P - vl.  Defined for j = nrows as well (the entry
-// past the last row is read but never dereferenced).
-__device__ __forceinline__ int row_base(const TileDesc& td, const unsigned char* in_depth, int j) {
-  const int ES = (td.flags & 1) ? 2 : 4, E = 16 / ES;
-  const long long KK = (long long)td.Ks * td.Kt;
-  const int Ksm = map_ks(td), nseg = tile_nseg(td);
-  const int a = pos_mod((int)td.p + (int)td.u0 + j - (Ksm - 1) / 2, td.Nx);
-  const long long t_lo = (long long)map_kt(td) - td.v0 - nseg;
-  const long long seg0 = (long long)a * td.Ny * KK + (long long)(Ksm - 1 - td.u0 - j) * td.Kt + t_lo;
-  const int ph = (int)(((long long)((uintptr_t)in_depth / ES) + seg0) & (E - 1));
-  return j * row_pitch(td.Ny, td.P, ES) + ph + nseg - 1;
+// The shape constants of a tile (host; the host emulation calls it too).
+// flags as in TileDesc; v0: the tile's first column (only whether the tile
+// reaches the map's last column matters).
+__host__ __device__ inline TileShape make_shape(int Nx, int Ny, int Ks, int Kt, int es, int flags,
+                                                int P, int nrows, int ncols, int v0) {
+  TileShape s;
+  const int E = 16 / es, GE = 128 / es;
+  const long long KK = (long long)Ks * Kt;
+  s.Nx = Nx;
+  s.Ny = Ny;
+  s.Ks = Ks;
+  s.Kt = Kt;
+  s.ncols = ncols;
+  s.nrows = nrows;
+  s.L = nrows * ncols;
+  s.P = P;
+  s.RP = row_pitch(Ny, P, es);
+  s.tile_bytes = nrows * s.RP * es;
+  s.Ksm = Ks - ((flags >> 3) & 1);
+  s.Ktm = Kt - ((flags >> 4) & 1);
+  {
+    const int n = s.Ktm - v0;
+    s.nseg = n < 0 ? 0 : (n > ncols ? ncols : n);
+  }
+  s.even = (flags >> 3) & 3;
+  s.Ks1 = Ks - 1;
+  s.Kt1 = Kt - 1;
+  s.es = es;
+  s.mode = (flags >> 1) & 3;
+  s.nkk = (int)(((long long)Ny * KK) & (E - 1));
+  s.ktm = Kt & (E - 1);
+  s.kks = (int)(KK & (GE - 1));
+  s.sbn = GE % Ny;
+  s.cmn = ncols % Ny;
+  {
+    const int ng = (s.L + 2 * GE - 2) / GE;  // groups per run, any alignment
+    s.ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
+    s.items = ((Ny + 3) >> 2) * s.ngc;
+    s.ngm = ng < 2 ? 2 : ng;
+    s.nunits = (Ny * s.ngm + 3) >> 2;
+  }
+  s.fast = s.mode <= 1 && ncols >= E && Ny >= E;
+  s.run_stride = (uint32_t)(KK * es);
+  s.PES = (uint32_t)P * es;
+  s.D = (uint32_t)(P - 1) * es;
+  s.W = (uint32_t)Ny * P * es;
+  s.cbb_add = ((GE + Ny - 1) / Ny) * Ny;
+  s.ctm = ((s.Ktm - 1) / 2) % Ny;
+  s.csm = ((s.Ksm - 1) / 2) % Nx;
+  s.fncols = make_fastdiv(ncols);
+  s.fNy = make_fastdiv(Ny);
+  s.fNx = make_fastdiv(Nx);
+  s.fngc = make_fastdiv(s.ngc);
+  s.fngm = make_fastdiv(s.ngm);
+  s.stripe = 0;
+  s.S = s.ns = s.rowns = s.nitems_s = s.nsteps_s = 0;
+  s.fns = s.frowns = make_fastdiv(1);
+  s.fnb = make_fastdiv(nrows + 1);
+  if (s.mode <= 1 && stripe_shape(Ny, Ks, Kt, ncols, es)) {
+    const int nrb = (Ny + 3) >> 2;
+    const int S = stripe_S(nrb);
+    const int nbands = (nrb + S - 1) / S;
+    const int ns = (ncols - 1 + 4 * (S - 1)) / 4 + 1;
+    const long long items = (long long)nbands * nrows * ns;
+    if (items < 65535 && (long long)nrows * ns < 65535) {
+      s.stripe = 1;
+      s.S = S;
+      s.ns = ns;
+      s.rowns = nrows * ns;
+      s.nitems_s = (int)items;
+      s.nsteps_s = (s.nitems_s + 7) >> 3;
+      s.fns = make_fastdiv(ns);
+      s.frowns = make_fastdiv(s.rowns);
+    }
+  }
+  return s;
 }
 
-// Lane `lane` (0..7) of a warp fills its share of the tile context; the
-// shares are independent, so the eight lanes run the divisions in parallel.
-// `tab` (shared memory, kMaxTileRows + 1 ints) receives the row-base table.
-__device__ __forceinline__ void make_ctx_lane(TileCtx& c, const TileDesc& td,
+// Shape class `cls` of a depth's tiles under tiling d: (last row block) +
+// 2 (last column block); the other blocks have d.J rows and d.V columns.
+inline TileShape depth_shape(const DepthTiling& d, int Nx, int Ny, int Ks, int Kt, int es,
+                             int flags, int cls) {
+  const int last_row = cls & 1, last_col = cls >> 1;
+  const int nrows = last_row ? Ks - (d.nU - 1) * d.J : lfbp_min(d.J, Ks);
+  const int v0 = last_col ? (d.nV - 1) * d.V : 0;
+  const int ncols = last_col ? Kt - v0 : lfbp_min(d.V, Kt);
+  return make_shape(Nx, Ny, Ks, Kt, es, flags, d.P, nrows, ncols, v0);
+}
+
+// The context of one tile: its shape constants plus the fields that depend on
+// the tile's position (p, u0, v0) and on the buffers.  Built once per tile in
+// shared memory; every consumer thread copies it into registers before its
+// gather loop (a copy in registers cannot be aliased by the gather's global
+// stores, so it is not re-read after each store).
+struct alignas(16) TileCtx : TileShape {
+  uint32_t stage_s;         // shared-memory address of the stage
+  uint32_t tab_s;           // shared-memory address of the row-base table: nrows + 1 ints
+  unsigned char* out_run0;  // byte address of run q = 0 at (u0, v0)
+  unsigned char* out_lo;    // the depth's output bytes [out_lo, out_hi)
+  unsigned char* out_hi;
+  int p, u0, v0;
+  int cb;    // (v0 - c_t) mod Ny
+  int cbb;   // cb + cbb_add
+  int ap0;   // (p + u0 - c_s) mod Nx
+  int s0;    // Ksm - 1 - u0
+  int inm;   // phase (mod E) of the input depth base + t_lo, in elements
+  int om0;   // absolute element index of run q = 0, mod 128/es
+  int rb0;   // row base of row 0 (elements): R_0 + nseg - 1
+  uint32_t A0;  // stage_s + rb0 * es
+  // paper-window masks (modes 1 and 2), as per-tile bounds on row j, column
+  // vl, run q and cells a, b (see keep_elem)
+  int m1_j0, m1_jw, m1_q0, m2_a, m2_b, jlim, vlim;
+};
+
+// Row base of tile row j (elements): the stage index of the segment (j, 0)'s
+// element for column 0, i.e. j*RP + R_j + nseg - 1 with R_j the 16-byte phase
+// of that segment's first element; row j of segment b then holds output
+// column vl at row_base(j) + b*P - vl.  Defined for j = nrows as well (the
+// entry past the last row is read but never dereferenced).  inm, s0 and ap0 as
+// in TileCtx.
+__device__ __forceinline__ int row_base(const TileShape& s, int inm, int s0, int ap0, int j) {
+  const int E = 16 / s.es;
+  const int a = (int)fmod_((uint32_t)(ap0 + j), s.fNx);
+  return j * s.RP + ((inm + a * s.nkk + (s0 - j) * s.ktm) & (E - 1)) + s.nseg - 1;
+}
+
+// The shape part of the context: lane `lane` of a full warp copies words
+// lane, lane + 32, ... of the shape record (coalesced loads).
+__device__ __forceinline__ void copy_shape(TileCtx& c, const TileShape* shp, int lane) {
+  constexpr int kWords = (int)(sizeof(TileShape) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(shp);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(static_cast<TileShape*>(&c));
+  for (int w = lane; w < kWords; w += 32) dst[w] = src[w];
+}
+
+// The tile part of the context, in four independent parts (part 0..3), each
+// run by one thread, plus the row-base table (rows part, part + 4, ...).
+// `shp` is the tile's shape record (it may be c itself once c holds it; the
+// parts write only tile fields).
+__device__ __forceinline__ void make_ctx_tile(TileCtx& c, const TileDesc& td, const TileShape* shp,
                                               const unsigned char* stage,
                                               const unsigned char* in_depth,
-                                              unsigned char* out_depth, int* tab, int lane) {
-  const int ES = (td.flags & 1) ? 2 : 4;
-  const int E = 16 / ES, GE = 128 / ES;  // GE: elements per run per gather group
-  const unsigned long long KK = (unsigned long long)td.Ks * td.Kt;
-  const int L = td.nrows * td.ncols;
-  for (int j = lane; j <= td.nrows; j += 8) tab[j] = row_base(td, in_depth, j);
-  switch (lane) {
+                                              unsigned char* out_depth, int* tab, int part) {
+  const TileShape& s = *shp;
+  const int ES = s.es, E = 16 / ES, GE = 128 / ES;
+  const int p = td.p, u0 = td.u0, v0 = td.v0;
+  // values every part needs
+  const int s0 = s.Ksm - 1 - u0;
+  const int ap0 = (int)fmod_((uint32_t)(p + u0 + s.Nx - s.csm), s.fNx);
+  const int t_lo = s.Ktm - v0 - s.nseg;
+  const int inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
+  for (int j = part; j <= s.nrows; j += 4) tab[j] = row_base(s, inm, s0, ap0, j);
+  switch (part) {
     case 0:
-      c.es = ES;
-      c.mode = (td.flags >> 1) & 3;
       c.stage_s = smem_addr(stage);
-      c.Nx = td.Nx;
-      c.Ny = td.Ny;
-      c.Ks = td.Ks;
-      c.Kt = td.Kt;
-      c.ncols = td.ncols;
-      c.L = L;
-      c.P = td.P;
-      c.RP = row_pitch(td.Ny, td.P, ES);
-      c.tile_bytes = td.nrows * c.RP * ES;
-      c.p = td.p;
-      c.u0 = td.u0;
-      c.v0 = td.v0;
-      c.Ksm = map_ks(td);
-      c.Ktm = map_kt(td);
-      c.nseg = tile_nseg(td);
-      c.even = (td.flags >> 3) & 3;
-      c.s0 = c.Ksm - 1 - td.u0;
-      c.nrows = td.nrows;
-      if (c.mode != 0) {
-        const int hx = (td.Nx - 1) >> 1, hy = (td.Ny - 1) >> 1;
-        c.Ks1 = td.Ks - 1;
-        c.Kt1 = td.Kt - 1;
-        c.jlim = c.Ksm - (int)td.u0;
-        c.vlim = c.Ktm - (int)td.v0;
-        const int j0 = hx - (int)td.p - (int)td.u0;
-        const int j1 = lfbp_dmin(td.Ks - 1 + j0, c.jlim - 1);
+      c.tab_s = smem_addr(tab);
+      c.p = p;
+      c.u0 = u0;
+      c.v0 = v0;
+      c.s0 = s0;
+      c.ap0 = ap0;
+      c.inm = inm;
+      break;
+    case 1: {
+      const int cb = (int)fmod_((uint32_t)(v0 + s.Ny - s.ctm), s.fNy);
+      c.cb = cb;
+      c.cbb = cb + s.cbb_add;
+      c.rb0 = row_base(s, inm, s0, ap0, 0);
+      c.A0 = smem_addr(stage) + (uint32_t)c.rb0 * ES;
+      break;
+    }
+    case 2: {
+      const unsigned long long run0 =
+          ((unsigned long long)p * s.Ny * s.Ks + u0) * s.Kt + v0;  // elements
+      c.out_run0 = out_depth + run0 * ES;
+      c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (GE - 1));
+      c.out_lo = out_depth;
+      c.out_hi = out_depth + (unsigned long long)s.Nx * s.Ny * s.Ks * s.Kt * ES;
+      break;
+    }
+    case 3:
+      if (s.mode != 0) {
+        const int hx = (s.Nx - 1) >> 1, hy = (s.Ny - 1) >> 1;
+        c.jlim = s.Ksm - u0;
+        c.vlim = s.Ktm - v0;
+        const int j0 = hx - p - u0;
+        const int j1 = lfbp_dmin(s.Ks - 1 + j0, c.jlim - 1);
         c.m1_j0 = j1 >= j0 ? j0 : (1 << 20);  // no row kept: an empty range
         c.m1_jw = j1 >= j0 ? j1 - j0 : 0;
-        c.m1_q0 = hy - (int)td.v0;
-        c.m2_a = c.s0 - hx;
-        c.m2_b = c.Ktm - 1 - (int)td.v0 - hy;
+        c.m1_q0 = hy - v0;
+        c.m2_a = s0 - hx;
+        c.m2_b = s.Ktm - 1 - v0 - hy;
       }
-      c.tab_s = smem_addr(tab);
-      c.fast = c.mode <= 1 && td.ncols >= E && td.Ny >= E;
       break;
-    case 1:
-      c.fncols = make_fastdiv(td.ncols);
-      c.rb0 = row_base(td, in_depth, 0);
-      c.A0 = smem_addr(stage) + (uint32_t)c.rb0 * ES;
-      c.PES = (uint32_t)td.P * ES;
-      c.D = (uint32_t)(td.P - 1) * ES;
-      c.W = (uint32_t)td.Ny * td.P * ES;
-      break;
-    case 2:
-      c.fNy = make_fastdiv(td.Ny);
-      c.sbn = GE % td.Ny;
-      c.cmn = td.ncols % td.Ny;
-      break;
-    case 3: {
-      c.fNx = make_fastdiv(td.Nx);
-      c.stripe = ((td.flags >> 1) & 3) <= 1 && stripe_shape(td.Ny, td.Ks, td.Kt, td.ncols);
-      if (!c.stripe) break;
-      const int nrb = (td.Ny + 3) >> 2;
-      const int S = stripe_S(nrb);
-      const int nbands = (nrb + S - 1) / S;
-      const int ns = (td.ncols - 1 + 4 * (S - 1)) / 4 + 1;
-      const long long items = (long long)nbands * td.nrows * ns;
-      c.S = S;
-      c.ns = ns;
-      c.rowns = td.nrows * ns;
-      c.nitems_s = (int)(items < 65535 ? items : 65535);
-      c.nsteps_s = (c.nitems_s + 7) >> 3;
-      c.fns = make_fastdiv(ns);
-      c.frowns = make_fastdiv(c.rowns < 65535 ? c.rowns : 65535);
-      c.fnb = make_fastdiv(td.nrows + 1);
-      c.stripe = items < 65535 && c.rowns < 65535;
-      break;
-    }
-    case 4: {
-      const int ng = (L + 2 * GE - 2) / GE;  // groups per run, any alignment
-      const int ngc = (ng + kGroupsPerItem - 1) / kGroupsPerItem;
-      c.ngc = ngc;
-      c.items = ((td.Ny + 3) >> 2) * ngc;
-      c.fngc = make_fastdiv(ngc);
-      c.ngm = ng < 2 ? 2 : ng;
-      c.nunits = (td.Ny * c.ngm + 3) >> 2;
-      c.fngm = make_fastdiv(c.ngm);
-      break;
-    }
-    case 5:
-      c.cb = pos_mod((int)td.v0 - (map_kt(td) - 1) / 2, td.Ny);
-      c.cbb = c.cb + ((GE + td.Ny - 1) / td.Ny) * td.Ny;
-      c.ap0 = pos_mod((int)td.p + (int)td.u0 - (map_ks(td) - 1) / 2, td.Nx);
-      break;
-    case 6: {
-      const unsigned long long run0 =
-          ((unsigned long long)td.p * td.Ny * td.Ks + td.u0) * td.Kt + td.v0;  // elements
-      c.out_run0 = out_depth + run0 * ES;
-      c.run_stride = (uint32_t)(KK * ES);
-      c.om0 = (int)((((uintptr_t)c.out_run0) / ES) & (GE - 1));
-      c.kks = (int)(KK & (GE - 1));
-      c.out_lo = out_depth;
-      c.out_hi = out_depth + (unsigned long long)td.Nx * td.Ny * KK * ES;
-      break;
-    }
-    case 7: {
-      const int t_lo = map_kt(td) - td.v0 - tile_nseg(td);
-      c.inm = (int)((((uintptr_t)in_depth / ES) + (unsigned long long)t_lo) & (E - 1));
-      c.nkk = (int)(((unsigned long long)td.Ny * KK) & (E - 1));
-      c.ktm = td.Kt & (E - 1);
-      break;
-    }
     default:
       break;
   }
 }
 
 // The whole context from one thread (used where no warp is at hand).
-__device__ __forceinline__ void make_ctx(TileCtx& c, const TileDesc& td, const unsigned char* stage,
-                                         const unsigned char* in_depth, unsigned char* out_depth,
-                                         int* tab) {
-  for (int l = 0; l < 8; ++l) make_ctx_lane(c, td, stage, in_depth, out_depth, tab, l);
+__device__ __forceinline__ void make_ctx(TileCtx& c, const TileDesc& td, const TileShape* shp,
+                                         const unsigned char* stage, const unsigned char* in_depth,
+                                         unsigned char* out_depth, int* tab) {
+  for (int l = 0; l < 32; ++l) copy_shape(c, shp, l);
+  for (int part = 0; part < 4; ++part)
+    make_ctx_tile(c, td, shp, stage, in_depth, out_depth, tab, part);
 }
 
 template <class T>

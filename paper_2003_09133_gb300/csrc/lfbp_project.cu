@@ -1409,6 +1409,37 @@ struct Planes {
 // LFBP_FAULT=stall: the TMA-path kernels register their copies' bytes without
 // issuing them, so every wait on those copies runs out (tests of the timeout
 // path; the cp.async path is not affected).
+// Helper streams for independent launches of one projection (per device,
+// created on first use and kept): launches that write different output
+// depths run side by side, so that small ones (a few depths of one cut-out
+// size) share the GPU instead of running one after the other.
+constexpr int kSideStreams = 4;
+struct SideStreams {
+  int dev = -1;
+  std::mutex mu;  // held from the fork to the join of one projection
+  cudaStream_t s[kSideStreams] = {};
+  cudaEvent_t fork = nullptr, join[kSideStreams] = {};
+};
+std::mutex g_side_mu;
+std::vector<SideStreams*> g_side;  // never freed: the streams live as long as the process
+
+SideStreams* side_streams() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  for (SideStreams* s : g_side)
+    if (s->dev == dev) return s;
+  SideStreams* s = new SideStreams();
+  s->dev = dev;
+  bool ok = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < kSideStreams; ++i)
+    ok = cudaStreamCreateWithFlags(&s->s[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) return nullptr;  // (a partly created set is dropped; launches stay on the caller's stream)
+  g_side.push_back(s);
+  return s;
+}
+
 int stall_injected() {
   const char* s = std::getenv("LFBP_FAULT");
   return s && !std::strcmp(s, "stall");
@@ -1614,6 +1645,36 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
   a.sum_depths = sum_depths;
   // (each launcher sets the output tiling of its kernel: nTI, nTJ)
   if ((long long)Nx * Ny * ((nI + 15) / 16) * ((nJ + kPcTJ - 1) / kPcTJ) > 0x7fffffffLL) return -1;
+  // Without a sum over depths every launch writes its own output depths: the
+  // launches fork from the caller's stream onto helper streams and join it
+  // again before the scratch planes are released (stream order).  With a sum,
+  // they run in order on the caller's stream (the sum's order is fixed).
+  SideStreams* side = sum_depths ? nullptr : side_streams();
+  std::unique_lock<std::mutex> side_lock;  // released after the join below
+  if (side) side_lock = std::unique_lock<std::mutex>(side->mu);
+  int nlaunch = 0;
+  bool forked = false;
+  auto next_stream = [&]() -> cudaStream_t {
+    if (!side) return st;
+    if (!forked) {
+      if (cudaEventRecord(side->fork, st) != cudaSuccess) return st;
+      for (int i = 0; i < kSideStreams; ++i) cudaStreamWaitEvent(side->s[i], side->fork, 0);
+      forked = true;
+    }
+    return side->s[nlaunch++ % kSideStreams];
+  };
+  struct JoinGuard {
+    SideStreams*& side;
+    bool& forked;
+    cudaStream_t st;
+    ~JoinGuard() {
+      if (!side || !forked) return;
+      for (int i = 0; i < kSideStreams; ++i) {
+        cudaEventRecord(side->join[i], side->s[i]);
+        cudaStreamWaitEvent(st, side->join[i], 0);
+      }
+    }
+  } jg{side, forked, st};
   // depths that read one shared image (backprojections) in groups of one
   // cut-out size: several depths per block (k_phase_conv_md)
   std::vector<char> done(Nz, 0);
@@ -1638,7 +1699,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         a.ndepth = n;
         a.epi = epi;
         const int db = md_depths_per_block(n);
-        const int rc = launch_pc_md(S, db, a, pl, (n + db - 1) / db, st);
+        const int rc = launch_pc_md(S, db, a, pl, (n + db - 1) / db, next_stream());
         if (rc) return rc;
       }
     }
@@ -1659,7 +1720,7 @@ int launch_phase_projection(const float* A, int mapped, int Nx, int Ny, int Nz,
         a.ndepth = n;
         // summed depths: the first launch stores (or applies epi), later ones add
         a.epi = sum_depths ? (first ? epi : kEpiAccumulate) : epi;
-        const int rc = launch_pc_size(S, a, pl, sum_depths ? 1 : n, st);
+        const int rc = launch_pc_size(S, a, pl, sum_depths ? 1 : n, next_stream());
         if (rc) return rc;
         first = false;
         n = 0;

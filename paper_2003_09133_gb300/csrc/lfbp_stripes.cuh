@@ -1,5 +1,8 @@
-// Stripe gather: the consumer of the H -> H' map for tiles whose run stride
-// Ks*Kt is 1 mod 4 (every odd square cut-out, among others).
+// Stripe gather: the consumer of the H -> H' map for fp16 tiles whose run
+// stride Ks*Kt is 1 mod 4 (every odd square cut-out, among others).  It
+// replaces eight 2-byte shared loads per 16-byte output chunk by 16-byte
+// loads and a lane exchange; for fp32 (four loads per chunk) it measured
+// slower than the chunk path of lfbp_device.cuh, which fp32 tiles keep.
 //
 // Inside one tile row j the map reads output element (q, v) of run q from
 // segment b = (q + v - c_t) mod Ny at pixel t = Kt-1-v: a walk along a

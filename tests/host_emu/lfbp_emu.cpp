@@ -291,7 +291,12 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           std::vector<int> tab(kMaxTileRows + 1, 0x7f7f7f7f);
           g_tab = (unsigned char*)tab.data();
           g_tab_bytes = (size_t)(td.nrows + 1) * sizeof(int);
-          make_ctx(ctx, td, stage.data(), in_depth, out_depth, tab.data());
+          const int cls = (ub + 1 == d.nU ? 1 : 0) + (vb + 1 == d.nV ? 2 : 0);
+          td.shape = (unsigned short)cls;
+          const TileShape shp = depth_shape(d, Nx, Ny, Ks[z], Kt[z], es, base.flags, cls);
+          // the shape class must describe this tile
+          if (shp.nrows != td.nrows || shp.ncols != td.ncols) err("shape class does not fit the tile", shp.nrows, td.nrows);
+          make_ctx(ctx, td, &shp, stage.data(), in_depth, out_depth, tab.data());
           nfast += ctx.fast ? 1 : 0;
           nstripe += ctx.stripe ? 1 : 0;
           const int nsteps = ctx.stripe ? ctx.nsteps_s : (ctx.fast ? ctx.nunits : ctx.items);

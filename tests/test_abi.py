@@ -240,7 +240,8 @@ def test_noalloc_size_check_before_any_cuda_call(lib, monkeypatch):
     so the (never dereferenced) buffer addresses below are safe on a machine
     without a GPU.  One depth of 51 x 51 cells with 1001 x 1001 cut-outs needs
     459,459 tiles at the default 32 KiB target but 255,255 with 48 KiB tiles:
-    it fits through the larger-tile fallback; two such depths do not."""
+    it fits through the larger-tile fallback; two such depths do not.  (Each
+    depth adds a few slots for its tile shapes.)"""
     import torch
     if torch.cuda.is_available():
         pytest.skip("fake buffer addresses may only meet a library that has no GPU")
@@ -253,8 +254,9 @@ def test_noalloc_size_check_before_any_cuda_call(lib, monkeypatch):
     assert rc == 0
     assert lib.lfbp_backproject_batched_noalloc(1, ctypes.cast((P * 1)(two), P), ins, outs,
                                                 None) == -1
-    assert b"needs 510510 tiles" in lib.lfbp_last_error()
-    assert b"at most 262144" in lib.lfbp_last_error()
+    msg = lib.lfbp_last_error().decode()
+    need = int(re.search(r"needs (\d+) descriptor slots", msg).group(1))
+    assert need >= 510510 and "at most 262144" in msg
     rc, one = _plan(lib, 51, 51, [1001], [1001])
     assert rc == 0
     for tile_bytes in (None, "16384", "65536"):

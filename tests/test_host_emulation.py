@@ -111,9 +111,12 @@ def test_tiles_transpose(emu, shape, dtype):
     # the chunk path takes every tile whose rows and cells are at least a chunk long
     if Ny >= 16 // H.itemsize and min(Kt) >= 16 // H.itemsize and target >= 32768:
         assert stats[3] == stats[0]
-    # the stripe path takes the tiles whose run stride Ks*Kt is 1 mod 4
-    if Ny >= 3 and all((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt)) and target >= 32768:
+    # the stripe path takes the fp16 tiles whose run stride Ks*Kt is 1 mod 4
+    if H.itemsize == 2 and Ny >= 3 and all((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt)) \
+            and target >= 32768:
         assert stats[4] == stats[0]
+    if H.itemsize == 4:
+        assert stats[4] == 0
 
 
 def _stripe_shape(Ny, Ks, Kt):
