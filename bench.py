@@ -536,7 +536,7 @@ def _summary(line):
     return out
 
 
-def _mid_extra(lf, timed, steps, world):
+def _mid_extra(lf, timed, steps, world, no_tune=False):
     """The mid-resolution array (N = 15, 51 depths, K 45..165, fp32): the plain
     form (one launch per depth) beside the batched form."""
     import torch
@@ -546,12 +546,14 @@ def _mid_extra(lf, timed, steps, world):
     H = lfgen.generate(s, device="cuda")
     O = torch.empty_like(H)
     nb = 2 * H.numel() * 4
+    tuned = None if no_tune else lf.tune_batched([plan], [H], [O])
     tb, _, _ = timed(lambda: lf.backproject_batched([plan], [H], [O]), steps, 3)
     tp, _, _ = timed(lambda: lf.backproject_array(plan, H, O), steps, 3)
     res = {"workload": "mid: N=15, 51 depths, K_z 45..165, fp32", "bytes_per_step": nb,
            "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
-           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4), "plain_launches_per_step": s.Nz}
+           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4), "plain_launches_per_step": s.Nz,
+           "tuned": _tuned_desc(tuned)}
     del H, O
     torch.cuda.empty_cache()
     return res
@@ -622,26 +624,27 @@ def _extra_forms(lf, plans, specs, Hs, outs, timed, args, world):
                      "tuned": _tuned_desc(rtuned)}
     del rH, rO
     torch.cuda.empty_cache()
-    res["mid"] = _mid_extra(lf, timed, steps, world)
-    res["paper_window"] = _paper_window_extra(lf, specs, Hs, outs, timed, steps, world)
+    res["mid"] = _mid_extra(lf, timed, steps, world, args.no_tune)
+    res["paper_window"] = _paper_window_extra(lf, specs, Hs, outs, timed, steps, world, args.no_tune)
     res["table1"] = _table1_extra(lf, world, args.no_tune)
     res["rl_step"] = _rl_extra(lf, timed, steps)
     res["autograd_step"] = _autograd_extra(lf, timed, steps)
     return res
 
 
-def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
+def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world, no_tune=False):
     """The headline array in the literal Eqs. (4)-(9) mode (entries the paper's
     loop ranges leave unwritten are zero-filled), batched and plain."""
     import torch
     pw = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float32, mode=lf.MAP_PAPER_WINDOW) for s in specs]
     nb = sum(2 * h.numel() * h.element_size() for h in Hs)
+    tuned = None if no_tune else lf.tune_batched(pw, Hs, outs)
     tb, _, _ = timed(lambda: lf.backproject_batched(pw, Hs, outs), steps, 3)
     tp, _, _ = timed(lambda: [lf.backproject_array(p, h, o) for p, h, o in zip(pw, Hs, outs)],
                      steps, 3)
     res = {"mode": "MAP_PAPER_WINDOW", "batched_GBps": round(world * nb / (tb * 1e-3) / 1e9, 1),
            "plain_GBps": round(world * nb / (tp * 1e-3) / 1e9, 1),
-           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4)}
+           "batched_ms": round(tb, 4), "plain_ms": round(tp, 4), "tuned": _tuned_desc(tuned)}
     # even cut-outs (the literal Eq. 8): the same depths with every K one larger,
     # through the same tiled gather (the cropped odd cut-out under the window)
     if len(specs) == 1:
@@ -650,6 +653,7 @@ def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
         pe = lf.Plan(s.Nx, s.Ny, ke, kte, torch.float32, mode=lf.MAP_PAPER_WINDOW)
         He = torch.empty(pe.elems, dtype=torch.float32, device="cuda").uniform_()
         Oe = torch.empty_like(He)
+        tuned_e = None if no_tune else lf.tune_batched([pe], [He], [Oe])
         tbe, _, _ = timed(lambda: lf.backproject_batched([pe], [He], [Oe]), steps, 3)
         te, _, _ = timed(lambda: lf.backproject_array(pe, He, Oe), steps, 3)
         nbe = 2 * pe.elems * 4
@@ -657,6 +661,7 @@ def _paper_window_extra(lf, specs, Hs, outs, timed, steps, world):
                          "batched_GBps": round(world * nbe / (tbe * 1e-3) / 1e9, 1),
                          "plain_GBps": round(world * nbe / (te * 1e-3) / 1e9, 1),
                          "batched_ms": round(tbe, 4), "plain_ms": round(te, 4),
+                         "tuned": _tuned_desc(tuned_e),
                          "kernel": "k_gather_persistent / k_gather_depth (masked chunk path)"}
         del He, Oe
         torch.cuda.empty_cache()

@@ -126,19 +126,31 @@ int lfbp_plan_partition(lfbp_plan p, int nparts, int part, int* z0, int* z1);
 int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_stream);
 
 /*
- * H -> H' from host memory to host memory.  The host->device copy of one
- * chunk of depths, the map of the previous chunk (one launch per depth) and
- * the device->host copy of the chunk before overlap on two library-owned
- * helper streams and the caller's stream (Sec. 4: the z-planes are
- * independent, so each chunk is mapped as soon as it has arrived).
+ * H -> H' from host memory to host memory (Sec. 4: the z-planes are
+ * independent, so the map streams through them in any order).
  * H_host, Hp_host: host buffers of lfbp_plan_elems(p) elements, not
- * overlapping; page-locked (pinned) memory is needed for the copies to run
- * asynchronously and overlap.  dH_work, dHp_work: caller-owned device
- * buffers of the same size, 16-byte aligned, not overlapping (they hold H
- * and H' afterwards).  All work is ordered after earlier work on cuda_stream,
- * and later work on cuda_stream waits for all of it (including the last
- * copy to Hp_host); the call itself does not block.  The first call on a
- * device creates the helper streams.
+ * overlapping.  Two paths:
+ *  - default: host->device copies of fixed 64 MB byte ranges (aligned;
+ *    LFBP_HOST_CHUNK_MB sets the size) on one library-owned helper stream,
+ *    the map of each depth (one launch per depth, on cuda_stream) as soon as
+ *    the range holding its last byte has arrived, and device->host copies of
+ *    each range once every depth overlapping it is mapped, on a second helper
+ *    stream: both directions of the host link run at the same time.
+ *    dH_work, dHp_work hold H and H' afterwards.  Page-locked (pinned) host
+ *    memory is needed for the copies to overlap; pageable memory works.
+ *  - LFBP_HOST_PATH=zerocopy in the environment (read at each call), with
+ *    both buffers page-locked, mapped into the device's address space
+ *    (cudaHostAlloc, cudaHostRegister, torch pinned tensors) and 16-byte
+ *    aligned: one persistent launch reads H from host memory and writes H'
+ *    to host memory itself (its loads are cp.async copies, not TMA).
+ *    dH_work and dHp_work are validated but not touched.  Otherwise the
+ *    default path runs.
+ * dH_work, dHp_work: caller-owned device buffers of the plan's size, 16-byte
+ * aligned, not overlapping.  All work is ordered after earlier work on
+ * cuda_stream, and later work on cuda_stream waits for all of it (including
+ * the last write to Hp_host); the call itself does not block.  The first
+ * call on a device creates the helper streams (copy path) or the work list
+ * (zero-copy path).
  */
 int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH_work,
                                 void* dHp_work, void* cuda_stream);
@@ -154,7 +166,10 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
  * handle) come back; pointers may change between calls.  The first call for
  * a new list of plans allocates device memory and must not be made during
  * stream capture.  plans[i], dH[i], dHp[i] as for lfbp_backproject_array;
- * no output may overlap any input or other output.
+ * no output may overlap any input or other output.  With LFBP_LOADS=lsu in
+ * the environment (read at each call) the kernel's producers move the input
+ * segments with 16-byte cp.async copies instead of TMA bulk copies; the
+ * result is the same.
  */
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream);

@@ -142,7 +142,12 @@ __global__ void __launch_bounds__(kPlainThreads)
 // issuing the copies, so no barrier phase completes, every consumer wait runs
 // out and the kernel ends with LFBP_ERR_TIMEOUT in the status word.  The
 // normal instantiation is kStall = false.
-template <bool kStall>
+// kLsu: the producers move the segments with 16-byte cp.async copies
+// (tile_copies_lsu) instead of TMA bulk copies; every producer lane then
+// arrives on the stage's full barrier once its copies have landed, so that
+// barrier counts 32 * kProducerWarps + kProducerWarps arrivals.  Used for
+// inputs in host memory, and for device inputs where it is faster.
+template <bool kStall, bool kLsu = false>
 #ifndef LFBP_PERSIST_MINB
 #define LFBP_PERSIST_MINB 3
 #endif
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
   if (tid == 0) {
     abort_flag = 0;
     for (int s = 0; s < nstages; ++s) {
-      mbar_init(smem_addr(&full[s]), kProducerWarps);
+      mbar_init(smem_addr(&full[s]), kLsu ? 33 * kProducerWarps : kProducerWarps);
       mbar_init(smem_addr(&empty[s]), kConsumerWarps);
       // the shape index held by the stage's context slot: none yet
       reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes)[1] = -1;
@@ -196,6 +201,7 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
         }
       }
       if (t >= ntiles) {
+        if (kLsu) cp_async_arrive_noinc(fb);  // no copies pending: arrives at once
         if (lane == 0) {
           if (warp == 0) *reinterpret_cast<int*>(info_base + (size_t)s * kInfoBytes) = 1;  // end of work
           mbar_arrive(fb);
@@ -208,6 +214,10 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
       const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
       if (kStall) {
         if (lane == 0) mbar_expect_tx(fb, 16);
+      } else if (kLsu) {
+        tile_copies_lsu(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, lane, warp,
+                        kProducerWarps);
+        cp_async_arrive_noinc(fb);
       } else {
         issue_tile_loads(td, in_depth, safe_end, smem + (size_t)s * stage_bytes, fb, lane, warp,
                          kProducerWarps);
@@ -237,8 +247,10 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
       td = next;
     }
     // make sure no copy into this CTA's shared memory is still in flight (the
-    // full barriers count the bytes of every producer warp's copies)
-    if (lane == 0 && !kStall) {
+    // full barriers count the bytes of every producer warp's copies; cp.async
+    // copies are waited for by the lane that issued them)
+    if (kLsu) cp_async_wait_all();
+    if (lane == 0 && !kStall && !kLsu) {
       const int armed = it;  // stages armed: iterations 0..it-1
       for (int s = 0; s < nstages && s < armed; ++s) {
         const int last = ((armed - 1 - s) / nstages) * nstages + s;  // last iteration using s
@@ -498,6 +510,34 @@ int get_pipe(int dev, HostPipe** out) {
   return LFBP_OK;
 }
 
+// Device address of a host buffer of `bytes` bytes that the current device can
+// read and write directly (page-locked and mapped: cudaHostAlloc,
+// cudaHostRegister, or torch's pinned tensors), or nullptr.  The buffer must
+// also be 16-byte aligned, as every array of the map.
+void* mapped_host_ptr(const void* h) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of a pointer the runtime does not know
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  if ((uintptr_t)a.devicePointer & 15) return nullptr;
+  return a.devicePointer;
+}
+
+// Host-to-host path: LFBP_HOST_PATH=zerocopy lets the kernel read and write
+// mapped host buffers itself (read at each call); the default stages aligned
+// chunks through the device buffers, which measured faster (23.8 against
+// 34.8 ms per highres step: the zero-copy kernel's 1.6 KB pieces scattered
+// over host memory run below the link's rate).
+bool env_zero_copy() {
+  const char* s = std::getenv("LFBP_HOST_PATH");
+  return s && !std::strcmp(s, "zerocopy");
+}
+
+int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* const* out,
+                cudaStream_t st, int lsu_force);
+
 int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp, int mode,
              cudaStream_t st) {
   int rc = check_buffers(p, dH, dHp);
@@ -507,26 +547,35 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
   if (!H_host || !Hp_host) return fail(LFBP_ERR_NULL, "host buffer pointer is NULL");
   if (overlaps(H_host, bytes, Hp_host, bytes))
     return fail(LFBP_ERR_ALIAS, "host input and output overlap");
+  // Zero-copy (opt-in): both buffers page-locked and mapped, the persistent
+  // kernel reads H from host memory and writes H' to host memory itself (one
+  // launch; loads by cp.async through the load/store path, not TMA); the
+  // device work buffers are not touched.
+  if (env_zero_copy()) {
+    void* din = mapped_host_ptr(H_host);
+    void* dout = din ? mapped_host_ptr(Hp_host) : nullptr;
+    if (din && dout) {
+      const void* ins[1] = {din};
+      void* outs[1] = {dout};
+      return run_batched(1, &p, ins, outs, st, 1);
+    }
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   HostPipe* hp = nullptr;
   if ((rc = get_pipe(dev, &hp))) return rc;
-  // chunks of consecutive depths of at least LFBP_HOST_CHUNK_MB (default 32)
-  // MB each (fewer, larger copies)
-  const size_t chunk_min = (size_t)std::max(1, env_int("LFBP_HOST_CHUNK_MB", 32)) << 20;
-  std::vector<int> cut(1, 0);
-  size_t acc = 0;
-  for (int z = 0; z < p->Nz; ++z) {
-    acc += (p->off[z + 1] - p->off[z]) * (size_t)p->es;
-    if (acc >= chunk_min || z + 1 == p->Nz) {
-      cut.push_back(z + 1);
-      acc = 0;
-    }
-  }
-  const int nch = (int)cut.size() - 1;
+  // The copies move fixed byte ranges of LFBP_HOST_CHUNK_MB (default 64) MB,
+  // cut at multiples of the chunk size whatever the depth boundaries (copies
+  // from and to aligned addresses run at the link's rate; copies cut at depth
+  // starts, which are only 4-byte aligned, measured 25 % slower).  Depth z is
+  // mapped once the chunk holding its last byte has arrived (consecutive
+  // depths waiting for the same chunk go in one launch sequence), and chunk k
+  // is copied back once every depth that overlaps it is mapped.
+  const size_t chunk = (size_t)std::max(1, env_int("LFBP_HOST_CHUNK_MB", 64)) << 20;
+  const int nch = (int)((bytes + chunk - 1) / chunk);
   std::lock_guard<std::mutex> lk(hp->mu);
-  while ((int)hp->ev.size() < 3 * nch + 1) {
+  while ((int)hp->ev.size() < 2 * nch + 1) {
     cudaEvent_t ev;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreate");
@@ -536,28 +585,63 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
   unsigned char* hout = (unsigned char*)Hp_host;
   unsigned char* din = (unsigned char*)dH;
   unsigned char* dout = (unsigned char*)dHp;
-  cudaEvent_t start = hp->ev[3 * nch];
+  cudaEvent_t start = hp->ev[2 * nch];
   if ((e = cudaEventRecord(start, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(hp->h2d, start, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
-  for (int c = 0; c < nch; ++c) {
-    const size_t o = p->off[cut[c]] * (size_t)p->es;
-    const size_t n = (p->off[cut[c + 1]] - p->off[cut[c]]) * (size_t)p->es;
-    cudaEvent_t in_ready = hp->ev[3 * c], mapped = hp->ev[3 * c + 1], out_done = hp->ev[3 * c + 2];
+  auto chunk_range = [&](int k, size_t* o, size_t* n) {
+    *o = (size_t)k * chunk;
+    *n = std::min(chunk, bytes - *o);
+  };
+  for (int k = 0; k < nch; ++k) {  // every host->device copy, each with its event
+    size_t o, n;
+    chunk_range(k, &o, &n);
     if ((e = cudaMemcpyAsync(din + o, hin + o, n, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    cudaEventRecord(in_ready, hp->h2d);
-    cudaStreamWaitEvent(st, in_ready, 0);
-    if ((rc = launch_plain(p, din, dout, mode, cut[c], cut[c + 1], st))) return rc;
-    cudaEventRecord(mapped, st);
-    cudaStreamWaitEvent(hp->d2h, mapped, 0);
-    if ((e = cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, hp->d2h)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpyAsync(D2H)");
-    cudaEventRecord(out_done, hp->d2h);
+    if ((e = cudaEventRecord(hp->ev[2 * k], hp->h2d)) != cudaSuccess)
+      return cuda_fail(e, "cudaEventRecord");
   }
-  // the caller's stream sees the whole call complete: last copy-out, and (by
-  // stream order) every map launched on it
-  if ((e = cudaStreamWaitEvent(st, hp->ev[3 * (nch - 1) + 2], 0)) != cudaSuccess)
+  int waited = -1;  // last chunk the caller's stream has waited for
+  int done = 0;     // chunks 0..done-1 are mapped and on their way back
+  for (int z = 0; z < p->Nz;) {
+    const size_t z_end = p->off[z + 1] * (size_t)p->es;  // byte end of depth z
+    if (z_end == p->off[z] * (size_t)p->es) {  // an empty depth
+      ++z;
+      continue;
+    }
+    const int k_need = (int)((z_end - 1) / chunk);
+    int z1 = z + 1;  // depths z..z1-1 all end in chunk k_need
+    while (z1 < p->Nz && (p->off[z1 + 1] * (size_t)p->es - 1) / chunk == (size_t)k_need) ++z1;
+    if (k_need > waited) {
+      if ((e = cudaStreamWaitEvent(st, hp->ev[2 * k_need], 0)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamWaitEvent");
+      waited = k_need;
+    }
+    if ((rc = launch_plain(p, din, dout, mode, z, z1, st))) return rc;
+    // chunks wholly before the end of depth z1-1 can go back now
+    const size_t mapped_end = p->off[z1] * (size_t)p->es;
+    const int ready = z1 == p->Nz ? nch : (int)(mapped_end / chunk);
+    if (ready > done) {
+      cudaEvent_t mapped = hp->ev[2 * (ready - 1) + 1];
+      if ((e = cudaEventRecord(mapped, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+      if ((e = cudaStreamWaitEvent(hp->d2h, mapped, 0)) != cudaSuccess)
+        return cuda_fail(e, "cudaStreamWaitEvent");
+      for (int k = done; k < ready; ++k) {
+        size_t o, n;
+        chunk_range(k, &o, &n);
+        if ((e = cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, hp->d2h)) !=
+            cudaSuccess)
+          return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+      }
+      done = ready;
+    }
+    z = z1;
+  }
+  // the caller's stream sees the whole call complete: the last copy back, and
+  // (by stream order) every map launched on it
+  cudaEvent_t fin = hp->ev[2 * (nch - 1) + 1];
+  if ((e = cudaEventRecord(fin, hp->d2h)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(st, fin, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
   return LFBP_OK;
 }
@@ -565,6 +649,7 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
 // ---------------------------------------------------------------- batched --
 struct BatchState {
   int dev = -1;
+  bool lsu = false;  // producers move the segments with cp.async (k_gather_persistent<false, true>)
   std::vector<unsigned long long> uids;
   Tuning tuning{0, 0, 0};
   int ntiles = 0;
@@ -641,6 +726,20 @@ void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc
   }
 }
 
+// The persistent kernel's entry for a batch: TMA bulk copies, or cp.async
+// copies through the load/store path.
+const void* persistent_fn(bool lsu) {
+  return lsu ? (const void*)k_gather_persistent<false, true>
+             : (const void*)k_gather_persistent<false, false>;
+}
+
+// Which copy path device-resident batches use: LFBP_LOADS=lsu or tma (default),
+// read at each call.
+bool env_lsu() {
+  const char* s = std::getenv("LFBP_LOADS");
+  return s && !std::strcmp(s, "lsu");
+}
+
 int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu) {
   int sms = 0, optin = 0, dev = 0;
   int rc = device_props(&dev, &sms, &optin);
@@ -674,7 +773,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
     if ((e = cudaMemcpy(bs.d_shapes, shapes.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(shapes)");
   }
-  if ((rc = ensure_smem_attr((const void*)k_gather_persistent<false>, bs.smem))) return rc;
+  if ((rc = ensure_smem_attr(persistent_fn(bs.lsu), bs.smem))) return rc;
   // a one-node graph: relaunching it costs one cudaGraphLaunch; pointer
   // changes are patched into the node's parameters
   if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
@@ -682,7 +781,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.d_shapes, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
   cudaKernelNodeParams kp;
   std::memset(&kp, 0, sizeof(kp));
-  kp.func = (void*)k_gather_persistent<false>;
+  kp.func = (void*)persistent_fn(bs.lsu);
   kp.gridDim = dim3(bs.grid);
   kp.blockDim = dim3(kPersistentThreads);
   kp.sharedMemBytes = bs.smem;
@@ -696,7 +795,8 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
 }
 
 int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* const* out,
-                cudaStream_t st) {
+                cudaStream_t st, int lsu_force) {
+  const bool lsu = lsu_force >= 0 ? lsu_force != 0 : env_lsu();
   if (n < 0 || n > kMaxBatch) return fail(LFBP_ERR_INVALID, "batch size must be in [0, 64]");
   if (n == 0) return LFBP_OK;
   if (!plans || !in || !out) return fail(LFBP_ERR_NULL, "NULL array argument");
@@ -721,7 +821,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   const Tuning want = tuning_for(dev, n, plans);
   BatchState* bs = nullptr;
   for (auto& b : g_batches) {
-    if (b->dev != dev || !same_uids(b->uids, n, plans)) continue;
+    if (b->dev != dev || b->lsu != lsu || !same_uids(b->uids, n, plans)) continue;
     if (b->tuning.tile_bytes != want.tile_bytes || b->tuning.ctas_per_sm != want.ctas_per_sm ||
         b->tuning.stages != want.stages)
       continue;
@@ -740,6 +840,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     std::unique_ptr<BatchState> nb(new BatchState());
     for (int i = 0; i < n; ++i) nb->uids.push_back(plans[i]->uid);
     nb->tuning = want;
+    nb->lsu = lsu;
     int rc = build_batch(*nb, n, plans, want);
     if (rc) return rc;
     bs = nb.get();
@@ -760,7 +861,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
                     &bs->nstages};
     cudaKernelNodeParams kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.func = (void*)k_gather_persistent<false>;
+    kp.func = (void*)persistent_fn(bs->lsu);
     kp.gridDim = dim3(bs->grid);
     kp.blockDim = dim3(kPersistentThreads);
     kp.sharedMemBytes = bs->smem;
@@ -999,7 +1100,8 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  const std::string sig = plans_signature(dev, n, plans);
+  const bool lsu = env_lsu();
+  const std::string sig = plans_signature(dev, n, plans) + (lsu ? "/lsu" : "");
   Tuning best = default_tuning();
   if (!cache_lookup(sig, &best)) {
     const int tiles[] = {12288, 16384, 24576, 32768, 40960, 49152, 65536};
@@ -1020,13 +1122,15 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
       for (int cp : ctas) {
         Tuning t{tb, cp, 0};
         BatchState bs;
+        bs.lsu = lsu;
         if (build_batch(bs, n, plans, t) != LFBP_OK || bs.nstages < 2) continue;
         if (bs.ntiles == 0) continue;
         const int smem = bs.smem;
         for (int r = 0; r <= reps; ++r) {
           if (r == 1) cudaEventRecord(a, st);
-          k_gather_persistent<false><<<bs.grid, kPersistentThreads, smem, st>>>(np, bs.d_tiles, bs.d_shapes, bs.ntiles,
-                                                                         bs.stage_bytes, bs.nstages);
+          void* args[] = {&np, &bs.d_tiles, &bs.d_shapes, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
+          cudaLaunchKernel(persistent_fn(bs.lsu), dim3(bs.grid), dim3(kPersistentThreads), args,
+                           (size_t)smem, st);
         }
         cudaEventRecord(b, st);
         if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
@@ -1212,7 +1316,7 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
 
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream) {
-  return run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);
+  return run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, -1);
 }
 
 int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* const* dH,
@@ -1222,7 +1326,7 @@ int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* 
 
 int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
                       void* cuda_stream, int reps, int* tuned) {
-  int rc = run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream);  // validates the arguments
+  int rc = run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, -1);  // validates the arguments
   if (rc) return rc;
   if (n == 0) return LFBP_OK;
   Tuning t{0, 0, 0};

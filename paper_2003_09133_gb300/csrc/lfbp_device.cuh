@@ -43,6 +43,11 @@ constexpr int kStatusTimeout = -7;  // LFBP_ERR_TIMEOUT
 constexpr int kGroupsPerItem = 4;   // 128-byte groups per run handled by one consumer work item
                                     // (element-walk path)
 constexpr int kMaxTileRows = 64;    // rows per tile (bounds the per-tile row-base table)
+// One-row tiles whose runs are at least this long store the chunks cut by a
+// run's ends inside the main loop; shorter ones leave them to the edge pass
+// (measured: runs of 616 B, N = 51: 3827 -> 4575 GB/s with the edge pass;
+// 2028 B, N = 11, K = 507: 6080 -> 6007).
+constexpr int kInlineEndsBytes = 1800;
 
 // One tile, self-contained (32 bytes).
 struct TileDesc {
@@ -336,6 +341,19 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(bar)
       : "memory");
 }
+// 16-byte copy from global to shared memory through the load/store path
+// (not the TMA unit); both addresses 16-byte aligned.  Completion is tracked
+// per thread: cp_async_arrive_noinc makes an mbarrier arrival once all of the
+// thread's earlier such copies have landed (the barrier's count includes it).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -542,6 +560,90 @@ __device__ __forceinline__ uint32_t tile_copies(const TileDesc& td, const unsign
   return 0;
 }
 
+// Producer side through the load/store path: the same segments, widened to
+// the same 16-byte boundaries and placed at the same stage addresses as
+// tile_copies, moved as 16-byte cp.async copies.  Warp pw of np takes slots
+// pw, pw + np, ... (slot = j*Ny + b); its lanes take the slot's 16-byte pieces.
+// Used where the TMA unit's per-copy cost would bound the read rate, and for
+// inputs in host memory.  The caller makes each lane arrive on the stage's
+// barrier (cp_async_arrive_noinc) after this returns.
+__device__ __forceinline__ void tile_copies_lsu(const TileDesc& td, const unsigned char* in_depth,
+                                                const unsigned char* in_safe_end,
+                                                unsigned char* stage, int lane, int pw, int np) {
+  const int es = (td.flags & 1) ? 2 : 4, E = 16 / es;
+  const int Nx = td.Nx, Ny = td.Ny, Ks = td.Ks, Kt = td.Kt, P = td.P;
+  const int RP = row_pitch(Ny, P, es);
+  const int Ksm = map_ks(td), nseg = tile_nseg(td);
+  const int cs = (Ksm - 1) / 2;
+  const int t_lo = map_kt(td) - td.v0 - nseg;
+  const uint32_t seg_bytes = (uint32_t)nseg * es;
+  const unsigned long long KK = (unsigned long long)Ks * Kt;
+  const unsigned long long NKK = (unsigned long long)Ny * KK;
+  const int a0 = pos_mod(td.p + td.u0 - cs, Nx);
+  const uintptr_t in_el = (uintptr_t)in_depth / es;
+#if LFBP_CHECKED
+  const int nrows_bytes = td.nrows * RP * es;
+  const unsigned char* in_array = in_depth - td.off_bytes;
+#endif
+  const int jmax = (int)td.nrows < Ksm - (int)td.u0 ? (int)td.nrows : Ksm - (int)td.u0;
+  if (nseg <= 0 || jmax <= 0) return;
+  const uint32_t stage_s = smem_addr(stage);
+  // slots in (j, b) order, warp pw starting at slot pw; (j, b, a) advanced
+  // incrementally by np slots per step
+  int j = 0, b = pw;
+  while (b >= Ny) { b -= Ny; ++j; }
+  int a = a0 + j;
+  while (a >= Nx) a -= Nx;
+  for (; j < jmax;) {
+    const unsigned long long seg0 =
+        (unsigned long long)a * NKK + (unsigned long long)(Ksm - 1 - td.u0 - j) * Kt + t_lo;
+    const unsigned long long seg = seg0 + (unsigned long long)b * KK;
+    const uintptr_t src = (uintptr_t)(in_depth + seg * es);
+    const int ph0 = (int)((in_el + seg0) & (E - 1));
+    const int phb = (int)((in_el + seg) & (E - 1));
+    const int dst_el = j * RP + ph0 + b * P - phb;  // a multiple of E by the choice of P
+    const uintptr_t lo = src & ~(uintptr_t)15;
+    const uintptr_t end = src + seg_bytes;
+    uintptr_t hi = (end + 15) & ~(uintptr_t)15;
+    if (hi > (uintptr_t)in_safe_end) {
+      hi = (uintptr_t)in_safe_end > lo ? (uintptr_t)in_safe_end : lo;
+      // tail beyond the last full 16-byte block of the array: plain loads, one
+      // element per lane
+      const uintptr_t x0 = hi > src ? hi : src;
+      const uintptr_t x = x0 + (uintptr_t)lane * es;
+      if (x < end) {
+        unsigned char* d = stage + (size_t)dst_el * es + (x - lo);
+#if LFBP_CHECKED
+        if ((long long)(d - stage) + es > (long long)nrows_bytes || x < (uintptr_t)in_array ||
+            x + es > (uintptr_t)in_safe_end + 16)
+          check_fail(4, (long long)(d - stage), (long long)nrows_bytes);
+        else
+#endif
+        if (es == 4)
+          *(uint32_t*)d = __ldg((const unsigned int*)x);
+        else
+          *(uint16_t*)d = __ldg((const unsigned short*)x);
+      }
+    }
+    const int npieces = hi > lo ? (int)((hi - lo) >> 4) : 0;
+#if LFBP_CHECKED
+    if (npieces && (dst_el * es < 0 || dst_el * es + npieces * 16 > nrows_bytes || ((dst_el * es) & 15) ||
+                    lo < (uintptr_t)in_array || hi > (uintptr_t)in_safe_end)) {
+      check_fail(3, (long long)dst_el * es, (long long)npieces * 16);
+    } else
+#endif
+    for (int k = lane; k < npieces; k += 32)
+      cp_async16(stage_s + (uint32_t)(dst_el * es + 16 * k), (const void*)(lo + 16 * (uintptr_t)k));
+    // next slot of this warp
+    b += np;
+    while (b >= Ny) {
+      b -= Ny;
+      ++j;
+      if (++a == Nx) a = 0;
+    }
+  }
+}
+
 #ifndef LFBP_HOST_EMULATION
 // One warp's share of the tile's copies: the bytes of all its lanes are
 // registered on `bar` with one expect_tx, then the copies are issued.  The
@@ -581,6 +683,9 @@ struct alignas(16) TileShape {
   int ngm;       // 128-byte lines per run (any alignment), at least 2
   int nunits;    // warp steps of the tile (chunk path): ceil(Ny * ngm / 4)
   int fast;      // 1: chunk path (mode 0 or 1, ncols >= 16/es, Ny >= 16/es)
+  int inl;       // 1: a one-row tile stores the chunks cut by its runs' ends in the main
+                 // loop, element by element; 0: in an edge pass after it (runs shorter
+                 // than kInlineEndsBytes, where the main loop's element stores cost more)
   uint32_t run_stride;  // bytes between runs q and q+1 (Ks*Kt*es < 2^32)
   uint32_t PES;  // P * es
   uint32_t D;    // bytes between diagonal neighbours: (P - 1) * es
@@ -641,6 +746,7 @@ __host__ __device__ inline TileShape make_shape(int Nx, int Ny, int Ks, int Kt, 
     s.nunits = (Ny * s.ngm + 3) >> 2;
   }
   s.fast = s.mode <= 1 && ncols >= E && Ny >= E;
+  s.inl = nrows == 1 && ncols * es >= kInlineEndsBytes;
   s.run_stride = (uint32_t)(KK * es);
   s.PES = (uint32_t)P * es;
   s.D = (uint32_t)(P - 1) * es;
@@ -1018,19 +1124,22 @@ __device__ __forceinline__ ChunkAddr chunk_addr(const TileCtx& c, int q, int e) 
 }
 
 // Paper-window mask of chunk element k (run q): rows j (k < kx) or j + 1,
-// columns vl + k or k - kx; see gather_chunks.
-template <bool ONEROW>
+// columns vl + k or k - kx; see gather_chunks.  EVEN: the tile is an even
+// cut-out, whose last column (vl >= vlim) is zero as well.
+template <bool ONEROW, bool EVEN>
 __device__ __forceinline__ bool chunk_keep(const TileCtx& c, const ChunkAddr& s, int q, int k) {
   const bool nxt = !ONEROW && k >= s.kx;
   const int j = nxt ? s.j + 1 : s.j;
   const int vl = nxt ? k - s.kx : s.vl + k;
   return (unsigned)(j - c.m1_j0) <= (unsigned)c.m1_jw &&
-         (unsigned)(q + vl - c.m1_q0) <= (unsigned)c.Kt1 && vl < c.vlim;
+         (unsigned)(q + vl - c.m1_q0) <= (unsigned)c.Kt1 && (!EVEN || vl < c.vlim);
 }
 
-template <class T, bool MASK, bool ONEROW>
+// MASK: 0 none (transpose mode), 1 the paper window on an odd cut-out, 2 the
+// paper window on an even cut-out.
+template <class T, int MASK, bool ONEROW>
 __device__ __forceinline__ T masked(const TileCtx& c, const ChunkAddr& s, int q, int k, T x) {
-  if (MASK && !chunk_keep<ONEROW>(c, s, q, k)) return (T)0;
+  if (MASK && !chunk_keep<ONEROW, MASK == 2>(c, s, q, k)) return (T)0;
   return x;
 }
 
@@ -1049,15 +1158,16 @@ __device__ __forceinline__ uint32_t chunk_elem(const TileCtx& c, const ChunkAddr
 }
 
 // The same, for a chunk whose elements may be masked: a masked element in
-// the zero column of an even cut-out can sit one element before the stage;
-// it is read inside the stage instead (the value is dropped either way).
-template <bool MASK, bool ONEROW>
+// the zero column of an even cut-out (MASK == 2) can sit one element before
+// the stage; it is read inside the stage instead (the value is dropped
+// either way).
+template <int MASK, bool ONEROW>
 __device__ __forceinline__ uint32_t chunk_elem_c(const TileCtx& c, const ChunkAddr& s, int k) {
   const uint32_t a = chunk_elem<ONEROW>(c, s, k);
-  return MASK && (int)(a - c.stage_s) < 0 ? c.stage_s : a;
+  return MASK == 2 && (int)(a - c.stage_s) < 0 ? c.stage_s : a;
 }
 
-template <int ES, bool ONEROW, bool MASK>
+template <int ES, bool ONEROW, int MASK>
 __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarps, int lane,
                                               int rot) {
   using T = typename std::conditional<ES == 4, uint32_t, uint16_t>::type;
@@ -1068,9 +1178,11 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
   const int Ny = c.Ny, L = c.L;
   int first = (w - rot) % nwarps;
   if (first < 0) first += nwarps;
-  // Chunks cut by a run's end: one-row tiles store them element by element in
-  // the step that meets them; multi-row tiles leave them to an edge pass after
-  // the loop (measured: each is the faster choice for its kind of tile).
+  // Chunks cut by a run's end: one-row tiles with long runs (c.inl) store
+  // them element by element in the step that meets them; other tiles leave
+  // them to an edge pass after the loop (measured: each is the faster choice
+  // for its kind of tile).
+  const bool inl = ONEROW && c.inl;
   for (int u = first; u < c.nunits; u += nwarps) {
     const int f = u * 4 + r;
     const int q = (int)fdiv2((uint32_t)f, c.fngm);
@@ -1079,7 +1191,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
     const int m = (c.om0 + q * c.kks) & (GE - 1);  // run q's first element within its line
     const int e = g * GE + lane_el - m;            // run element of chunk element 0
     const bool whole = e >= 0 && e + EPL <= L;
-    if (ONEROW ? (e >= L || e <= -EPL) : !whole) continue;
+    if (inl ? (e >= L || e <= -EPL) : !whole) continue;
     unsigned char* dst =
         c.out_run0 + (unsigned long long)(uint32_t)q * c.run_stride + (long long)e * ES;
     const ChunkAddr s = chunk_addr<ES, ONEROW>(c, q, e);
@@ -1099,7 +1211,7 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
       }
     }
   }
-  if (ONEROW) return;
+  if (inl) return;
   // edge pass: the first and the last chunk of every run where a run end cuts
   // them, element by element; edge chunk i goes to the warp whose rotated
   // index is i mod nwarps, so each warp takes at most a few of them
@@ -1243,26 +1355,38 @@ __device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nw
     if (c.mode == 0) {
       if (c.es == 4) {
         if (c.nrows == 1)
-          gather_chunks<4, true, false>(c, w, nwarps, lane, rot);
+          gather_chunks<4, true, 0>(c, w, nwarps, lane, rot);
         else
-          gather_chunks<4, false, false>(c, w, nwarps, lane, rot);
+          gather_chunks<4, false, 0>(c, w, nwarps, lane, rot);
       } else {
         if (c.nrows == 1)
-          gather_chunks<2, true, false>(c, w, nwarps, lane, rot);
+          gather_chunks<2, true, 0>(c, w, nwarps, lane, rot);
         else
-          gather_chunks<2, false, false>(c, w, nwarps, lane, rot);
+          gather_chunks<2, false, 0>(c, w, nwarps, lane, rot);
+      }
+    } else if (!c.even) {
+      if (c.es == 4) {
+        if (c.nrows == 1)
+          gather_chunks<4, true, 1>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<4, false, 1>(c, w, nwarps, lane, rot);
+      } else {
+        if (c.nrows == 1)
+          gather_chunks<2, true, 1>(c, w, nwarps, lane, rot);
+        else
+          gather_chunks<2, false, 1>(c, w, nwarps, lane, rot);
       }
     } else {
       if (c.es == 4) {
         if (c.nrows == 1)
-          gather_chunks<4, true, true>(c, w, nwarps, lane, rot);
+          gather_chunks<4, true, 2>(c, w, nwarps, lane, rot);
         else
-          gather_chunks<4, false, true>(c, w, nwarps, lane, rot);
+          gather_chunks<4, false, 2>(c, w, nwarps, lane, rot);
       } else {
         if (c.nrows == 1)
-          gather_chunks<2, true, true>(c, w, nwarps, lane, rot);
+          gather_chunks<2, true, 2>(c, w, nwarps, lane, rot);
         else
-          gather_chunks<2, false, true>(c, w, nwarps, lane, rot);
+          gather_chunks<2, false, 2>(c, w, nwarps, lane, rot);
       }
     }
     return;

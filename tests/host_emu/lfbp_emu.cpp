@@ -85,6 +85,15 @@ static inline void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint3
   if (g_errors == 0) std::memcpy(g_stage + dst, s, bytes);
   g_copied += bytes;
 }
+// 16-byte cp.async (load/store path): same checks as a bulk copy of 16 bytes
+static inline void cp_async16(uint32_t dst, const void* src) {
+  const unsigned char* s = (const unsigned char*)src;
+  if (((uintptr_t)s & 15) || (dst & 15)) err("cp.async misaligned", (uintptr_t)s & 15, dst & 15);
+  if (s < g_in || s + 16 > g_in + g_in_bytes) err("cp.async reads outside input", s - g_in, 16);
+  if ((size_t)dst + 16 > g_stage_bytes) err("cp.async writes outside stage", dst, 16);
+  if (g_errors == 0) std::memcpy(g_stage + dst, s, 16);
+  g_copied += 16;
+}
 static inline void emu_smem_check(long long byte_off) {
   if (byte_off < 0 || (size_t)byte_off >= g_stage_bytes) err("smem read outside stage", byte_off, 0);
 }
@@ -285,6 +294,23 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
             for (int lane = 0; lane < 32; ++lane)
               tile_copies(td, in_depth, safe_end, stage.data(), 0, lane, pw, np, false);
           if (g_expect != g_copied) err("expect_tx bytes differ from bytes copied", g_expect, g_copied);
+          // the load/store-path copies (tile_copies_lsu) must fill a second
+          // stage with exactly the same bytes, poison included
+          {
+            std::vector<unsigned char> stage2(stage.size());
+            std::memset(stage2.data(), 0xA5, stage2.size());
+            const unsigned long long copied_tma = g_copied;
+            g_copied = 0;
+            g_stage = stage2.data();
+            for (int pw = 0; pw < np; ++pw)
+              for (int lane = 0; lane < 32; ++lane)
+                tile_copies_lsu(td, in_depth, safe_end, stage2.data(), lane, pw, np);
+            if (g_copied != copied_tma) err("cp.async bytes differ from bulk-copy bytes", g_copied, copied_tma);
+            if (std::memcmp(stage.data(), stage2.data(), stage.size()) != 0)
+              err("cp.async stage differs from the bulk-copy stage", (long long)tiles, 0);
+            g_stage = stage.data();
+            g_copied = copied_tma;
+          }
           const int nwarps = nthr;  // here: number of consumer warps
           TileCtx ctx;
           // table entries past nrows stay poisoned: reading them is an error

@@ -72,6 +72,24 @@ def test_random_bits_plain_batched_adjoint(lf, shape, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}")
+def test_random_bits_batched_lsu_copies(lf, shape, dtype, monkeypatch):
+    """The persistent kernel with its segments moved by 16-byte cp.async copies
+    (LFBP_LOADS=lsu) instead of TMA bulk copies: the same bits, both modes."""
+    monkeypatch.setenv("LFBP_LOADS", "lsu")
+    Nx, Ny, Ks, Kt = shape
+    plan = lf.Plan(Nx, Ny, Ks, Kt, dtype)
+    H = _random_bits(plan.elems, dtype, 14)
+    Hn = H.cpu().numpy()
+    _assert_same_bits(lf.backproject_batched([plan], [H])[0],
+                      oracle.transpose(Hn, Nx, Ny, Ks, Kt), "batched lsu")
+    pw = lf.Plan(Nx, Ny, Ks, Kt, dtype, mode=lf.MAP_PAPER_WINDOW)
+    _assert_same_bits(lf.backproject_batched([pw], [H])[0],
+                      oracle.paper_window(Hn, Nx, Ny, Ks, Kt), "batched lsu, paper window")
+    lf.sync_status()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
 @pytest.mark.parametrize("shape", SHAPES[:7], ids=lambda s: f"{s[0]}x{s[1]}_K{s[2][0]}")
 def test_paper_window_mode(lf, shape, dtype):
     Nx, Ny, Ks, Kt = shape
@@ -208,8 +226,16 @@ def test_autograd_workload_map(lf):
     _full_workload(lf, "autograd")
 
 
-def test_host_to_host_pipeline(lf):
-    """Pinned host H -> device -> H' -> pinned host, copies overlapped with the map."""
+@pytest.mark.parametrize("path", ["copy", "zerocopy"])
+def test_host_to_host_pipeline(lf, path, monkeypatch):
+    """Pinned host H -> H' -> pinned host: by default aligned byte ranges are
+    staged through the device buffers with overlapped copies (here 1 MB ranges,
+    so that depths straddle them); LFBP_HOST_PATH=zerocopy lets the kernel read
+    and write the mapped host buffers itself."""
+    if path == "zerocopy":
+        monkeypatch.setenv("LFBP_HOST_PATH", "zerocopy")
+    else:
+        monkeypatch.setenv("LFBP_HOST_CHUNK_MB", "1")
     for name, dtype in (("mid", torch.float32), ("tiny", torch.float16)):
         spec = lfgen.config_specs(name)[0]
         plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, dtype)
@@ -218,7 +244,32 @@ def test_host_to_host_pipeline(lf):
         torch.cuda.current_stream().synchronize()
         lf.sync_status()
         _assert_same_bits(out, oracle.transpose(H.numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt),
-                          f"host pipeline {name}")
+                          f"host pipeline {name} ({path})")
+
+
+@pytest.mark.parametrize("path", ["copy", "zerocopy"])
+def test_host_to_host_pageable_and_odd_shapes(lf, path, monkeypatch):
+    """Both host paths on pinned and pageable buffers (pageable ones always
+    take the staged copies), on shapes with column splits, fp16, an even
+    cut-out, and ranges of 1 MB that cut through depths."""
+    if path == "zerocopy":
+        monkeypatch.setenv("LFBP_HOST_PATH", "zerocopy")
+    monkeypatch.setenv("LFBP_HOST_CHUNK_MB", "1")
+    for Nx, Ny, Ks, Kt, dtype, mode in ((51, 51, [153], [153], torch.float32, 0),
+                                        (9, 13, [27, 3, 1], [39, 13, 5], torch.float16, 0),
+                                        (19, 19, [57, 95, 19, 133], [57, 95, 19, 133], torch.float16, 0),
+                                        (5, 5, [16, 10], [16, 10], torch.float32, 1)):
+        plan = lf.Plan(Nx, Ny, Ks, Kt, dtype, mode=mode)
+        Hd = _random_bits(plan.elems, dtype, 15)
+        Hn = Hd.cpu().numpy()
+        want = (oracle.paper_window(Hn, Nx, Ny, Ks, Kt) if mode else
+                oracle.transpose(Hn, Nx, Ny, Ks, Kt))
+        for pinned in (True, False):
+            H = Hd.cpu().pin_memory() if pinned else Hd.cpu()
+            out = lf.backproject_array_host(plan, H)
+            torch.cuda.current_stream().synchronize()
+            lf.sync_status()
+            _assert_same_bits(out, want, f"host {Nx}x{Ny} pinned={pinned} ({path})")
 
 
 def test_tuner_then_batched(lf, tmp_path, monkeypatch):

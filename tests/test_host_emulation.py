@@ -96,6 +96,8 @@ SHAPES = [
     (3, 7, [9, 21], [9, 21], 32768),      # 1 and 2
     (7, 27, [21, 35], [21, 35], 32768),   # 7 run blocks: bands of 4
     (5, 3, [13, 21], [9, 17], 8192),      # Ks*Kt = 1 mod 4 with Ks != Kt, multi-row tiles
+    (3, 3, [461], [461], 8192),           # one-row fp32 tiles with runs of >= 1800 B: run ends
+                                          # stored inside the main loop (shorter: edge pass)
 ]
 
 
