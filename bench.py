@@ -749,7 +749,8 @@ def _autograd_extra(lf, timed, steps):
 def _tuned_desc(t):
     if t is None:
         return None
-    return {"tile_bytes": t[0], "ctas_per_sm": t[1], "stages": t[2] or "as many as fit"}
+    return {"tile_bytes": t[0], "ctas_per_sm": t[1], "stages": t[2] or "as many as fit",
+            "consumer": "pairs where eligible" if t[3] else "chunks / stripes"}
 
 
 def _fp32_fma_peak_tflops():

@@ -212,14 +212,17 @@ int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* 
 /*
  * Autotuner for lfbp_backproject_batched: times a small grid of launch shapes
  * (shared-memory bytes per tile in {12, 16, 24, 32, 40, 48, 64} KiB x
- * persistent CTAs per SM in {1, 2, 3, 4}) on the given buffers with CUDA events (reps timed launches
+ * persistent CTAs per SM in {1, 2, 3, 4} x the pair consumer on or off) on
+ * the given buffers with CUDA events (reps timed launches
  * each, after one warm-up) and keeps the fastest for later batched calls with
  * the same plans (by handle).  Writes H' into dHp as a side effect and
  * synchronises the stream.  If the environment variable LFBP_TUNE_CACHE names
  * a file, the choice is appended there, keyed by device name and array
  * shapes, and later processes take it from there without timing.  tuned
- * (may be NULL) receives {tile bytes, CTAs per SM, stages (0 = as many as
- * fit)}.  Arguments otherwise as for lfbp_backproject_batched.
+ * (may be NULL, else 4 ints) receives {tile bytes, CTAs per SM, stages (0 =
+ * as many as fit), pair consumer (1 = on)}.  Arguments otherwise as for
+ * lfbp_backproject_batched.  Without tuning, LFBP_PAIRS=0 in the environment
+ * turns the pair consumer off (it is on by default; the result is the same).
  */
 int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
                       void* cuda_stream, int reps, int* tuned);

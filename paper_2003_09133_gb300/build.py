@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "liblfbp.so")
 LIB_CHECK = os.path.join(BUILD, "liblfbp_check.so")
 
 SOURCES = ["lfbp.cu", "lfbp_project.cu"]
-HEADERS = ["lfbp_device.cuh", "lfbp_stripes.cuh", "lfbp_project.h"]
+HEADERS = ["lfbp_device.cuh", "lfbp_stripes.cuh", "lfbp_pairs.cuh", "lfbp_project.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

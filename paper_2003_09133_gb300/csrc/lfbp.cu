@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
       if (*reinterpret_cast<const int*>(info) != 0) break;
       // rotate the step-to-warp assignment by the tile's step count
       const TileCtx& tc = *reinterpret_cast<const TileCtx*>(info + 16);
-      const int nsteps = tc.stripe ? tc.nsteps_s : (tc.fast ? tc.nunits : tc.items);
+      const int nsteps = tc.pair ? (tc.punits + 31) / 32
+                                 : (tc.stripe ? tc.nsteps_s : (tc.fast ? tc.nunits : tc.items));
       gather_tile_ctx(tc, cw, kConsumerWarps, lane, (it * nsteps) % kConsumerWarps);
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_addr(&empty[s]));
@@ -348,6 +349,7 @@ struct Tuning {
   int tile_bytes;   // target shared-memory bytes of one tile
   int ctas_per_sm;  // persistent CTAs per SM
   int stages;       // stages per persistent CTA (0 = as many as fit)
+  int pairs;        // 1: tiles that can take the pair consumer do (lfbp_pairs.cuh)
 };
 
 Tuning default_tuning() {
@@ -355,6 +357,7 @@ Tuning default_tuning() {
   t.tile_bytes = env_int("LFBP_TILE_BYTES", 32768);
   t.ctas_per_sm = env_int("LFBP_CTAS_PER_SM", 3);
   t.stages = env_int("LFBP_STAGES", 0);
+  t.pairs = env_int("LFBP_PAIRS", 1) != 0;
   if (t.tile_bytes < 1024) t.tile_bytes = 1024;
   if (t.tile_bytes > 65536) t.tile_bytes = 65536;
   if (t.ctas_per_sm < 1) t.ctas_per_sm = 1;
@@ -405,7 +408,8 @@ const std::vector<DepthTiling>& plan_tiling(lfbp_plan p, int target) {
   return t;
 }
 
-TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr) {
+// pairs = 0 keeps the depth's tiles off the pair consumer (flags bit 5).
+TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr, int pairs) {
   TileDesc t;
   std::memset(&t, 0, sizeof(t));
   t.off_bytes = p->off[z] * (size_t)p->es;
@@ -416,7 +420,7 @@ TileDesc depth_desc(lfbp_plan p, int z, const DepthTiling& d, int mode, int arr)
   t.P = (unsigned short)d.P;
   t.arr = (unsigned char)arr;
   t.flags = (unsigned char)((p->es == 2 ? 1 : 0) | (mode << 1) | ((p->Ks[z] % 2 == 0) << 3) |
-                            ((p->Kt[z] % 2 == 0) << 4));
+                            ((p->Kt[z] % 2 == 0) << 4) | (pairs ? 0 : 32));
   return t;
 }
 
@@ -447,7 +451,8 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
   if (rc) return rc;
   for (int z = z0; z < z1; ++z) {
     const DepthTiling& d = tl[z];
-    const TileDesc base = depth_desc(p, z, d, mode, 0);
+    // the pair consumer measured faster for fp16 plain launches, slower for fp32
+    const TileDesc base = depth_desc(p, z, d, mode, 0, p->es == 2);
     DepthShapes ds;
     depth_shapes(p, z, d, base, ds.s);
     dim3 grid(d.nV, p->Nx, d.nU);
@@ -651,7 +656,7 @@ struct BatchState {
   int dev = -1;
   bool lsu = false;  // producers move the segments with cp.async (k_gather_persistent<false, true>)
   std::vector<unsigned long long> uids;
-  Tuning tuning{0, 0, 0};
+  Tuning tuning{0, 0, 0, 0};
   int ntiles = 0;
   int stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
   TileDesc* d_tiles = nullptr;    // work list, followed in the same allocation by
@@ -697,7 +702,7 @@ constexpr size_t kMaxCachedBatches = 8;
 // then v-block, so that tiles in flight together touch neighbouring input
 // segments and neighbouring output runs.
 // With each depth come its four tile shapes (depth_shapes), referenced by index.
-void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc>& tiles,
+void build_tiles(int n, const lfbp_plan* plans, int target, int pairs, std::vector<TileDesc>& tiles,
                  std::vector<TileShape>& shapes, int* max_tile) {
   *max_tile = 0;
   for (int i = 0; i < n; ++i) {
@@ -706,7 +711,7 @@ void build_tiles(int n, const lfbp_plan* plans, int target, std::vector<TileDesc
     for (int z = 0; z < p->Nz; ++z) {
       const DepthTiling& d = tl[z];
       *max_tile = std::max(*max_tile, d.max_tile_bytes);
-      const TileDesc base = depth_desc(p, z, d, (int)p->mode, i);
+      const TileDesc base = depth_desc(p, z, d, (int)p->mode, i, pairs);
       const size_t s0 = shapes.size();
       shapes.resize(s0 + 4);
       depth_shapes(p, z, d, base, &shapes[s0]);
@@ -748,7 +753,7 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   std::vector<TileDesc> tiles;
   std::vector<TileShape> shapes;
   int max_tile = 0;
-  build_tiles(n, plans, tu.tile_bytes, tiles, shapes, &max_tile);
+  build_tiles(n, plans, tu.tile_bytes, tu.pairs, tiles, shapes, &max_tile);
   if (shapes.size() > 65536) return fail(LFBP_ERR_BAD_SHAPE, "more than 16384 depths in one batch");
   bs.ntiles = (int)tiles.size();
   bs.stage_bytes = (max_tile + 127) & ~127;
@@ -823,7 +828,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   for (auto& b : g_batches) {
     if (b->dev != dev || b->lsu != lsu || !same_uids(b->uids, n, plans)) continue;
     if (b->tuning.tile_bytes != want.tile_bytes || b->tuning.ctas_per_sm != want.ctas_per_sm ||
-        b->tuning.stages != want.stages)
+        b->tuning.stages != want.stages || b->tuning.pairs != want.pairs)
       continue;
     bs = b.get();
     break;
@@ -997,7 +1002,7 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
     std::vector<TileShape> shapes;
     tiles.reserve((size_t)need);
     int max_tile = 0;
-    build_tiles(n, plans, tu.tile_bytes, tiles, shapes, &max_tile);
+    build_tiles(n, plans, tu.tile_bytes, tu.pairs, tiles, shapes, &max_tile);
     const int stage_bytes = (max_tile + 127) & ~127;
     const int per_cta_budget = std::min(nd->optin, (227 * 1024) / tu.ctas_per_sm - 1024);
     const int per_stage = stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
@@ -1075,9 +1080,10 @@ bool cache_lookup(const std::string& sig, Tuning* t) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
   char key[4096];
-  Tuning x{0, 0, 0};
+  Tuning x{0, 0, 0, 1};
   bool found = false;
-  while (std::fscanf(f, "%4095s %d %d %d", key, &x.tile_bytes, &x.ctas_per_sm, &x.stages) == 4)
+  while (std::fscanf(f, "%4095s %d %d %d %d", key, &x.tile_bytes, &x.ctas_per_sm, &x.stages,
+                     &x.pairs) == 5)
     if (sig == key) {
       *t = x;
       found = true;
@@ -1091,7 +1097,8 @@ void cache_store(const std::string& sig, const Tuning& t) {
   if (!path || !*path || sig.size() > 4000) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d\n", sig.c_str(), t.tile_bytes, t.ctas_per_sm, t.stages);
+  std::fprintf(f, "%s %d %d %d %d\n", sig.c_str(), t.tile_bytes, t.ctas_per_sm, t.stages,
+               t.pairs);
   std::fclose(f);
 }
 
@@ -1118,9 +1125,10 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
       np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
     }
     int rc = LFBP_OK;
+    for (int pr = 1; pr >= 0; --pr)
     for (int tb : tiles)
       for (int cp : ctas) {
-        Tuning t{tb, cp, 0};
+        Tuning t{tb, cp, 0, pr};
         BatchState bs;
         bs.lsu = lsu;
         if (build_batch(bs, n, plans, t) != LFBP_OK || bs.nstages < 2) continue;
@@ -1329,13 +1337,14 @@ int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void
   int rc = run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, -1);  // validates the arguments
   if (rc) return rc;
   if (n == 0) return LFBP_OK;
-  Tuning t{0, 0, 0};
+  Tuning t{0, 0, 0, 0};
   rc = tune_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, reps < 1 ? 3 : reps, &t);
   if (rc) return rc;
   if (tuned) {
     tuned[0] = t.tile_bytes;
     tuned[1] = t.ctas_per_sm;
     tuned[2] = t.stages;
+    tuned[3] = t.pairs;
   }
   return LFBP_OK;
 }

@@ -56,7 +56,8 @@ struct TileDesc {
   unsigned short Nx, Ny, Ks, Kt;
   unsigned short P;     // slot pitch in elements
   unsigned char arr;    // array slot in BatchPtrs
-  unsigned char flags;  // bit 0: fp16 storage; bits 1-2: mode; bits 3-4: Ks, Kt even
+  unsigned char flags;  // bit 0: fp16 storage; bits 1-2: mode; bits 3-4: Ks, Kt even;
+                        // bit 5: the pair consumer is off for this tile
   unsigned short shape; // index of the tile's TileShape in the launch's shape table
 };
 static_assert(sizeof(TileDesc) == 32, "TileDesc layout");
@@ -93,6 +94,10 @@ inline int lfbp_max(int a, int b) { return a > b ? a : b; }
 #define LFBP_STRIPES 1  // 0: every tile takes the chunk or element-walk path
 #endif
 constexpr int kStripeMaxS = LFBP_STRIPE_SMAX;  // run blocks per stripe (template instances 1..)
+#ifndef LFBP_PAIRS
+#define LFBP_PAIRS 1  // 0: no tile takes the pair path
+#endif
+constexpr bool kPairs = LFBP_PAIRS != 0;
 
 // Run blocks per stripe for nrb = ceil(Ny/4) run blocks: all of them up to
 // five; beyond, the size in 3..5 whose bands waste the fewest chunk slots
@@ -395,6 +400,11 @@ __device__ __forceinline__ uint16_t lds<uint16_t>(uint32_t addr) {
   asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
   return v;
 }
+__device__ __forceinline__ uint2 lds64(uint32_t addr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+  return v;
+}
 __device__ __forceinline__ uint4 lds128(uint32_t addr) {
   uint4 v;
   asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -692,6 +702,13 @@ struct alignas(16) TileShape {
   uint32_t W;    // bytes of Ny slots: Ny * P * es
   int cbb_add;   // a multiple of Ny that is >= 128/es
   int ctm, csm;  // c_t mod Ny, c_s mod Nx (c from the map's cut-out)
+  // pair path (lfbp_pairs.cuh)
+  int pair;      // 1: pair path (mode 0, Ks*Kt = 1 mod 16/es, Ny >= 16/es, ncols > 16/es)
+  int pnd;       // anti-diagonals per tile row
+  int pnpr;      // pair slots per anti-diagonal: (Ny - 1) / 2
+  int pnu;       // anti-diagonals per row on which one slot can hold a unit
+  int punits;    // pair units of the tile: nrows * pnpr * pnu
+  FastDiv fpnd, fpnpr, fpnu;
   // stripe path (lfbp_stripes.cuh)
   int stripe;    // 1: stripe path (mode 0 or 1, Ks*Kt = 1 mod 4, Ny >= 3, ncols >= 8)
   int S;         // run blocks of 4 runs per stripe
@@ -759,11 +776,28 @@ __host__ __device__ inline TileShape make_shape(int Nx, int Ny, int Ks, int Kt, 
   s.fNx = make_fastdiv(Nx);
   s.fngc = make_fastdiv(s.ngc);
   s.fngm = make_fastdiv(s.ngm);
+  s.pair = 0;
+  s.pnd = s.pnpr = s.pnu = s.punits = 0;
+  s.fpnd = s.fpnpr = s.fpnu = make_fastdiv(1);
+  if (kPairs && !(flags & 32) && s.mode == 0 && s.fast && (KK & (E - 1)) == 1 && (Ny & 1) &&
+      ncols > E) {
+    s.pnd = (Ny + ncols - 2) / E + 2;
+    s.pnpr = (Ny - 1) / 2;
+    s.pnu = (ncols - E) / E + 2;
+    const long long units = (long long)nrows * s.pnpr * s.pnu;
+    if (units < (1 << 24) && s.pnpr >= 2 && s.pnd >= 2) {
+      s.pair = 1;
+      s.punits = (int)units;
+      s.fpnd = make_fastdiv(s.pnd);
+      s.fpnpr = make_fastdiv(s.pnpr);
+      s.fpnu = make_fastdiv(s.pnu);
+    }
+  }
   s.stripe = 0;
   s.S = s.ns = s.rowns = s.nitems_s = s.nsteps_s = 0;
   s.fns = s.frowns = make_fastdiv(1);
   s.fnb = make_fastdiv(nrows + 1);
-  if (s.mode <= 1 && stripe_shape(Ny, Ks, Kt, ncols, es)) {
+  if (!s.pair && s.mode <= 1 && stripe_shape(Ny, Ks, Kt, ncols, es)) {
     const int nrb = (Ny + 3) >> 2;
     const int S = stripe_S(nrb);
     const int nbands = (nrb + S - 1) / S;
@@ -1338,12 +1372,17 @@ __device__ __forceinline__ void gather_tile(const TileCtx& c, int w, int nwarps,
 }  // namespace lfbp
 
 #include "lfbp_stripes.cuh"
+#include "lfbp_pairs.cuh"
 
 namespace lfbp {
 
 // Consumer side, given the tile's context (in shared memory).
 __device__ __forceinline__ void gather_tile_ctx(const TileCtx& cs, int w, int nwarps, int lane,
                                                 int rot = 0) {
+  if (cs.pair) {
+    gather_pairs_ctx(cs, w, nwarps, lane, rot);
+    return;
+  }
 #if !defined(LFBP_HOST_EMULATION) && LFBP_STRIPES
   if (cs.stripe) {
     gather_stripes_ctx(cs, w, nwarps, lane, rot);

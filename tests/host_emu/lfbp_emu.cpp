@@ -29,6 +29,10 @@ struct uint4 {
 struct uint2 {
   unsigned x, y;
 };
+static inline uint2 make_uint2(unsigned x, unsigned y) { return uint2{x, y}; }
+static inline uint4 make_uint4(unsigned x, unsigned y, unsigned z, unsigned w) {
+  return uint4{x, y, z, w};
+}
 
 namespace {
 const unsigned char* g_in = nullptr;
@@ -126,6 +130,15 @@ static inline T lds(uint32_t addr) {
 template <class T, int OFF>
 static inline T lds_off(uint32_t addr) {
   return lds<T>(addr + OFF);
+}
+static inline uint2 lds64(uint32_t addr) {
+  uint2 v{0, 0};
+  if (addr >= kTabBase || (size_t)addr + 8 > g_stage_bytes || (addr & 7)) {
+    err("8-byte lds outside stage or misaligned", addr, (long long)g_stage_bytes);
+    return v;
+  }
+  std::memcpy(&v, g_stage + addr, 8);
+  return v;
 }
 static inline uint4 lds128(uint32_t addr) {
   uint4 v{0, 0, 0, 0};
@@ -231,7 +244,8 @@ static void emu_stripes_ctx(const TileCtx& c, int nwarps, int rot) {
 // Returns the number of violations (0 = clean); stats[0] = tiles, stats[1] =
 // bytes copied by bulk copies, stats[2] = max tile bytes, stats[3] = tiles
 // whose context selects the chunk path, stats[4] = tiles that took the stripe
-// path (which comes first).  nthr = consumer warps.
+// path, stats[5] = tiles that took the pair path (pair, then stripe, then the
+// chunk or element-walk path).  nthr = consumer warps.
 extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned char* counts,
                         int Nx, int Ny, int Nz, const int* Ks, const int* Kt, int es, int mode,
                         int target, int nthr, unsigned long long* stats) {
@@ -249,7 +263,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
   g_out_bytes = total;
   g_counts = counts;
   const unsigned char* safe_end = in + (total & ~(size_t)15);
-  unsigned long long tiles = 0, copied = 0, maxb = 0, nfast = 0, nstripe = 0;
+  unsigned long long tiles = 0, copied = 0, maxb = 0, nfast = 0, nstripe = 0, npair = 0;
   for (int z = 0; z < Nz && g_errors == 0; ++z) {
     DepthTiling d = tile_depth(Ny, Ks[z], Kt[z], es, target);
     if ((unsigned long long)d.max_tile_bytes > maxb) maxb = d.max_tile_bytes;
@@ -325,7 +339,9 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
           make_ctx(ctx, td, &shp, stage.data(), in_depth, out_depth, tab.data());
           nfast += ctx.fast ? 1 : 0;
           nstripe += ctx.stripe ? 1 : 0;
-          const int nsteps = ctx.stripe ? ctx.nsteps_s : (ctx.fast ? ctx.nunits : ctx.items);
+          npair += ctx.pair ? 1 : 0;
+          const int nsteps = ctx.pair ? (ctx.punits + 31) / 32
+                                      : (ctx.stripe ? ctx.nsteps_s : (ctx.fast ? ctx.nunits : ctx.items));
           const int rot = (int)((tiles * (unsigned long long)nsteps) % nwarps);
           if (ctx.stripe) {
             emu_stripes_ctx(ctx, nwarps, rot);
@@ -346,6 +362,7 @@ extern "C" long emu_run(const unsigned char* in, unsigned char* out, unsigned ch
     stats[2] = maxb;
     stats[3] = nfast;
     stats[4] = nstripe;
+    stats[5] = npair;
   }
   return g_errors;
 }

@@ -51,7 +51,7 @@ def _run(emu, H, Nx, Ny, Ks, Kt, mode=0, target=32768, nthr=8):
     counts = np.zeros(nbytes, dtype=np.uint8)
     ks = np.asarray(Ks, dtype=np.int32)
     kt = np.asarray(Kt, dtype=np.int32)
-    stats = np.zeros(5, dtype=np.uint64)
+    stats = np.zeros(6, dtype=np.uint64)
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     nerr = emu.emu_run(p(hin), p(out), p(counts), Nx, Ny, len(ks), p(ks), p(kt), es, mode,
                        target, nthr, p(stats))
@@ -110,12 +110,19 @@ def test_tiles_transpose(emu, shape, dtype):
     got, stats = _run(emu, H, Nx, Ny, Ks, Kt, 0, target)
     want = oracle.transpose(H, Nx, Ny, Ks, Kt)
     np.testing.assert_array_equal(got.view(np.uint8), want.view(np.uint8))
-    # the chunk path takes every tile whose rows and cells are at least a chunk long
-    if Ny >= 16 // H.itemsize and min(Kt) >= 16 // H.itemsize and target >= 32768:
+    E = 16 // H.itemsize
+    # the chunk path's context fits every tile whose rows and cells are at least a chunk long
+    if Ny >= E and min(Kt) >= E and target >= 32768:
         assert stats[3] == stats[0]
-    # the stripe path takes the fp16 tiles whose run stride Ks*Kt is 1 mod 4
-    if H.itemsize == 2 and Ny >= 3 and all((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt)) \
-            and target >= 32768:
+    # the pair path takes the tiles whose run stride Ks*Kt is 1 mod E (odd Ny >= E,
+    # rows longer than a chunk); the stripe path the other fp16 tiles with Ks*Kt = 1 mod 4
+    pair_ok = [(a * b) % E == 1 and Ny % 2 == 1 and Ny >= E and b > E for a, b in zip(Ks, Kt)]
+    if all(pair_ok) and target >= 32768:
+        assert stats[5] == stats[0]
+    if not any(pair_ok):
+        assert stats[5] == 0
+    if H.itemsize == 2 and Ny >= 3 and not any(pair_ok) and target >= 32768 and \
+            all((a * b) % 4 == 1 and b >= 8 for a, b in zip(Ks, Kt)):
         assert stats[4] == stats[0]
     if H.itemsize == 4:
         assert stats[4] == 0
