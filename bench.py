@@ -44,12 +44,14 @@ def _peaks():
 
 
 def _kernel_source_sha():
-    """Hash of the gather kernels' source: lfbp_device.cuh and the device part
-    of lfbp.cu (everything before its host section)."""
+    """Hash of the gather kernels' source: lfbp_device.cuh, the consumer
+    headers it includes, and the device part of lfbp.cu (everything before its
+    host section)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2003_09133_gb300", "csrc")
-    with open(os.path.join(csrc, "lfbp_device.cuh"), "rb") as fh:
-        h.update(fh.read())
+    for name in ("lfbp_device.cuh", "lfbp_stripes.cuh", "lfbp_pairs.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
     with open(os.path.join(csrc, "lfbp.cu"), "rb") as fh:
         h.update(fh.read().split(b"// ====================================================================== host")[0])
     return h.hexdigest()[:16]
@@ -469,9 +471,30 @@ def run_ours(args):
         n_e2e = max(3, min(args.steps, 20))
         t_e2e, _, _ = timed(step_e2e, n_e2e, 2)
         nbytes = sum(h.numel() * h.element_size() for h in Hs)
+
+        # the host link alone on this machine: the same bytes copied host -> device
+        # and device -> host at the same time on two streams, no map (context
+        # for the e2e number: its floor)
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def link_only():
+            cur = torch.cuda.current_stream()
+            s_in.wait_stream(cur)
+            s_out.wait_stream(cur)
+            for hi, ho, di, do in zip(hosts, host_out, dev_in, outs):
+                with torch.cuda.stream(s_in):
+                    di.copy_(hi, non_blocking=True)
+                with torch.cuda.stream(s_out):
+                    ho.copy_(do, non_blocking=True)
+            cur.wait_stream(s_in)
+            cur.wait_stream(s_out)
+
+        t_link, _, _ = timed(link_only, max(3, n_e2e // 4), 2)
         e2e = {"value": round(job_total / (t_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": round(t_e2e, 3)}
+               "ms_per_step": round(t_e2e, 3),
+               "link_only_ms": round(t_link, 3),
+               "link_only": "the same bytes copied both ways at once, no map (not timed in e2e)"}
         del hosts, host_out, dev_in
 
     peak, peak_kind = _peaks()
@@ -675,7 +698,7 @@ TABLE1 = [(89, 11, 11, 0.10), (177, 11, 11, 0.36), (287, 11, 11, 1.05), (507, 11
           (311, 31, 31, 4.74), (307, 51, 51, 11.3), (181, 95, 55, 5.9)]
 
 
-def _table1_extra(lf, world, no_tune=False, reps=5):
+def _table1_extra(lf, world, no_tune=False, reps=5, rows=None, nz=11):
     """Every PSF-array size of Table 1 (11 depths of one K; K not a multiple of
     N; the last row the non-square 95 x 55 cell), fp32, seeded uniform values:
     one batched launch per array, in the launch shape the library's autotuner
@@ -683,14 +706,15 @@ def _table1_extra(lf, world, no_tune=False, reps=5):
     0.04-10.8 GB per direction; arrays below 2 x L2 are timed with an L2 flush
     between launches."""
     import torch
-    nmax = max(nx * ny * k * k * 11 for k, nx, ny, _ in TABLE1)
+    table = [t for t in TABLE1 if rows is None or t[0] in rows]
+    nmax = max(nx * ny * k * k * nz for k, nx, ny, _ in table)
     gen = torch.Generator(device="cuda").manual_seed(7)
     Hbuf = torch.empty(nmax, dtype=torch.float32, device="cuda").uniform_(generator=gen)
     Obuf = torch.empty_like(Hbuf)
     flush = torch.empty(int(256e6) // 4, dtype=torch.float32, device="cuda")
-    rows = []
-    for k, nx, ny, paper_s in TABLE1:
-        plan = lf.Plan(nx, ny, [k] * 11, [k] * 11, torch.float32)
+    out_rows = []
+    for k, nx, ny, paper_s in table:
+        plan = lf.Plan(nx, ny, [k] * nz, [k] * nz, torch.float32)
         H, O = Hbuf[:plan.elems], Obuf[:plan.elems]
         nb = 2 * plan.elems * 4
 
@@ -711,14 +735,14 @@ def _table1_extra(lf, world, no_tune=False, reps=5):
         t_default = time_it()
         tuned = None if no_tune else lf.tune_batched([plan], [H], [O])
         t = time_it() if tuned else t_default
-        rows.append({"K": k, "Nx": nx, "Ny": ny, "Nz": 11, "elements": plan.elems,
+        out_rows.append({"K": k, "Nx": nx, "Ny": ny, "Nz": nz, "elements": plan.elems,
                      "ms": round(t, 4), "GBps": round(world * nb / (t * 1e-3) / 1e9, 1),
                      "default_shape_GBps": round(world * nb / (t_default * 1e-3) / 1e9, 1),
                      "tuned": _tuned_desc(tuned), "paper_s": paper_s})
     del Hbuf, Obuf, flush
     torch.cuda.empty_cache()
     return {"dtype": "f32", "data": "seeded uniform values (a permutation's time does not "
-                                     "depend on them)", "rows": rows}
+                                     "depend on them)", "rows": out_rows}
 
 
 def _autograd_extra(lf, timed, steps):
@@ -818,6 +842,11 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default launch shape instead of the autotuner's")
+    ap.add_argument("--table1-rows", default=None,
+                    help="with --only table1: comma-separated cut-out sizes K of the rows to time")
+    ap.add_argument("--table1-depths", type=int, default=11,
+                    help="with --only table1: depths per array (Table 1 has 11; fewer make a "
+                         "smaller case of the same shapes)")
     ap.add_argument("--only", choices=["rl", "autograd", "table1", "window"], default=None,
                     help="time only one of the extra measurements and print that (for "
                          "profiling): the RL update (Eq. 2) or the autograd step on the "
@@ -854,15 +883,18 @@ def run_only(args):
         return a.elapsed_time(b) / n, None, None
 
     if args.only == "table1":
-        res = _table1_extra(lf, 1, args.no_tune)
+        rows = None if not args.table1_rows else {int(k) for k in args.table1_rows.split(",")}
+        res = _table1_extra(lf, 1, args.no_tune, rows=rows, nz=args.table1_depths)
     elif args.only == "window":
         import lfgen
-        specs = lfgen.config_specs("highres")
+        args.workload = "highres"
+        specs = _pick_specs(args)  # every depth_stride-th depth
         s = specs[0]
         plans = [lf.Plan(s.Nx, s.Ny, s.Ks, s.Kt, torch.float32)]
         Hs = [lfgen.generate(s, device="cuda")]
         outs = [torch.empty_like(Hs[0])]
-        res = _paper_window_extra(lf, specs, Hs, outs, timed, max(3, args.steps // 4), 1)
+        res = _paper_window_extra(lf, specs, Hs, outs, timed, max(3, args.steps // 4), 1,
+                                  args.no_tune)
     else:
         fn = _rl_extra if args.only == "rl" else _autograd_extra
         res = fn(lf, timed, args.steps)
