@@ -2,7 +2,8 @@
 
 One step = H -> H' over every depth of the workload (all steps of the map:
 per-depth split, index map, flip, exchange, data movement), with the input
-resident in HBM.  The headline form is the batched persistent launch; the
+resident in HBM.  The headline form is the batched launch (one CUDA graph in
+the autotuner's form: persistent CTAs, one tile per CTA, or per-depth grids); the
 plain per-depth form is timed beside it on the same GPU.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -57,18 +58,24 @@ def _kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def _traffic_record(workload, dtype):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel is unchanged."""
+def _traffic_record(workload, dtype, kernel):
+    """DRAM bytes per step from a committed ncu summary of `kernel`, if the
+    kernels' source is unchanged since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        ent = rec.get(f"{workload}:{dtype}")
-        if ent and ent.get("source_sha") == _kernel_source_sha():
-            return ent
+        for ent in rec.values():
+            if (ent.get("workload") == workload and ent.get("dtype") == dtype and
+                    ent.get("kernel") == kernel and ent.get("source_sha") == _kernel_source_sha()):
+                return ent
     except Exception:
         pass
     return None
+
+
+# the kernel that does the work of each batched form (lfbp_tune_batched's fifth value)
+FORM_KERNEL = {0: "k_gather_persistent", 1: "k_gather_tiles", 2: "k_gather_depth"}
 
 
 class ClockSampler:
@@ -363,7 +370,7 @@ def _config(args, specs, world=1):
     import lfgen
     elems = sum(lfgen.array_elems(s) for s in specs)
     cfg = {"workload": _workload_desc(specs, args.dtype), "arrays": len(specs),
-           "elements_per_rank": elems, "form": "batched persistent (1 launch, CUDA graph)",
+           "elements_per_rank": elems, "form": "batched (1 CUDA graph launch; the autotuner's form)",
            "l2": "inputs larger than L2 (no flush)" if elems * 2 > 129e6 else
                  "L2 flushed between steps"}
     if args.scaling == "strong":
@@ -500,7 +507,8 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     achieved = step_bytes / (t_batched * 1e-3) / 1e9
     value = job_total / (t_batched * 1e-3) / 1e9
-    traffic = None if strong else _traffic_record(args.workload, _dtype_name(args, specs))
+    kernel = FORM_KERNEL[tuned[4] if tuned else 1]
+    traffic = None if strong else _traffic_record(args.workload, _dtype_name(args, specs), kernel)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_batched, 4),
@@ -510,11 +518,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "k_gather_persistent",
+                     "kernel": kernel,
                      "traffic": traffic["bytes_per_launch"] if traffic else None,
                      "algorithmic_bytes_per_launch": step_bytes},
         "pct_of_8TBps_spec": round(100 * achieved / SPEC_GBS, 2),
-        "launch_shape": _tuned_desc(tuned) or "default (3 CTAs/SM, 32 KB tiles)",
+        "launch_shape": _tuned_desc(tuned) or "default (one tile per CTA, 64 KB tiles)",
         "elements_per_s": round(job_total * step_elems / step_bytes / (t_batched * 1e-3), 1)
         if step_bytes else 0.0,
         "best_ms_per_step": round(best_batched, 4),
@@ -523,7 +531,10 @@ def run_ours(args):
                   "best_ms_per_step": round(best_plain, 4),
                   "launches_per_step": sum(p.Nz for p in plans), "kernel": "k_gather_depth"},
         "e2e": e2e,
-        "gpu_launches": args.steps if plans else 0,
+        # kernel launches of the timed steps: one per step, or one grid per depth
+        # of every array in the per-depth graph form
+        "gpu_launches": (args.steps * (sum(p.Nz for p in plans) if (tuned and tuned[4] == 2) else 1)
+                         if plans else 0),
         "clocks": clocks,
     }
     if not args.no_extra and not strong and args.workload == "highres" and args.dtype in (None, "f32"):
@@ -773,7 +784,13 @@ def _autograd_extra(lf, timed, steps):
 def _tuned_desc(t):
     if t is None:
         return None
-    return {"tile_bytes": t[0], "ctas_per_sm": t[1], "stages": t[2] or "as many as fit",
+    if t[4] in (1, 2):
+        form = ("one tile per CTA (k_gather_tiles)" if t[4] == 1 else
+                "graph of per-depth grids (k_gather_depth)")
+        return {"form": form, "tile_bytes": t[0],
+                "consumer": "pairs where eligible" if t[3] else "chunks / stripes"}
+    return {"form": "persistent (k_gather_persistent)", "tile_bytes": t[0], "ctas_per_sm": t[1],
+            "stages": t[2] or "as many as fit",
             "consumer": "pairs where eligible" if t[3] else "chunks / stripes"}
 
 

@@ -156,20 +156,27 @@ int lfbp_backproject_array_host(lfbp_plan p, const void* H_host, void* Hp_host, 
                                 void* dHp_work, void* cuda_stream);
 
 /*
- * H -> H' for n arrays at once, in one persistent launch over a ragged work
+ * H -> H' for n arrays at once, as one CUDA graph launch over a ragged work
  * list of all depths of all arrays (mixed fp32 / fp16 plans allowed).  Sec. 4
  * maps each z-plane on its own (the index relations of Eqs. 4-9 never mix
  * depths), so the depths of several arrays form one list of independent
- * pieces of work, whatever their cell and cut-out sizes.  The
- * work list, launch shape and a CUDA graph of the launch are built on the
- * first call for a given list of plans and reused while the same plans (by
- * handle) come back; pointers may change between calls.  The first call for
- * a new list of plans allocates device memory and must not be made during
- * stream capture.  plans[i], dH[i], dHp[i] as for lfbp_backproject_array;
- * no output may overlap any input or other output.  With LFBP_LOADS=lsu in
- * the environment (read at each call) the kernel's producers move the input
- * segments with 16-byte cp.async copies instead of TMA bulk copies; the
- * result is the same.
+ * pieces of work, whatever their cell and cut-out sizes.  The launch takes
+ * one of three forms (the autotuner's choice, lfbp_tune_batched; untuned:
+ * one tile per CTA):
+ *  - persistent CTAs that stream the tiles of the list through a ring of
+ *    shared-memory stages (producer warps, consumer warps);
+ *  - one grid over the whole list, one tile per CTA;
+ *  - one grid per depth of every array, all in one graph with no dependencies
+ *    between them.
+ * The work list, launch shape and graph are built on the first call for a
+ * given list of plans and reused while the same plans (by handle) come back;
+ * pointers may change between calls.  The first call for a new list of plans
+ * allocates device memory and must not be made during stream capture.
+ * plans[i], dH[i], dHp[i] as for lfbp_backproject_array; no output may
+ * overlap any input or other output.  With LFBP_LOADS=lsu in the environment
+ * (read at each call) the persistent kernel's producers move the input
+ * segments with 16-byte cp.async copies instead of TMA bulk copies, and the
+ * persistent form is used; the result is the same.
  */
 int lfbp_backproject_batched(int n, const lfbp_plan* plans, const void* const* dH,
                              void* const* dHp, void* cuda_stream);
@@ -211,18 +218,23 @@ int lfbp_backproject_batched_noalloc(int n, const lfbp_plan* plans, const void* 
 
 /*
  * Autotuner for lfbp_backproject_batched: times a small grid of launch shapes
- * (shared-memory bytes per tile in {12, 16, 24, 32, 40, 48, 64} KiB x
- * persistent CTAs per SM in {1, 2, 3, 4} x the pair consumer on or off) on
+ * (persistent CTAs: shared-memory bytes per tile in {12, 16, 24, 32, 40, 48,
+ * 64} KiB x persistent CTAs per SM in {1, 2, 3, 4}; one tile per CTA, and a
+ * graph of one grid per depth of every array: tile bytes in {24, 32, 40, 48,
+ * 64} KiB; each with the pair consumer on or off) on
  * the given buffers with CUDA events (reps timed launches
  * each, after one warm-up) and keeps the fastest for later batched calls with
  * the same plans (by handle).  Writes H' into dHp as a side effect and
  * synchronises the stream.  If the environment variable LFBP_TUNE_CACHE names
  * a file, the choice is appended there, keyed by device name and array
  * shapes, and later processes take it from there without timing.  tuned
- * (may be NULL, else 4 ints) receives {tile bytes, CTAs per SM, stages (0 =
- * as many as fit), pair consumer (1 = on)}.  Arguments otherwise as for
- * lfbp_backproject_batched.  Without tuning, LFBP_PAIRS=0 in the environment
- * turns the pair consumer off (it is on by default; the result is the same).
+ * (may be NULL, else 5 ints) receives {tile bytes, CTAs per SM (0 unless
+ * persistent), stages (0 = as many as fit), pair consumer (1 = on), form (0 =
+ * persistent CTAs, 1 = one tile per CTA, 2 = per-depth grids in one graph)}.
+ * Arguments otherwise as for lfbp_backproject_batched.  Without tuning,
+ * LFBP_PAIRS=0 turns the pair consumer off and LFBP_FORM selects the form
+ * (defaults: on, one tile per CTA with 64 KiB tiles; the result is the
+ * same).
  */
 int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void* const* dHp,
                       void* cuda_stream, int reps, int* tuned);

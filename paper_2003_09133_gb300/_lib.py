@@ -248,8 +248,9 @@ def tune_batched(plans: Sequence[Plan], Hs: Sequence[torch.Tensor],
                  outs: Sequence[torch.Tensor] = None, reps: int = 3, stream=None):
     """Pick the fastest batched launch shape for these plans (``lfbp_tune_batched``).
 
-    Returns (tile_bytes, ctas_per_sm, stages, pair_consumer); later
-    ``backproject_batched`` calls with the same plans use it.
+    Returns (tile_bytes, ctas_per_sm, stages, pair_consumer, form), form 0 for
+    persistent CTAs and 1 for one tile per CTA; later ``backproject_batched``
+    calls with the same plans use it.
     """
     n = len(plans)
     if outs is None:
@@ -261,7 +262,7 @@ def tune_batched(plans: Sequence[Plan], Hs: Sequence[torch.Tensor],
     hp = (_P * max(1, n))(*[p.handle for p in plans])
     ip = (_P * max(1, n))(*[h.data_ptr() for h in Hs])
     op = (_P * max(1, n))(*[o.data_ptr() for o in outs])
-    res = (ctypes.c_int * 4)()
+    res = (ctypes.c_int * 5)()
     with torch.cuda.device(Hs[0].device):
         _check(lib.lfbp_tune_batched(n, ctypes.cast(hp, _P), ctypes.cast(ip, _P), ctypes.cast(op, _P),
                                      _stream_ptr(stream), int(reps), ctypes.cast(res, _P)),

@@ -127,6 +127,60 @@ __global__ void __launch_bounds__(kPlainThreads)
   gather_tile_ctx(*ctx, warp, kPlainThreads / 32, lane);
 }
 
+// ------------------------------------------------------------------ tiles --
+// The batched form with one tile of the work list per CTA: grid = ntiles,
+// block = kPlainThreads, the body of k_gather_depth (every warp issues a share
+// of the tile's copies, the context is built while they are in flight, then
+// every warp gathers).  The hardware block scheduler overlaps the CTAs of an
+// SM that wait for their copies with those that gather.
+// smem: [stage: stage_bytes][mbarrier][TileCtx][row-base table]
+__global__ void __launch_bounds__(kPlainThreads)
+    k_gather_tiles(const __grid_constant__ BatchPtrs ptrs, const TileDesc* __restrict__ tiles,
+                   const TileShape* __restrict__ shapes, int stage_bytes) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* stage = smem;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + stage_bytes);
+  TileCtx* ctx = reinterpret_cast<TileCtx*>(smem + stage_bytes + 16);
+  int* tab = reinterpret_cast<int*>(smem + stage_bytes + 16 + kCtxBytes);
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (dynamic_smem_size() < (uint32_t)plain_smem_bytes(stage_bytes)) {
+    if (tid == 0) set_status(kStatusBadLaunch);
+    return;
+  }
+  const TileDesc td = tiles[blockIdx.x];
+  const unsigned char* in_arr = ptrs.in[td.arr];
+  const unsigned char* in_depth = in_arr + td.off_bytes;
+  const unsigned char* safe_end = in_arr + (ptrs.in_bytes[td.arr] & ~15ull);
+  unsigned char* out_depth = ptrs.out[td.arr] + td.off_bytes;
+
+  const uint32_t b = smem_addr(bar);
+  constexpr int kWarps = kPlainThreads / 32;
+  if (tid == 0) {
+    abort_flag = 0;
+    mbar_init(b, kWarps);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  issue_tile_loads(td, in_depth, safe_end, stage, b, lane, warp, kWarps);
+  __syncwarp();
+  if (lane == 0) mbar_arrive(b);
+  {
+    const TileShape* shp = shapes + td.shape;
+    if (warp == 0) copy_shape(*ctx, shp, lane);
+    if (warp >= 1 && warp <= 4 && lane == 0)
+      make_ctx_tile(*ctx, td, shp, stage, in_depth, out_depth, tab, warp - 1);
+  }
+  __syncthreads();
+  if (!mbar_wait_bounded(b, 0, &abort_flag, kWaitLimitNs)) {
+    set_status(kStatusTimeout);
+    abort_flag = 1;
+    mbar_wait_bounded(b, 0, nullptr, kWaitLimitNs);
+    return;
+  }
+  gather_tile_ctx(*ctx, warp, kWarps, lane);
+}
+
 // ------------------------------------------------------------- persistent --
 // grid = SMs * ctas_per_sm; block = kPersistentThreads.  CTA c takes tiles
 // c, c + grid, c + 2 grid, ... (consecutive tiles are neighbours in memory, so
@@ -350,11 +404,19 @@ struct Tuning {
   int ctas_per_sm;  // persistent CTAs per SM
   int stages;       // stages per persistent CTA (0 = as many as fit)
   int pairs;        // 1: tiles that can take the pair consumer do (lfbp_pairs.cuh)
+  int form;         // 0: persistent CTAs (k_gather_persistent); 1: one tile per CTA (k_gather_tiles)
 };
 
+// Untuned launch shape: one tile per CTA with 64 KB tiles (measured the most
+// even across the workloads: highres fp32 5696, fp16 5227, mid 5821, Table 1
+// N = 51 5215, 95 x 55 5777 GB/s; persistent CTAs with 32 KB tiles, the
+// default before, 5577 / 4615 / 5185 / 4095 / 3809).  The graph of per-depth
+// grids is faster on few large depths (highres fp32 6296) but pays a launch
+// per node on many small ones (mid 2929): the autotuner chooses per batch.
 Tuning default_tuning() {
   Tuning t;
-  t.tile_bytes = env_int("LFBP_TILE_BYTES", 32768);
+  t.form = std::min(2, std::max(0, env_int("LFBP_FORM", 1)));
+  t.tile_bytes = env_int("LFBP_TILE_BYTES", t.form == 0 ? 32768 : 65536);
   t.ctas_per_sm = env_int("LFBP_CTAS_PER_SM", 3);
   t.stages = env_int("LFBP_STAGES", 0);
   t.pairs = env_int("LFBP_PAIRS", 1) != 0;
@@ -440,6 +502,40 @@ int plain_tile_bytes() {
   return t < 1024 ? 1024 : (t > 65536 ? 65536 : t);
 }
 
+// Helper streams of the plain form, per device: consecutive depth launches go
+// round-robin to kPlainStreams streams forked from the caller's stream and
+// joined back into it, so that a depth too small to fill the GPU runs beside
+// its neighbours (each depth is still one launch).
+constexpr int kPlainStreams = 4;
+struct PlainStreams {
+  int dev = -1;
+  std::mutex mu;  // held from the fork to the join of one call
+  cudaStream_t s[kPlainStreams] = {};
+  cudaEvent_t fork = nullptr, join[kPlainStreams] = {};
+};
+std::vector<PlainStreams*> g_plain_streams;  // guarded by g_mu; live as long as the process
+
+PlainStreams* plain_streams() {
+  if (env_int("LFBP_PLAIN_STREAMS", 1) == 0) return nullptr;  // 0: the caller's stream only
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (PlainStreams* s : g_plain_streams)
+    if (s->dev == dev) return s;
+  PlainStreams* s = new PlainStreams();
+  s->dev = dev;
+  bool ok = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int i = 0; ok && i < kPlainStreams; ++i)
+    ok = cudaStreamCreateWithFlags(&s->s[i], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&s->join[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {  // a partly created set is dropped; launches stay on the caller's stream
+    cudaGetLastError();
+    return nullptr;
+  }
+  g_plain_streams.push_back(s);
+  return s;
+}
+
 int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int mode, int z0,
                  int z1, cudaStream_t st) {
   const size_t arr_bytes = p->off.back() * (size_t)p->es;
@@ -449,7 +545,17 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
   for (int z = z0; z < z1; ++z) max_smem = std::max(max_smem, tl[z].max_tile_bytes);
   int rc = ensure_smem_attr((const void*)k_gather_depth, plain_smem_bytes((max_smem + 15) & ~15));
   if (rc) return rc;
+  PlainStreams* ps = z1 - z0 > 1 ? plain_streams() : nullptr;
+  std::unique_lock<std::mutex> ps_lock;
+  if (ps) {
+    ps_lock = std::unique_lock<std::mutex>(ps->mu);
+    cudaError_t e = cudaEventRecord(ps->fork, st);
+    for (int i = 0; e == cudaSuccess && i < kPlainStreams; ++i)
+      e = cudaStreamWaitEvent(ps->s[i], ps->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "plain-form fork");
+  }
   for (int z = z0; z < z1; ++z) {
+    cudaStream_t sz = ps ? ps->s[(z - z0) % kPlainStreams] : st;
     const DepthTiling& d = tl[z];
     // the pair consumer measured faster for fp16 plain launches, slower for fp32
     const TileDesc base = depth_desc(p, z, d, mode, 0, p->es == 2);
@@ -457,10 +563,18 @@ int launch_plain(lfbp_plan p, const unsigned char* inb, unsigned char* outb, int
     depth_shapes(p, z, d, base, ds.s);
     dim3 grid(d.nV, p->Nx, d.nU);
     const int smem = (d.max_tile_bytes + 15) & ~15;
-    k_gather_depth<<<grid, kPlainThreads, plain_smem_bytes(smem), st>>>(
+    k_gather_depth<<<grid, kPlainThreads, plain_smem_bytes(smem), sz>>>(
         base, ds, inb + base.off_bytes, safe_end, outb + base.off_bytes, d.J, d.V, smem);
   }
   cudaError_t e = cudaGetLastError();
+  if (ps) {  // join: later work on st waits for every depth
+    const int used = std::min(kPlainStreams, z1 - z0);
+    for (int i = 0; i < used; ++i) {
+      cudaError_t e2 = cudaEventRecord(ps->join[i], ps->s[i]);
+      if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, ps->join[i], 0);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
   if (e != cudaSuccess) return cuda_fail(e, "k_gather_depth launch");
   return LFBP_OK;
 }
@@ -652,11 +766,33 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
 }
 
 // ---------------------------------------------------------------- batched --
+// One depth of one array in the form-2 graph (k_gather_depth's arguments
+// apart from the pointers, which come from the batch's pointers at launch).
+struct DepthNode {
+  TileDesc base;    // arr, off_bytes, sizes, pitch, flags
+  DepthShapes ds;
+  dim3 grid;
+  int J = 0, V = 0, stage = 0;
+};
+struct DepthNodeArgs {  // storage for one node's kernel arguments
+  TileDesc base;
+  DepthShapes ds;
+  const unsigned char* in = nullptr;
+  const unsigned char* safe_end = nullptr;
+  unsigned char* out = nullptr;
+  int J = 0, V = 0, stage = 0;
+  void* args[8];
+};
+
 struct BatchState {
   int dev = -1;
   bool lsu = false;  // producers move the segments with cp.async (k_gather_persistent<false, true>)
+  int form = 0;      // 0: k_gather_persistent; 1: k_gather_tiles (one tile per CTA);
+                     // 2: a graph of k_gather_depth grids, one per depth of every array
+  std::vector<DepthNode> dnodes;         // form 2: the depths
+  std::vector<cudaGraphNode_t> knodes;   // form 2: their graph nodes
   std::vector<unsigned long long> uids;
-  Tuning tuning{0, 0, 0, 0};
+  Tuning tuning{0, 0, 0, 0, 0};
   int ntiles = 0;
   int stage_bytes = 0, nstages = 0, grid = 0, smem = 0;
   TileDesc* d_tiles = nullptr;    // work list, followed in the same allocation by
@@ -745,11 +881,106 @@ bool env_lsu() {
   return s && !std::strcmp(s, "lsu");
 }
 
+// The kernel of a batch, and its graph node's launch parameters (args: room
+// for 6 pointers, kept alive by the caller until the node is set).
+const void* batch_fn(const BatchState& bs) {
+  return bs.form == 1 ? (const void*)k_gather_tiles : persistent_fn(bs.lsu);
+}
+void batch_node_params(BatchState& bs, void** args, cudaKernelNodeParams* kp) {
+  std::memset(kp, 0, sizeof(*kp));
+  args[0] = &bs.ptrs;
+  args[1] = &bs.d_tiles;
+  args[2] = &bs.d_shapes;
+  if (bs.form == 1) {
+    args[3] = &bs.stage_bytes;
+    kp->blockDim = dim3(kPlainThreads);
+  } else {
+    args[3] = &bs.ntiles;
+    args[4] = &bs.stage_bytes;
+    args[5] = &bs.nstages;
+    kp->blockDim = dim3(kPersistentThreads);
+  }
+  kp->func = (void*)batch_fn(bs);
+  kp->gridDim = dim3(bs.grid);
+  kp->sharedMemBytes = bs.smem;
+  kp->kernelParams = args;
+}
+
+// Sets the launch parameters of a depth node (form 2) for the batch's
+// pointers: the k_gather_depth arguments of one depth of one array.
+void depth_node_params(const BatchState& bs, const DepthNode& dn, DepthNodeArgs& a,
+                       cudaKernelNodeParams* kp) {
+  a.base = dn.base;
+  a.ds = dn.ds;
+  const unsigned char* in_arr = bs.ptrs.in[dn.base.arr];
+  a.in = in_arr ? in_arr + dn.base.off_bytes : nullptr;
+  a.safe_end = in_arr ? in_arr + (bs.ptrs.in_bytes[dn.base.arr] & ~15ull) : nullptr;
+  a.out = bs.ptrs.out[dn.base.arr] ? bs.ptrs.out[dn.base.arr] + dn.base.off_bytes : nullptr;
+  a.J = dn.J;
+  a.V = dn.V;
+  a.stage = dn.stage;
+  a.args[0] = &a.base;
+  a.args[1] = &a.ds;
+  a.args[2] = &a.in;
+  a.args[3] = &a.safe_end;
+  a.args[4] = &a.out;
+  a.args[5] = &a.J;
+  a.args[6] = &a.V;
+  a.args[7] = &a.stage;
+  std::memset(kp, 0, sizeof(*kp));
+  kp->func = (void*)k_gather_depth;
+  kp->gridDim = dn.grid;
+  kp->blockDim = dim3(kPlainThreads);
+  kp->sharedMemBytes = plain_smem_bytes(dn.stage);
+  kp->kernelParams = a.args;
+}
+
 int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu) {
   int sms = 0, optin = 0, dev = 0;
   int rc = device_props(&dev, &sms, &optin);
   if (rc) return rc;
   bs.dev = dev;
+  bs.form = tu.form;
+  cudaError_t e;
+  if (tu.form == 2) {
+    // one graph node per depth of every array: k_gather_depth grids with no
+    // dependencies between them, so that the GPU runs them side by side
+    int max_smem = 0;
+    for (int i = 0; i < n; ++i) {
+      lfbp_plan p = plans[i];
+      const std::vector<DepthTiling>& tl = plan_tiling(p, tu.tile_bytes);
+      for (int z = 0; z < p->Nz; ++z) {
+        if (p->off[z + 1] == p->off[z]) continue;
+        const DepthTiling& dt = tl[z];
+        DepthNode dn;
+        dn.base = depth_desc(p, z, dt, (int)p->mode, i, tu.pairs);
+        depth_shapes(p, z, dt, dn.base, dn.ds.s);
+        dn.grid = dim3(dt.nV, p->Nx, dt.nU);
+        dn.J = dt.J;
+        dn.V = dt.V;
+        dn.stage = (dt.max_tile_bytes + 15) & ~15;
+        max_smem = std::max(max_smem, plain_smem_bytes(dn.stage));
+        bs.ntiles += dt.nV * p->Nx * dt.nU;
+        bs.dnodes.push_back(dn);
+      }
+    }
+    if (max_smem > optin) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
+    if ((rc = ensure_smem_attr((const void*)k_gather_depth, max_smem))) return rc;
+    if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
+    std::memset(&bs.ptrs, 0, sizeof(bs.ptrs));
+    bs.knodes.resize(bs.dnodes.size());
+    for (size_t k = 0; k < bs.dnodes.size(); ++k) {
+      DepthNodeArgs a;
+      cudaKernelNodeParams kp;
+      depth_node_params(bs, bs.dnodes[k], a, &kp);
+      if ((e = cudaGraphAddKernelNode(&bs.knodes[k], bs.graph, nullptr, 0, &kp)) != cudaSuccess)
+        return cuda_fail(e, "cudaGraphAddKernelNode");
+    }
+    if (fault_mode() == kFaultGraph) return fail(LFBP_ERR_CUDA, "injected failure (LFBP_FAULT=graph)");
+    if ((e = cudaGraphInstantiate(&bs.exec, bs.graph, 0)) != cudaSuccess)
+      return cuda_fail(e, "cudaGraphInstantiate");
+    return LFBP_OK;
+  }
   std::vector<TileDesc> tiles;
   std::vector<TileShape> shapes;
   int max_tile = 0;
@@ -757,16 +988,23 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
   if (shapes.size() > 65536) return fail(LFBP_ERR_BAD_SHAPE, "more than 16384 depths in one batch");
   bs.ntiles = (int)tiles.size();
   bs.stage_bytes = (max_tile + 127) & ~127;
-  const int per_cta_budget = std::min(optin, (227 * 1024) / tu.ctas_per_sm - 1024);
-  const int per_stage = bs.stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
-  int nst = per_cta_budget / per_stage;
-  if (tu.stages > 0) nst = std::min(nst, tu.stages);
-  if (nst < 2) nst = std::min(2, optin / per_stage);
-  if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
-  bs.nstages = nst;
-  bs.smem = persistent_smem_bytes(bs.stage_bytes, nst);
-  bs.grid = std::max(1, std::min(sms * tu.ctas_per_sm, bs.ntiles));
-  cudaError_t e;
+  if (tu.form == 1) {  // one tile per CTA: the whole list is the grid
+    bs.nstages = 1;
+    bs.smem = plain_smem_bytes(bs.stage_bytes);
+    if (bs.smem > optin) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
+    bs.grid = std::max(1, bs.ntiles);
+  } else {  // persistent CTAs: as many stages as fit next to the others on an SM
+    const int cps = std::max(1, tu.ctas_per_sm);
+    const int per_cta_budget = std::min(optin, (227 * 1024) / cps - 1024);
+    const int per_stage = bs.stage_bytes + kInfoBytes + 16;  // as persistent_smem_bytes
+    int nst = per_cta_budget / per_stage;
+    if (tu.stages > 0) nst = std::min(nst, tu.stages);
+    if (nst < 2) nst = std::min(2, optin / per_stage);
+    if (nst < 1) return fail(LFBP_ERR_BAD_SHAPE, "tile does not fit in shared memory");
+    bs.nstages = nst;
+    bs.smem = persistent_smem_bytes(bs.stage_bytes, nst);
+    bs.grid = std::max(1, std::min(sms * cps, bs.ntiles));
+  }
   if (bs.ntiles) {
     if (fault_mode() == kFaultAlloc) return fail(LFBP_ERR_NOMEM, "injected failure (LFBP_FAULT=alloc)");
     const size_t tb = sizeof(TileDesc) * tiles.size(), sb = sizeof(TileShape) * shapes.size();
@@ -778,24 +1016,45 @@ int build_batch(BatchState& bs, int n, const lfbp_plan* plans, const Tuning& tu)
     if ((e = cudaMemcpy(bs.d_shapes, shapes.data(), sb, cudaMemcpyHostToDevice)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpy(shapes)");
   }
-  if ((rc = ensure_smem_attr(persistent_fn(bs.lsu), bs.smem))) return rc;
+  if ((rc = ensure_smem_attr(batch_fn(bs), bs.smem))) return rc;
   // a one-node graph: relaunching it costs one cudaGraphLaunch; pointer
   // changes are patched into the node's parameters
   if ((e = cudaGraphCreate(&bs.graph, 0)) != cudaSuccess) return cuda_fail(e, "cudaGraphCreate");
   std::memset(&bs.ptrs, 0, sizeof(bs.ptrs));
-  void* args[] = {&bs.ptrs, &bs.d_tiles, &bs.d_shapes, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
+  void* args[6];
   cudaKernelNodeParams kp;
-  std::memset(&kp, 0, sizeof(kp));
-  kp.func = (void*)persistent_fn(bs.lsu);
-  kp.gridDim = dim3(bs.grid);
-  kp.blockDim = dim3(kPersistentThreads);
-  kp.sharedMemBytes = bs.smem;
-  kp.kernelParams = args;
+  batch_node_params(bs, args, &kp);
   if ((e = cudaGraphAddKernelNode(&bs.knode, bs.graph, nullptr, 0, &kp)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphAddKernelNode");
   if (fault_mode() == kFaultGraph) return fail(LFBP_ERR_CUDA, "injected failure (LFBP_FAULT=graph)");
   if ((e = cudaGraphInstantiate(&bs.exec, bs.graph, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaGraphInstantiate");
+  return LFBP_OK;
+}
+
+// Launches a built batch for the pointers np on st: patches the graph's
+// node parameters when the pointers changed, then launches the graph.
+int launch_batch(BatchState& bs, const BatchPtrs& np, cudaStream_t st) {
+  cudaError_t e;
+  if (std::memcmp(&np, &bs.ptrs, sizeof(np)) != 0) {
+    bs.ptrs = np;
+    if (bs.form == 2) {
+      for (size_t k = 0; k < bs.dnodes.size(); ++k) {
+        DepthNodeArgs a;
+        cudaKernelNodeParams kp;
+        depth_node_params(bs, bs.dnodes[k], a, &kp);
+        if ((e = cudaGraphExecKernelNodeSetParams(bs.exec, bs.knodes[k], &kp)) != cudaSuccess)
+          return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
+      }
+    } else {
+      void* args[6];
+      cudaKernelNodeParams kp;
+      batch_node_params(bs, args, &kp);
+      if ((e = cudaGraphExecKernelNodeSetParams(bs.exec, bs.knode, &kp)) != cudaSuccess)
+        return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
+    }
+  }
+  if ((e = cudaGraphLaunch(bs.exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
   return LFBP_OK;
 }
 
@@ -823,12 +1082,14 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   std::lock_guard<std::mutex> lk(g_mu);
-  const Tuning want = tuning_for(dev, n, plans);
+  Tuning want = tuning_for(dev, n, plans);
+  if (fault_mode() == kFaultStall || lsu) want.form = 0;  // both need the persistent kernel
   BatchState* bs = nullptr;
   for (auto& b : g_batches) {
     if (b->dev != dev || b->lsu != lsu || !same_uids(b->uids, n, plans)) continue;
     if (b->tuning.tile_bytes != want.tile_bytes || b->tuning.ctas_per_sm != want.ctas_per_sm ||
-        b->tuning.stages != want.stages || b->tuning.pairs != want.pairs)
+        b->tuning.stages != want.stages || b->tuning.pairs != want.pairs ||
+        b->tuning.form != want.form)
       continue;
     bs = b.get();
     break;
@@ -860,21 +1121,8 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     np.out[i] = (unsigned char*)out[i];
     np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
   }
-  if (std::memcmp(&np, &bs->ptrs, sizeof(np)) != 0) {
-    bs->ptrs = np;
-    void* args[] = {&bs->ptrs, &bs->d_tiles, &bs->d_shapes, &bs->ntiles, &bs->stage_bytes,
-                    &bs->nstages};
-    cudaKernelNodeParams kp;
-    std::memset(&kp, 0, sizeof(kp));
-    kp.func = (void*)persistent_fn(bs->lsu);
-    kp.gridDim = dim3(bs->grid);
-    kp.blockDim = dim3(kPersistentThreads);
-    kp.sharedMemBytes = bs->smem;
-    kp.kernelParams = args;
-    if ((e = cudaGraphExecKernelNodeSetParams(bs->exec, bs->knode, &kp)) != cudaSuccess)
-      return cuda_fail(e, "cudaGraphExecKernelNodeSetParams");
-  }
   if (fault_mode() == kFaultStall) {  // the injected kernel, launched directly
+    bs->ptrs = np;
     int rc = ensure_smem_attr((const void*)k_gather_persistent<true>, bs->smem);
     if (rc) return rc;
     k_gather_persistent<true><<<bs->grid, kPersistentThreads, bs->smem, st>>>(
@@ -882,8 +1130,7 @@ int run_batched(int n, const lfbp_plan* plans, const void* const* in, void* cons
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "k_gather_persistent launch");
     return LFBP_OK;
   }
-  if ((e = cudaGraphLaunch(bs->exec, st)) != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  return LFBP_OK;
+  return launch_batch(*bs, np, st);
 }
 
 // ------------------------------------------------------- no-allocation path --
@@ -968,7 +1215,10 @@ int run_batched_noalloc(int n, const lfbp_plan* plans, const void* const* in, vo
   if (batch_empty(n, plans)) return LFBP_OK;  // nothing to map: no CUDA call at all
   // the size check comes before any CUDA call, so a batch too large for the
   // array is refused without touching the device or the buffers
+  // the persistent kernel, in its own default shape (32 KB tiles unless set)
   Tuning tu = default_tuning();
+  tu.form = 0;
+  tu.tile_bytes = std::min(65536, std::max(1024, env_int("LFBP_TILE_BYTES", 32768)));
   long long need = 0;
   noalloc_target(n, plans, tu, &tu.tile_bytes, &need);
   if (need > kNoAllocMaxTiles) {
@@ -1080,10 +1330,10 @@ bool cache_lookup(const std::string& sig, Tuning* t) {
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
   char key[4096];
-  Tuning x{0, 0, 0, 1};
+  Tuning x{0, 0, 0, 1, 0};
   bool found = false;
-  while (std::fscanf(f, "%4095s %d %d %d %d", key, &x.tile_bytes, &x.ctas_per_sm, &x.stages,
-                     &x.pairs) == 5)
+  while (std::fscanf(f, "%4095s %d %d %d %d %d", key, &x.tile_bytes, &x.ctas_per_sm, &x.stages,
+                     &x.pairs, &x.form) == 6)
     if (sig == key) {
       *t = x;
       found = true;
@@ -1097,8 +1347,8 @@ void cache_store(const std::string& sig, const Tuning& t) {
   if (!path || !*path || sig.size() > 4000) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %d %d\n", sig.c_str(), t.tile_bytes, t.ctas_per_sm, t.stages,
-               t.pairs);
+  std::fprintf(f, "%s %d %d %d %d %d\n", sig.c_str(), t.tile_bytes, t.ctas_per_sm, t.stages,
+               t.pairs, t.form);
   std::fclose(f);
 }
 
@@ -1125,21 +1375,30 @@ int tune_batched(int n, const lfbp_plan* plans, const void* const* in, void* con
       np.in_bytes[i] = plans[i]->off.back() * plans[i]->es;
     }
     int rc = LFBP_OK;
-    for (int pr = 1; pr >= 0; --pr)
-    for (int tb : tiles)
-      for (int cp : ctas) {
-        Tuning t{tb, cp, 0, pr};
+    // the candidates: persistent CTAs (tile size x CTAs per SM) and one tile
+    // per CTA (tile size), each with the pair consumer on and off
+    std::vector<Tuning> cands;
+    for (int pr = 1; pr >= 0; --pr) {
+      for (int tb : tiles)
+        for (int cp : ctas) cands.push_back(Tuning{tb, cp, 0, pr, 0});
+      if (!lsu)
+        for (int tb : tiles)
+          if (tb >= 24576)
+            for (int form = 1; form <= 2; ++form) cands.push_back(Tuning{tb, 0, 0, pr, form});
+    }
+    for (const Tuning& t : cands) {
         BatchState bs;
         bs.lsu = lsu;
-        if (build_batch(bs, n, plans, t) != LFBP_OK || bs.nstages < 2) continue;
+        if (build_batch(bs, n, plans, t) != LFBP_OK || (t.form == 0 && bs.nstages < 2)) {
+          cudaGetLastError();
+          continue;
+        }
         if (bs.ntiles == 0) continue;
-        const int smem = bs.smem;
         for (int r = 0; r <= reps; ++r) {
           if (r == 1) cudaEventRecord(a, st);
-          void* args[] = {&np, &bs.d_tiles, &bs.d_shapes, &bs.ntiles, &bs.stage_bytes, &bs.nstages};
-          cudaLaunchKernel(persistent_fn(bs.lsu), dim3(bs.grid), dim3(kPersistentThreads), args,
-                           (size_t)smem, st);
+          if ((rc = launch_batch(bs, np, st)) != LFBP_OK) break;
         }
+        if (rc) break;
         cudaEventRecord(b, st);
         if ((e = cudaEventSynchronize(b)) != cudaSuccess) {
           rc = cuda_fail(e, "tuning launch");
@@ -1337,7 +1596,7 @@ int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void
   int rc = run_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, -1);  // validates the arguments
   if (rc) return rc;
   if (n == 0) return LFBP_OK;
-  Tuning t{0, 0, 0, 0};
+  Tuning t{0, 0, 0, 0, 0};
   rc = tune_batched(n, plans, dH, dHp, (cudaStream_t)cuda_stream, reps < 1 ? 3 : reps, &t);
   if (rc) return rc;
   if (tuned) {
@@ -1345,6 +1604,7 @@ int lfbp_tune_batched(int n, const lfbp_plan* plans, const void* const* dH, void
     tuned[1] = t.ctas_per_sm;
     tuned[2] = t.stages;
     tuned[3] = t.pairs;
+    tuned[4] = t.form;
   }
   return LFBP_OK;
 }

@@ -1169,6 +1169,36 @@ __device__ __forceinline__ bool chunk_keep(const TileCtx& c, const ChunkAddr& s,
          (unsigned)(q + vl - c.m1_q0) <= (unsigned)c.Kt1 && (!EVEN || vl < c.vlim);
 }
 
+// The same test for all E elements of a chunk at once, as a bit mask (bit k:
+// element k kept).  Along a chunk the row is j (k < kx) or j + 1, and the
+// column tests of Eqs. 4-9's loop ranges keep a contiguous range of k in each
+// row, so the mask is at most two bit ranges.
+__device__ __forceinline__ uint32_t bit_range(int lo, int hi) {
+  return lo > hi ? 0u : (2u << hi) - (1u << lo);  // bits lo..hi, 0 <= lo, hi < 31
+}
+template <bool ONEROW, bool EVEN, int E>
+__device__ __forceinline__ uint32_t chunk_keep_mask(const TileCtx& c, const ChunkAddr& s, int q) {
+  const int kx = ONEROW ? E : (s.kx < E ? s.kx : E);  // first element of row j + 1
+  // row j: columns vl + k, kept for q + vl + k - m1_q0 in [0, Kt1] (and vl + k < vlim)
+  uint32_t m = 0;
+  if ((unsigned)(s.j - c.m1_j0) <= (unsigned)c.m1_jw) {
+    int lo = c.m1_q0 - q - s.vl, hi = lo + c.Kt1;
+    if (EVEN && c.vlim - 1 - s.vl < hi) hi = c.vlim - 1 - s.vl;
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > kx - 1 ? kx - 1 : hi;
+    m = bit_range(lo, hi);
+  }
+  // row j + 1: columns k - kx
+  if (!ONEROW && kx < E && (unsigned)(s.j + 1 - c.m1_j0) <= (unsigned)c.m1_jw) {
+    int lo = kx + c.m1_q0 - q, hi = lo + c.Kt1;
+    if (EVEN && kx + c.vlim - 1 < hi) hi = kx + c.vlim - 1;
+    lo = lo < kx ? kx : lo;
+    hi = hi > E - 1 ? E - 1 : hi;
+    m |= bit_range(lo, hi);
+  }
+  return m;
+}
+
 // MASK: 0 none (transpose mode), 1 the paper window on an odd cut-out, 2 the
 // paper window on an even cut-out.
 template <class T, int MASK, bool ONEROW>
@@ -1231,9 +1261,11 @@ __device__ __forceinline__ void gather_chunks(const TileCtx& c, int w, int nwarp
     const ChunkAddr s = chunk_addr<ES, ONEROW>(c, q, e);
     if (whole) {
       T v[EPL];
+      const uint32_t keep = MASK ? chunk_keep_mask<ONEROW, MASK == 2, EPL>(c, s, q) : 0u;
       static_for<0, EPL>([&](auto kc) {
         constexpr int k = decltype(kc)::value;
-        v[k] = masked<T, MASK, ONEROW>(c, s, q, k, smem_load_at<T>(c, chunk_elem_c<MASK, ONEROW>(c, s, k)));
+        const T x = smem_load_at<T>(c, chunk_elem_c<MASK, ONEROW>(c, s, k));
+        v[k] = (!MASK || ((keep >> k) & 1u)) ? x : (T)0;
       });
       store_out16(c, dst, pack16(v));
     } else {

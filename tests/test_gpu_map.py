@@ -278,24 +278,27 @@ def test_tuner_then_batched(lf, tmp_path, monkeypatch):
     shapes = [(5, 5, [15, 25], [15, 25], torch.float32), (19, 19, [57, 95], [57, 95], torch.float16)]
     plans = [lf.Plan(a, b, c, d, t) for a, b, c, d, t in shapes]
     Hs = [_random_bits(p.elems, p.dtype, 40 + i) for i, p in enumerate(plans)]
-    tb, cps, st, pairs = lf.tune_batched(plans, Hs, reps=1)
-    assert tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536) and cps in (1, 2, 3, 4)
-    assert pairs in (0, 1)
+    tb, cps, st, pairs, form = lf.tune_batched(plans, Hs, reps=1)
+    assert tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536)
+    assert pairs in (0, 1) and form in (0, 1, 2) and (cps in (1, 2, 3, 4) if form == 0 else cps == 0)
     assert (tmp_path / "tune.txt").read_text().strip()
     for rep in range(2):
         outs = lf.backproject_batched(plans, Hs)
         for p, H, o in zip(plans, Hs, outs):
             _assert_same_bits(o, oracle.transpose(H.cpu().numpy(), p.Nx, p.Ny, p.Ks, p.Kt), "tuned")
     # a second process-level tune reads the cache instead of timing
-    assert lf.tune_batched(plans, Hs, reps=1) == (tb, cps, st, pairs)
+    assert lf.tune_batched(plans, Hs, reps=1) == (tb, cps, st, pairs, form)
     lf.sync_status()
 
 
+@pytest.mark.parametrize("form", ["0", "1", "2"])
 @pytest.mark.parametrize("pairs", ["1", "0"])
-def test_random_bits_batched_pair_consumer_on_off(lf, pairs, monkeypatch):
-    """The batched form with the pair consumer switched on and off (LFBP_PAIRS,
-    the autotuner's fourth dimension): the same bits either way."""
+def test_random_bits_batched_pair_consumer_on_off(lf, pairs, form, monkeypatch):
+    """The batched form with the pair consumer switched on and off (LFBP_PAIRS)
+    and as persistent CTAs, one tile per CTA, or a graph of per-depth grids
+    (LFBP_FORM), the autotuner's last two dimensions: the same bits either way."""
     monkeypatch.setenv("LFBP_PAIRS", pairs)
+    monkeypatch.setenv("LFBP_FORM", form)
     for Nx, Ny, Ks, Kt in SHAPES:
         for dtype in (torch.float32, torch.float16):
             plan = lf.Plan(Nx, Ny, Ks, Kt, dtype)
