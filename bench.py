@@ -859,6 +859,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the default launch shape instead of the autotuner's")
+    ap.add_argument("--form", choices=["0", "1", "2"], default=None,
+                    help="with --no-tune: the batched form (0 persistent CTAs, 1 one tile per "
+                         "CTA, 2 per-depth grids in one graph; sets LFBP_FORM)")
+    ap.add_argument("--pairs", choices=["0", "1"], default=None,
+                    help="with --no-tune: the pair consumer off or on (sets LFBP_PAIRS)")
+    ap.add_argument("--tile-bytes", type=int, default=None,
+                    help="with --no-tune: the tile-size target (sets LFBP_TILE_BYTES)")
     ap.add_argument("--table1-rows", default=None,
                     help="with --only table1: comma-separated cut-out sizes K of the rows to time")
     ap.add_argument("--table1-depths", type=int, default=11,
@@ -872,6 +879,11 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    # launch-shape knobs of the library, read at each call
+    for flag, env in ((args.form, "LFBP_FORM"), (args.pairs, "LFBP_PAIRS"),
+                      (args.tile_bytes, "LFBP_TILE_BYTES")):
+        if flag is not None:
+            os.environ[env] = str(flag)
     if args.impl == "reference":
         return run_reference(args)
     if args.only:
