@@ -694,17 +694,21 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
   const size_t chunk = (size_t)std::max(1, env_int("LFBP_HOST_CHUNK_MB", 64)) << 20;
   const int nch = (int)((bytes + chunk - 1) / chunk);
   std::lock_guard<std::mutex> lk(hp->mu);
-  while ((int)hp->ev.size() < 2 * nch + 1) {
+  while ((int)hp->ev.size() < 3 * nch + 1) {
     cudaEvent_t ev;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreate");
     hp->ev.push_back(ev);
   }
+  // events: in[k] = ev[3k], mapped[k] = ev[3k+1], out[k] = ev[3k+2], start = ev[3 nch].
+  // (Holding copy k in until copy k - 2 or k - 1 is back measured 2-3 x slower:
+  // a depth spanning several ranges holds its ranges back until its last one
+  // has arrived.)
   const unsigned char* hin = (const unsigned char*)H_host;
   unsigned char* hout = (unsigned char*)Hp_host;
   unsigned char* din = (unsigned char*)dH;
   unsigned char* dout = (unsigned char*)dHp;
-  cudaEvent_t start = hp->ev[2 * nch];
+  cudaEvent_t start = hp->ev[3 * nch];
   if ((e = cudaEventRecord(start, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(hp->h2d, start, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
@@ -712,55 +716,59 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
     *o = (size_t)k * chunk;
     *n = std::min(chunk, bytes - *o);
   };
-  for (int k = 0; k < nch; ++k) {  // every host->device copy, each with its event
+  int waited = -1;  // last chunk the caller's stream has waited for
+  int done = 0;     // chunks 0..done-1 are mapped and their copies back issued
+  int z = 0;        // next depth to map
+  for (int k = 0; k < nch; ++k) {
     size_t o, n;
     chunk_range(k, &o, &n);
     if ((e = cudaMemcpyAsync(din + o, hin + o, n, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess)
       return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    if ((e = cudaEventRecord(hp->ev[2 * k], hp->h2d)) != cudaSuccess)
+    if ((e = cudaEventRecord(hp->ev[3 * k], hp->h2d)) != cudaSuccess)
       return cuda_fail(e, "cudaEventRecord");
-  }
-  int waited = -1;  // last chunk the caller's stream has waited for
-  int done = 0;     // chunks 0..done-1 are mapped and on their way back
-  for (int z = 0; z < p->Nz;) {
-    const size_t z_end = p->off[z + 1] * (size_t)p->es;  // byte end of depth z
-    if (z_end == p->off[z] * (size_t)p->es) {  // an empty depth
-      ++z;
-      continue;
-    }
-    const int k_need = (int)((z_end - 1) / chunk);
-    int z1 = z + 1;  // depths z..z1-1 all end in chunk k_need
-    while (z1 < p->Nz && (p->off[z1 + 1] * (size_t)p->es - 1) / chunk == (size_t)k_need) ++z1;
-    if (k_need > waited) {
-      if ((e = cudaStreamWaitEvent(st, hp->ev[2 * k_need], 0)) != cudaSuccess)
-        return cuda_fail(e, "cudaStreamWaitEvent");
-      waited = k_need;
-    }
-    if ((rc = launch_plain(p, din, dout, mode, z, z1, st))) return rc;
-    // chunks wholly before the end of depth z1-1 can go back now
-    const size_t mapped_end = p->off[z1] * (size_t)p->es;
-    const int ready = z1 == p->Nz ? nch : (int)(mapped_end / chunk);
-    if (ready > done) {
-      cudaEvent_t mapped = hp->ev[2 * (ready - 1) + 1];
-      if ((e = cudaEventRecord(mapped, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-      if ((e = cudaStreamWaitEvent(hp->d2h, mapped, 0)) != cudaSuccess)
-        return cuda_fail(e, "cudaStreamWaitEvent");
-      for (int k = done; k < ready; ++k) {
-        size_t o, n;
-        chunk_range(k, &o, &n);
-        if ((e = cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, hp->d2h)) !=
-            cudaSuccess)
-          return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+    // map the depths whose last byte has now been copied in (consecutive depths
+    // waiting for the same chunk go in one launch sequence), and send back the
+    // chunks that every depth overlapping them has mapped
+    while (z < p->Nz) {
+      const size_t z_end = p->off[z + 1] * (size_t)p->es;  // byte end of depth z
+      if (z_end == p->off[z] * (size_t)p->es) {  // an empty depth
+        ++z;
+        continue;
       }
-      done = ready;
+      const int k_need = (int)((z_end - 1) / chunk);
+      if (k_need > k) break;
+      int z1 = z + 1;  // depths z..z1-1 all end in chunk k_need
+      while (z1 < p->Nz && (p->off[z1 + 1] * (size_t)p->es - 1) / chunk == (size_t)k_need) ++z1;
+      if (k_need > waited) {
+        if ((e = cudaStreamWaitEvent(st, hp->ev[3 * k_need], 0)) != cudaSuccess)
+          return cuda_fail(e, "cudaStreamWaitEvent");
+        waited = k_need;
+      }
+      if ((rc = launch_plain(p, din, dout, mode, z, z1, st))) return rc;
+      const size_t mapped_end = p->off[z1] * (size_t)p->es;
+      const int ready = z1 == p->Nz ? nch : (int)(mapped_end / chunk);
+      if (ready > done) {
+        cudaEvent_t mapped = hp->ev[3 * (ready - 1) + 1];
+        if ((e = cudaEventRecord(mapped, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(hp->d2h, mapped, 0)) != cudaSuccess)
+          return cuda_fail(e, "cudaStreamWaitEvent");
+        for (int kk = done; kk < ready; ++kk) {
+          size_t o2, n2;
+          chunk_range(kk, &o2, &n2);
+          if ((e = cudaMemcpyAsync(hout + o2, dout + o2, n2, cudaMemcpyDeviceToHost, hp->d2h)) !=
+              cudaSuccess)
+            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
+          if ((e = cudaEventRecord(hp->ev[3 * kk + 2], hp->d2h)) != cudaSuccess)
+            return cuda_fail(e, "cudaEventRecord");
+        }
+        done = ready;
+      }
+      z = z1;
     }
-    z = z1;
   }
   // the caller's stream sees the whole call complete: the last copy back, and
   // (by stream order) every map launched on it
-  cudaEvent_t fin = hp->ev[2 * (nch - 1) + 1];
-  if ((e = cudaEventRecord(fin, hp->d2h)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-  if ((e = cudaStreamWaitEvent(st, fin, 0)) != cudaSuccess)
+  if ((e = cudaStreamWaitEvent(st, hp->ev[3 * (nch - 1) + 2], 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
   return LFBP_OK;
 }
