@@ -70,7 +70,14 @@ struct DepthShapes {
   TileShape s[4];
 };
 
-__global__ void __launch_bounds__(kPlainThreads)
+// Register cap of the one-tile-per-CTA kernels: 48 registers (room for 5 CTAs
+// of 256 threads per SM).  Measured against the uncapped 61 registers, per-depth
+// graph: highres fp32 6080 -> 6273 GB/s, Table 1 N = 51 4709 -> 5692, fp16
+// 5330 -> 5410 (at 40 registers, 6 CTAs, the spills cost more than the warps
+// gain).
+constexpr int kPlainMinBlocks = 5;
+
+__global__ void __launch_bounds__(kPlainThreads, kPlainMinBlocks)
     k_gather_depth(TileDesc base, const __grid_constant__ DepthShapes shapes,
                    const unsigned char* __restrict__ in_depth, const unsigned char* in_safe_end,
                    unsigned char* __restrict__ out_depth, int J, int V, int stage_bytes) {
@@ -134,7 +141,7 @@ __global__ void __launch_bounds__(kPlainThreads)
 // every warp gathers).  The hardware block scheduler overlaps the CTAs of an
 // SM that wait for their copies with those that gather.
 // smem: [stage: stage_bytes][mbarrier][TileCtx][row-base table]
-__global__ void __launch_bounds__(kPlainThreads)
+__global__ void __launch_bounds__(kPlainThreads, kPlainMinBlocks)
     k_gather_tiles(const __grid_constant__ BatchPtrs ptrs, const TileDesc* __restrict__ tiles,
                    const TileShape* __restrict__ shapes, int stage_bytes) {
   extern __shared__ __align__(128) unsigned char smem[];
