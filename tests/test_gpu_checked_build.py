@@ -4,7 +4,8 @@ of the tile code is bounds- and alignment-checked on the GPU, the first
 violation is recorded (the access skipped, no trap) and lfbp_sync_status
 reports it.  Here the gather runs through it on tile shapes of every kind
 (one-row and multi-row tiles, column splits, fp16, the paper window, the
-batched form) and must report nothing and still match the oracle bit for bit.
+batched form in each of its three shapes) and must report nothing and still
+match the oracle bit for bit.
 The library is chosen at load time, so this runs in a child process."""
 import os
 import subprocess
@@ -53,8 +54,10 @@ print("checked ok")
 """
 
 
-def test_self_checking_build_reports_nothing():
-    env = dict(os.environ, LFBP_CHECK="1")
+@pytest.mark.parametrize("form", ["0", "1", "2"])
+def test_self_checking_build_reports_nothing(form):
+    """Each batched form (persistent CTAs, one tile per CTA, per-depth grids)."""
+    env = dict(os.environ, LFBP_CHECK="1", LFBP_FORM=form)
     out = subprocess.run([sys.executable, "-c", CHILD], cwd=ROOT, env=env, capture_output=True,
                          text=True, timeout=1500)
     assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-3000:]

@@ -139,8 +139,12 @@ def test_special_bit_patterns(lf):
     _assert_same_bits(lf.backproject_batched([plan], [H])[0], want, "batched")
 
 
-def test_batched_mixed_dtypes_and_pointer_changes(lf):
-    """One persistent launch over fp32 and fp16 arrays; replay with new buffers."""
+@pytest.mark.parametrize("form", ["0", "1", "2"])
+def test_batched_mixed_dtypes_and_pointer_changes(lf, form, monkeypatch):
+    """One batched launch over fp32 and fp16 arrays, replayed with new buffers (the
+    graph's node parameters patched), in each batched form: persistent CTAs, one
+    tile per CTA, per-depth grids (one graph node per depth of every array)."""
+    monkeypatch.setenv("LFBP_FORM", form)
     shapes = [(5, 5, [15, 25], [15, 25], torch.float32), (3, 7, [9, 27, 3], [21, 7, 35], torch.float16),
               (19, 19, [57], [57], torch.float16), (11, 11, [33, 55], [33, 55], torch.float32)]
     plans = [lf.Plan(a, b, c, d, t) for a, b, c, d, t in shapes]
@@ -327,22 +331,26 @@ def test_ragged_workload_full_tuned(lf):
 
 
 def test_every_launch_shape_of_the_tuner_grid(lf, monkeypatch):
-    """Each tile-size x CTAs-per-SM shape the autotuner may pick maps bit-exactly
-    (mid workload, fp32, and its fp16 copy in the same batch)."""
+    """Each launch shape the autotuner may pick maps bit-exactly (mid workload,
+    fp32, and its fp16 copy in the same batch): persistent CTAs at every tile
+    size x CTAs per SM, and the two one-tile-per-CTA forms at every tile size."""
     spec = lfgen.config_specs("mid")[0]
     H32 = lfgen.generate(spec, device="cuda")
     H16 = H32.half()
     plans = [lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float32),
              lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, torch.float16)]
     want = [oracle.transpose(h.cpu().numpy(), spec.Nx, spec.Ny, spec.Ks, spec.Kt) for h in (H32, H16)]
-    for tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536):
-        for cps in (1, 2, 3, 4):
-            monkeypatch.setenv("LFBP_TILE_BYTES", str(tb))
-            monkeypatch.setenv("LFBP_CTAS_PER_SM", str(cps))
-            outs = lf.backproject_batched(plans, [H32, H16])
-            lf.sync_status()
-            for o, w in zip(outs, want):
-                _assert_same_bits(o, w, f"tile {tb} cps {cps}")
+    shapes = [("0", tb, cps) for tb in (12288, 16384, 24576, 32768, 40960, 49152, 65536)
+              for cps in (1, 2, 3, 4)]
+    shapes += [(form, tb, 0) for form in ("1", "2") for tb in (24576, 32768, 40960, 49152, 65536)]
+    for form, tb, cps in shapes:
+        monkeypatch.setenv("LFBP_FORM", form)
+        monkeypatch.setenv("LFBP_TILE_BYTES", str(tb))
+        monkeypatch.setenv("LFBP_CTAS_PER_SM", str(max(cps, 1)))
+        outs = lf.backproject_batched(plans, [H32, H16])
+        lf.sync_status()
+        for o, w in zip(outs, want):
+            _assert_same_bits(o, w, f"form {form} tile {tb} cps {cps}")
 
 
 # Table 1 of the paper (n_s = n_t, n_x, n_y): K not a multiple of N, rows of
