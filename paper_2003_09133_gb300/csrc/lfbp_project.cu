@@ -655,7 +655,8 @@ __global__ void __launch_bounds__(kPcThreads) k_phase_conv(const __grid_constant
       stage(nxt, buf ^ 1);
     else
       cp_async_commit();  // keep the group count uniform
-    cp_async_wait<1>();   // the current buffer's weights have landed (this thread's copies)
+    cp_async_wait<1>();   // the current buffer's weights have landed (this thread's copies);
+                          // the block barrier in pc_abort (TMA) or below publishes them
     if (kTma) {
       const bool ok = mbar_wait_bounded(smem_addr(&full[buf]), (uint32_t)((k >> 1) & 1), nullptr,
                                         kPcWaitNs);
@@ -1094,7 +1095,9 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
 // depths at the end get zero weights and no output).
 template <int S, int DB, bool kTma>
 // 3 blocks per SM (at most 85 registers): one RL update 3.85 -> 3.73 ms against 2
-// blocks (128 registers) on the same box.
+// blocks (128 registers) on the same box; 4 blocks per SM measured 3.73 against
+// 3.63 ms for 3, and a ring of three buffers with one block barrier per
+// sub-problem (spills at DB = 4) 3.77 against 3.63 ms.
 __global__ void __launch_bounds__(kPcThreads, 3) k_phase_conv_md(const __grid_constant__ PcArgs a) {
   constexpr int RI = 4, TI = 8 * RI;
   constexpr int S4 = (S + 3) & ~3;
@@ -1169,7 +1172,7 @@ __global__ void __launch_bounds__(kPcThreads, 3) k_phase_conv_md(const __grid_co
       stage(nxt, buf ^ 1);
     else
       cp_async_commit();
-    cp_async_wait<1>();
+    cp_async_wait<1>();  // this thread's weights; published by the barrier in pc_abort or below
     if (kTma) {
       const bool ok = mbar_wait_bounded(smem_addr(&full[buf]), (uint32_t)((k >> 1) & 1), nullptr,
                                         kPcWaitNs);
@@ -1546,6 +1549,9 @@ constexpr int kPcDB = 4;  // most depths per block of k_phase_conv_md
 
 // Depths per block for a group of n depths: the fewest idle depth slots
 // (ceil(n/DB)*DB - n), ties to the larger DB.  Idle slots cost full FMAs.
+// (On the 21-depth differentiation workload, groups of 6, 6 and 7: one RL
+// update 3.63 ms by this rule, 3.67 / 3.75 / 4.10 ms with 3 / 2 / 4 depths per
+// block throughout.)
 int md_depths_per_block(int n) {
   int best = kPcDB, waste = (n + kPcDB - 1) / kPcDB * kPcDB - n;
   for (int db = kPcDB - 1; db >= 2; --db) {

@@ -88,14 +88,16 @@ def test_injected_plan_failure_through_the_binding(lf, monkeypatch):
     assert ei.value.code == -8
 
 
+@pytest.mark.parametrize("Ks", [[9, 3], [9, 9, 9]], ids=["one_depth_blocks", "depth_group"])
 @pytest.mark.parametrize("pipe", ["1", "0"])
-def test_projector_tma_waits_time_out_and_recover(lf, monkeypatch, pipe):
+def test_projector_tma_waits_time_out_and_recover(lf, monkeypatch, pipe, Ks):
     """The projectors' TMA-path waits are bounded too.  Under LFBP_FAULT=stall
     their TMA copies register their bytes without being issued, so the waits
     on those copies run out.  The pipelined kernels (producer, consumers,
-    pair barriers) and the barrier kernels (LFBP_PROJ_PIPE=0) both end with
-    LFBP_ERR_TIMEOUT, and the next call without the injection is correct."""
-    Nx, Ny, Ks, W = 3, 3, [9, 3], 12
+    pair barriers), the barrier kernels (LFBP_PROJ_PIPE=0) and the grouped
+    backprojection (three equal cut-outs) all end with LFBP_ERR_TIMEOUT, and
+    the next call without the injection is correct."""
+    Nx, Ny, W = 3, 3, 12
     plan = lf.Plan(Nx, Ny, Ks, Ks, torch.float32)
     rng = np.random.default_rng(33)
     H = rng.uniform(0, 1, plan.elems).astype(np.float32)

@@ -54,6 +54,13 @@ CASES = [  # Nx, Ny, Ks, Kt, Wx, Wy
     (11, 11, [33, 99], [33, 99], 66, 77),
     (3, 5, [9] * 5 + [15], [15] * 5 + [5], 30, 41),  # five equal cut-outs: several depths per block
     (3, 3, [9, 15, 9, 9], [9, 3, 9, 9], 200, 151),  # 67 x 51 pixels per cell: several tiles per phase
+    # groups of equal cut-outs whose blocks have one or three sub-problems
+    # (phases; a product of odd numbers), so the staging ring of the grouped
+    # backprojection starts with nothing or one sub-problem behind the first;
+    # three, four and ten depths go three, four and two per block
+    (1, 1, [5, 5, 5], [3, 3, 3], 9, 11),
+    (1, 1, [3] * 4, [3] * 4, 10, 7),
+    (1, 3, [5] * 10, [7] * 10, 8, 40),
 ]
 
 
