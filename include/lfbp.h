@@ -135,7 +135,9 @@ int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_st
  *    the map of each depth (one launch per depth, on cuda_stream) as soon as
  *    the range holding its last byte has arrived, and device->host copies of
  *    each range once every depth overlapping it is mapped, on a second helper
- *    stream: both directions of the host link run at the same time.
+ *    stream: both directions of the host link run at the same time.  The
+ *    depths go in memory order; LFBP_HOST_ORDER=rotate (read at each call)
+ *    takes them in a rotation that starts at the smallest depth.
  *    dH_work, dHp_work hold H and H' afterwards.  Page-locked (pinned) host
  *    memory is needed for the copies to overlap; pageable memory works.
  *  - LFBP_HOST_PATH=zerocopy in the environment (read at each call), with

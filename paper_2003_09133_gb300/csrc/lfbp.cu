@@ -21,6 +21,7 @@
 
 #include "lfbp.h"
 #include "lfbp_device.cuh"
+#include "lfbp_host_sched.h"
 #include "lfbp_project.h"
 
 namespace lfbp {
@@ -694,88 +695,74 @@ int run_host(lfbp_plan p, const void* H_host, void* Hp_host, void* dH, void* dHp
   // The copies move fixed byte ranges of LFBP_HOST_CHUNK_MB (default 64) MB,
   // cut at multiples of the chunk size whatever the depth boundaries (copies
   // from and to aligned addresses run at the link's rate; copies cut at depth
-  // starts, which are only 4-byte aligned, measured 25 % slower).  Depth z is
-  // mapped once the chunk holding its last byte has arrived (consecutive
-  // depths waiting for the same chunk go in one launch sequence), and chunk k
-  // is copied back once every depth that overlaps it is mapped.
+  // starts, which are only 4-byte aligned, measured 25 % slower).  A depth is
+  // mapped once every chunk it overlaps has arrived, and a chunk is copied back
+  // once every depth overlapping it is mapped.  host_schedule gives the order:
+  // the depths in memory order (LFBP_HOST_ORDER=rotate: a rotation that starts
+  // and ends on small depths, which measured slower).
+  // (Holding copy k in until copy k - 2 or k - 1 is back measured 2-3 x slower:
+  // a depth spanning several ranges holds its ranges back until its last one
+  // has arrived.)
   const size_t chunk = (size_t)std::max(1, env_int("LFBP_HOST_CHUNK_MB", 64)) << 20;
   const int nch = (int)((bytes + chunk - 1) / chunk);
+  const char* ord = std::getenv("LFBP_HOST_ORDER");
+  std::vector<size_t> zoff(p->Nz + 1);
+  for (int z = 0; z <= p->Nz; ++z) zoff[z] = p->off[z] * (size_t)p->es;
+  const std::vector<HostOp> ops = host_schedule(zoff, chunk, !(ord && !std::strcmp(ord, "rotate")));
   std::lock_guard<std::mutex> lk(hp->mu);
-  while ((int)hp->ev.size() < 3 * nch + 1) {
+  while ((int)hp->ev.size() < 2 * nch + 2) {
     cudaEvent_t ev;
     if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
       return cuda_fail(e, "cudaEventCreate");
     hp->ev.push_back(ev);
   }
-  // events: in[k] = ev[3k], mapped[k] = ev[3k+1], out[k] = ev[3k+2], start = ev[3 nch].
-  // (Holding copy k in until copy k - 2 or k - 1 is back measured 2-3 x slower:
-  // a depth spanning several ranges holds its ranges back until its last one
-  // has arrived.)
+  // events: in[k] = ev[k]; the j-th release of copies back ev[nch + j] (at
+  // most nch: each releases a chunk); start ev[2 nch]; end ev[2 nch + 1]
   const unsigned char* hin = (const unsigned char*)H_host;
   unsigned char* hout = (unsigned char*)Hp_host;
   unsigned char* din = (unsigned char*)dH;
   unsigned char* dout = (unsigned char*)dHp;
-  cudaEvent_t start = hp->ev[3 * nch];
+  cudaEvent_t start = hp->ev[2 * nch], end = hp->ev[2 * nch + 1];
   if ((e = cudaEventRecord(start, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(hp->h2d, start, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
-  auto chunk_range = [&](int k, size_t* o, size_t* n) {
-    *o = (size_t)k * chunk;
-    *n = std::min(chunk, bytes - *o);
-  };
-  int waited = -1;  // last chunk the caller's stream has waited for
-  int done = 0;     // chunks 0..done-1 are mapped and their copies back issued
-  int z = 0;        // next depth to map
-  for (int k = 0; k < nch; ++k) {
-    size_t o, n;
-    chunk_range(k, &o, &n);
-    if ((e = cudaMemcpyAsync(din + o, hin + o, n, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess)
-      return cuda_fail(e, "cudaMemcpyAsync(H2D)");
-    if ((e = cudaEventRecord(hp->ev[3 * k], hp->h2d)) != cudaSuccess)
-      return cuda_fail(e, "cudaEventRecord");
-    // map the depths whose last byte has now been copied in (consecutive depths
-    // waiting for the same chunk go in one launch sequence), and send back the
-    // chunks that every depth overlapping them has mapped
-    while (z < p->Nz) {
-      const size_t z_end = p->off[z + 1] * (size_t)p->es;  // byte end of depth z
-      if (z_end == p->off[z] * (size_t)p->es) {  // an empty depth
-        ++z;
-        continue;
-      }
-      const int k_need = (int)((z_end - 1) / chunk);
-      if (k_need > k) break;
-      int z1 = z + 1;  // depths z..z1-1 all end in chunk k_need
-      while (z1 < p->Nz && (p->off[z1 + 1] * (size_t)p->es - 1) / chunk == (size_t)k_need) ++z1;
-      if (k_need > waited) {
-        if ((e = cudaStreamWaitEvent(st, hp->ev[3 * k_need], 0)) != cudaSuccess)
+  std::vector<int> pos(nch, -1);  // issue position of each copy in
+  int issued = 0, waited = -1;    // copies in issued; position the caller's stream waited for
+  int releases = 0;
+  bool mapped_since_release = false;
+  for (const HostOp& op : ops) {
+    const size_t o = (size_t)op.a * chunk, n = std::min(chunk, bytes - o);
+    if (op.kind == HostOp::kIn) {
+      if ((e = cudaMemcpyAsync(din + o, hin + o, n, cudaMemcpyHostToDevice, hp->h2d)) != cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(H2D)");
+      if ((e = cudaEventRecord(hp->ev[op.a], hp->h2d)) != cudaSuccess)
+        return cuda_fail(e, "cudaEventRecord");
+      pos[op.a] = issued++;
+    } else if (op.kind == HostOp::kMap) {
+      if (pos[op.wait] > waited) {  // copies in land in issue order
+        if ((e = cudaStreamWaitEvent(st, hp->ev[op.wait], 0)) != cudaSuccess)
           return cuda_fail(e, "cudaStreamWaitEvent");
-        waited = k_need;
+        waited = pos[op.wait];
       }
-      if ((rc = launch_plain(p, din, dout, mode, z, z1, st))) return rc;
-      const size_t mapped_end = p->off[z1] * (size_t)p->es;
-      const int ready = z1 == p->Nz ? nch : (int)(mapped_end / chunk);
-      if (ready > done) {
-        cudaEvent_t mapped = hp->ev[3 * (ready - 1) + 1];
-        if ((e = cudaEventRecord(mapped, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
-        if ((e = cudaStreamWaitEvent(hp->d2h, mapped, 0)) != cudaSuccess)
+      if ((rc = launch_plain(p, din, dout, mode, op.a, op.b, st))) return rc;
+      mapped_since_release = true;
+    } else {
+      if (mapped_since_release) {
+        cudaEvent_t rel = hp->ev[nch + releases++];
+        if ((e = cudaEventRecord(rel, st)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+        if ((e = cudaStreamWaitEvent(hp->d2h, rel, 0)) != cudaSuccess)
           return cuda_fail(e, "cudaStreamWaitEvent");
-        for (int kk = done; kk < ready; ++kk) {
-          size_t o2, n2;
-          chunk_range(kk, &o2, &n2);
-          if ((e = cudaMemcpyAsync(hout + o2, dout + o2, n2, cudaMemcpyDeviceToHost, hp->d2h)) !=
-              cudaSuccess)
-            return cuda_fail(e, "cudaMemcpyAsync(D2H)");
-          if ((e = cudaEventRecord(hp->ev[3 * kk + 2], hp->d2h)) != cudaSuccess)
-            return cuda_fail(e, "cudaEventRecord");
-        }
-        done = ready;
+        mapped_since_release = false;
       }
-      z = z1;
+      if ((e = cudaMemcpyAsync(hout + o, dout + o, n, cudaMemcpyDeviceToHost, hp->d2h)) !=
+          cudaSuccess)
+        return cuda_fail(e, "cudaMemcpyAsync(D2H)");
     }
   }
   // the caller's stream sees the whole call complete: the last copy back, and
   // (by stream order) every map launched on it
-  if ((e = cudaStreamWaitEvent(st, hp->ev[3 * (nch - 1) + 2], 0)) != cudaSuccess)
+  if ((e = cudaEventRecord(end, hp->d2h)) != cudaSuccess) return cuda_fail(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(st, end, 0)) != cudaSuccess)
     return cuda_fail(e, "cudaStreamWaitEvent");
   return LFBP_OK;
 }

@@ -230,16 +230,20 @@ def test_autograd_workload_map(lf):
     _full_workload(lf, "autograd")
 
 
-@pytest.mark.parametrize("path", ["copy", "zerocopy"])
+@pytest.mark.parametrize("path", ["copy", "copy_rotation", "zerocopy"])
 def test_host_to_host_pipeline(lf, path, monkeypatch):
     """Pinned host H -> H' -> pinned host: by default aligned byte ranges are
     staged through the device buffers with overlapped copies (here 1 MB ranges,
-    so that depths straddle them); LFBP_HOST_PATH=zerocopy lets the kernel read
-    and write the mapped host buffers itself."""
+    so that depths straddle them), the depths in memory order
+    (LFBP_HOST_ORDER=rotate: in a rotation that starts at the smallest);
+    LFBP_HOST_PATH=zerocopy lets the kernel read and write the mapped host
+    buffers itself."""
     if path == "zerocopy":
         monkeypatch.setenv("LFBP_HOST_PATH", "zerocopy")
     else:
         monkeypatch.setenv("LFBP_HOST_CHUNK_MB", "1")
+    if path == "copy_rotation":
+        monkeypatch.setenv("LFBP_HOST_ORDER", "rotate")
     for name, dtype in (("mid", torch.float32), ("tiny", torch.float16)):
         spec = lfgen.config_specs(name)[0]
         plan = lf.Plan(spec.Nx, spec.Ny, spec.Ks, spec.Kt, dtype)
