@@ -430,6 +430,8 @@ def run_ours(args):
         for p, h, o in zip(plans, Hs, outs):
             lf.backproject_array(p, h, o)
 
+    step_ms = []  # the per-step times of the last timed() call (this rank)
+
     def timed(fn, steps, warmup, clocks=False):
         for _ in range(warmup):
             fn()
@@ -453,6 +455,7 @@ def run_ours(args):
             sampler.__exit__(None, None, None)
         lf.sync_status()
         ms = [a.elapsed_time(b) for a, b in ev]
+        step_ms[:] = ms
         mean = sum(ms) / len(ms)
         return _max_over_ranks(mean, world), min(ms), (sampler.summary() if sampler else None)
 
@@ -476,7 +479,8 @@ def run_ours(args):
                 lf.backproject_array_host(p, hi, ho, work=(di, do))
 
         n_e2e = max(3, min(args.steps, 20))
-        t_e2e, _, _ = timed(step_e2e, n_e2e, 2)
+        t_e2e, best_e2e, _ = timed(step_e2e, n_e2e, 2)
+        e2e_ms = sorted(step_ms)
         nbytes = sum(h.numel() * h.element_size() for h in Hs)
 
         # the host link alone on this machine: the same bytes copied host -> device
@@ -500,6 +504,10 @@ def run_ours(args):
         e2e = {"value": round(job_total / (t_e2e * 1e-3) / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                "ms_per_step": round(t_e2e, 3),
+               # the spread of the steps behind the mean (this rank): sporadic
+               # slow steps on a shared host show as a mean above the median
+               "step_ms_median": round(e2e_ms[len(e2e_ms) // 2], 3),
+               "step_ms_min": round(best_e2e, 3),
                "link_only_ms": round(t_link, 3),
                "link_only": "the same bytes copied both ways at once, no map (not timed in e2e)"}
         del hosts, host_out, dev_in
