@@ -483,7 +483,7 @@ def run_ours(args):
         e2e_ms = sorted(step_ms)
         nbytes = sum(h.numel() * h.element_size() for h in Hs)
 
-        # the host link alone on this machine: the same bytes copied host -> device
+        # the host link alone: the same bytes copied host -> device
         # and device -> host at the same time on two streams, no map (context
         # for the e2e number: its floor)
         s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()

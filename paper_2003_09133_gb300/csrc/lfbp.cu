@@ -21,7 +21,6 @@
 
 #include "lfbp.h"
 #include "lfbp_device.cuh"
-#include "lfbp_host_sched.h"
 #include "lfbp_project.h"
 
 namespace lfbp {
@@ -350,6 +349,8 @@ __global__ void __launch_bounds__(kPersistentThreads, LFBP_PERSIST_MINB)
 
 // ====================================================================== host
 #include <cmath>
+
+#include "lfbp_host_sched.h"
 
 using namespace lfbp;
 

@@ -1095,7 +1095,7 @@ __global__ void __launch_bounds__(kPcPipeThreads) k_phase_grad_pipe(const __grid
 // depths at the end get zero weights and no output).
 template <int S, int DB, bool kTma>
 // 3 blocks per SM (at most 85 registers): one RL update 3.85 -> 3.73 ms against 2
-// blocks (128 registers) on the same box; 4 blocks per SM measured 3.73 against
+// blocks (128 registers) on the same GPU; 4 blocks per SM measured 3.73 against
 // 3.63 ms for 3, and a ring of three buffers with one block barrier per
 // sub-problem (spills at DB = 4) 3.77 against 3.63 ms.
 __global__ void __launch_bounds__(kPcThreads, 3) k_phase_conv_md(const __grid_constant__ PcArgs a) {
