@@ -133,7 +133,7 @@ int lfbp_backproject_array(lfbp_plan p, const void* dH, void* dHp, void* cuda_st
  *  - default: host->device copies of fixed 64 MB byte ranges (aligned;
  *    LFBP_HOST_CHUNK_MB sets the size) on one library-owned helper stream,
  *    the map of each depth (one launch per depth, on cuda_stream) as soon as
- *    the range holding its last byte has arrived, and device->host copies of
+ *    every range it overlaps has arrived, and device->host copies of
  *    each range once every depth overlapping it is mapped, on a second helper
  *    stream: both directions of the host link run at the same time.  The
  *    depths go in memory order; LFBP_HOST_ORDER=rotate (read at each call)
